@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of the AIM matrix-vector product on synthetic PEC scatterers.
+
+Default workload: the 4 lambda PEC sphere of the paper's sphere family
+(Section 2.1; geodesic icosphere at mean edge <= lambda/9, N = 58,080 RWG
+unknowns, grid 83^3 zero-padded to 180^3, h = lambda/10, 27-point stencils,
+near radius 3h), one right-hand side, plain complex128 (FP64) product.  A
+step is one full AIM product (projection, five FFT passes, interpolation and
+near correction).  Inputs are resident in HBM; the working set of a product
+(~1.4 GB) exceeds L2 and L2 is also flushed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload NAME] [--impl ours|reference]
+
+One JSON line on stdout (rank 0).  Multi-GPU runs are replicas: each rank
+solves its own copy (no data-path collective), value = total products / time.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AIM matvec/s and served solves/s (p50/p99) at stated err, vs FP64 plain path"
+ETA0 = 376.730313668
+K0 = 2.0 * np.pi
+H = 0.1
+
+WORKLOADS = {
+    # name: (kind, size, nrhs, precision)
+    "pec-sphere-r4lambda-fp64-1rhs": ("sphere", 4.0, 1, "c128"),
+    "pec-sphere-r4lambda-c64-1rhs": ("sphere", 4.0, 1, "c64"),
+    "pec-plate-1lambda-fp64-1rhs": ("plate", 1.0, 1, "c128"),
+    "pec-plate-32lambda-c64-64rhs": ("plate", 32.0, 64, "c64"),
+    "pec-sphere-r16lambda-c64-8rhs": ("sphere", 16.0, 8, "c64"),
+}
+DEFAULT = "pec-sphere-r4lambda-fp64-1rhs"
+
+
+def mesh_for(kind, size):
+    from aim_inputs import icosphere_frequency, icosphere_mesh, plate_mesh
+
+    if kind == "plate":
+        return plate_mesh(size, int(round(9 * size)))
+    return icosphere_mesh(size, icosphere_frequency(size))
+
+
+# ---------------------------------------------------------------- kernel models
+def kernel_models(N, n, L, nnz, nent, S, nrhs, e):
+    """Algorithmic bytes and flops per launch of each product kernel.
+
+    e = bytes per complex value, w = bytes per real weight.  FFT flops use
+    the 5 L log2 L convention per length-L transform.
+    """
+    nx, ny, nz = n
+    Lx, Ly, Lz = L
+    G = 4 * nrhs
+    w = e // 2
+    Nc = nx * ny * nz
+    lg = np.log2
+    oct_ = (Lx // 2 + 1) * (Ly // 2 + 1) * (Lz // 2 + 1)
+    m = {}
+    m["proj_gather"] = (nent * (4 + 4 * w) + (Nc + 1) * 4 + nrhs * N * e + G * Nc * e, 16.0 * nent * nrhs)
+    m["fft_z_fwd"] = (G * (Nc + Lz * ny * nx) * e, G * nx * ny * 5.0 * Lz * lg(Lz))
+    m["fft_y_fwd"] = (G * (Lz * ny * nx + Lz * Ly * nx) * e, G * nx * Lz * 5.0 * Ly * lg(Ly))
+    m["fft_x_conv"] = (2 * G * Lz * Ly * nx * e + oct_ * e, G * Ly * Lz * (10.0 * Lx * lg(Lx) + 6.0 * Lx))
+    m["fft_y_inv"] = m["fft_y_fwd"]
+    m["fft_z_inv"] = m["fft_z_fwd"]
+    m["interp_near"] = (
+        G * Nc * e + N * 4 * S * w + N * 4 + nnz * (e + 4) + (N + 1) * 4 + 2 * nrhs * N * e,
+        nrhs * (16.0 * N * S + 8.0 * nnz),
+    )
+    return m
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1010_1456_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(workload, kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the sources still match."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    dig = source_digest()
+    for line in open(path):
+        p = line.split()
+        if len(p) == 4 and p[0] == workload and p[1] == kernel and p[2] == dig:
+            return float(p[3])
+    return None
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_matvec_rate(verts, tris, nrhs, budget_s=20.0, sample_rows=192, seed=0):
+    """Oracle products per second on this host, as the oracle stands.
+
+    The oracle's near-zone setup for all rows of a large problem takes far
+    longer than a bench run, so the near matrix is built for a seeded sample
+    of rows; one product is timed as the full grid part (projection, FFT
+    convolution, interpolation of every row) plus the near SpMV of the sampled
+    rows scaled by N / rows.
+    """
+    from aim_inputs import random_complex
+    from oracle import aim as oaim
+    from oracle.rwg import RWG
+
+    rwg = RWG(verts, tris)
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(rwg.N, min(sample_rows, rwg.N), replace=False))
+    op = oaim.AIMOperator(rwg, K0, H, 2, near_rows=rows)
+    x = random_complex((nrhs, rwg.N), seed + 1)
+    reps, t_far, t_near = 0, 0.0, 0.0
+    t_start = time.perf_counter()
+    while reps < 1 or (time.perf_counter() - t_start < budget_s and reps < 50):
+        t0 = time.perf_counter()
+        op.far_matvec(x)
+        t1 = time.perf_counter()
+        (op.Znear @ x.T)
+        t2 = time.perf_counter()
+        t_far += t1 - t0
+        t_near += t2 - t1
+        reps += 1
+    per = (t_far + t_near * (rwg.N / len(rows))) / reps
+    return {
+        "value": nrhs / per,
+        "unit": "matvec/s",
+        "cores": os.cpu_count(),
+        "kind": "oracle",
+        "sample": f"{reps} oracle products (NumPy/SciPy FP64, scipy.fft workers={os.cpu_count()}); full grid part, "
+                  f"near SpMV of {len(rows)} seeded rows scaled by N/{len(rows)}",
+    }
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    kind, size, nrhs, prec = WORKLOADS[args.workload]
+    verts, tris = mesh_for(kind, size)
+    base = oracle_matvec_rate(verts, tris, nrhs, budget_s=max(5.0, 4.0 * args.steps))
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": base["value"],
+        "unit": "matvec/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 / base["value"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "nrhs": nrhs},
+        "cpu_baseline": base,
+        "e2e": {"value": base["value"], "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_1010_1456_gb300 as g
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    kind, size, nrhs, prec = WORKLOADS[args.workload]
+    verts, tris = mesh_for(kind, size)
+    P = g.AIM_C128 if prec == "c128" else g.AIM_C64
+    cdt = torch.complex128 if prec == "c128" else torch.complex64
+    e = 16 if prec == "c128" else 8
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    ctx = g.aim_setup(verts, tris, K0, H, M=2, near_radius=3 * H, max_rhs=nrhs, precision=P,
+                      stream=stream.cuda_stream)
+    setup_s = time.perf_counter() - t0
+    n, L, nnz = g.aim_grid_info(ctx)
+    N = ctx.N
+    from aim_inputs import random_complex
+
+    xh = random_complex((nrhs, N), 1000 + rank).astype(np.complex128 if prec == "c128" else np.complex64)
+    x = torch.from_numpy(xh).to(dev)
+    y = torch.empty_like(x)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        g.aim_matvec(ctx, x, y, precision=P)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    g.aim_profile(ctx, 2)
+    g.aim_profile(ctx, 1)
+    l0 = g.aim_launch_count(ctx)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush between timed products, outside the events
+            ev[i][0].record(stream)
+            g.aim_matvec(ctx, x, y, precision=P)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+    launches = g.aim_launch_count(ctx) - l0
+    g.aim_profile(ctx, 0)
+    prof = g.aim_profile_read(ctx)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * nrhs / (total_ms * 1e-3)
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    e2e_steps = max(3, args.steps)
+    g.aim_matvec_host(ctx, xh, precision=P)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.aim_matvec_host(ctx, xh, precision=P)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * e2e_steps * nrhs / e2e_s, "unit": "matvec/s",
+           "h2d_bytes_per_step": int(xh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
+
+    # roofline of the dominant kernel
+    nent = int(g.aim_export(ctx, g.AIM_EXPORT_PROJ_PTR)[-1])
+    models = kernel_models(N, n, L, nnz, nent, 27, nrhs, e)
+    kernels = {k: {"launches": c, "avg_ms": ms / max(c, 1), "share": ms / max(sum(v[1] for v in prof.values()), 1e-30)}
+               for k, (c, ms) in prof.items()}
+    dom = max(kernels, key=lambda k: kernels[k]["share"])
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+    alu64 = g.aim_probe_fma_peak(64)
+    alu32 = g.aim_probe_fma_peak(32)
+    alu = alu64 if prec == "c128" else alu32
+    bytes_, flops = models.get(dom, (None, None))
+    avg_s = kernels[dom]["avg_ms"] * 1e-3
+    if bytes_ is not None:
+        intensity = flops / bytes_
+        ridge = alu * 1e12 / (hbm * 1e9)
+        if intensity > ridge:
+            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": alu, "unit": "TFLOP/s",
+                    "peak_source": f"FP{'64' if prec == 'c128' else '32'} FMA probe (aim_probe_fma_peak), this run"}
+        else:
+            roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+                    "peak_source": hbm_src}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["kernel"] = dom
+        roof["algorithmic_bytes"] = bytes_
+        roof["algorithmic_flops"] = flops
+        roof["traffic"] = ncu_traffic(args.workload, dom)
+    else:
+        roof = None
+    for k, v in kernels.items():
+        if k in models:
+            b, f = models[k]
+            s = v["avg_ms"] * 1e-3
+            v["GB/s"] = b / s / 1e9
+            v["TFLOP/s"] = f / s / 1e12
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "matvec/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if prec == "c128" else "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "grid": n, "padded": L, "nnz_near": nnz, "nrhs": nrhs,
+                   "M": 2, "h_lambda": H, "near_radius_h": 3, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2)},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "kernels": kernels,
+        "fp64_fma_tflops": alu64,
+        "fp32_fma_tflops": alu32,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_matvec_rate(verts, tris, nrhs, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,212 @@
+/*
+ * aim.h - C ABI of the GB300 AIM library: AIM-accelerated EFIE method of
+ * moments for time-harmonic scattering from PEC surfaces (Wei & Yilmaz,
+ * "A Hybrid Parallelization of AIM for Multi-Core Clusters", Sections 2.2
+ * and 4.1; eq. 1 for the RCS error).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units: lengths in wavelengths is customary (k = 2 pi) but any consistent
+ * unit works; k is the wavenumber in the same unit.  Time convention
+ * exp(+j w t), Green's function exp(-j k R) / (4 pi R), free-space impedance
+ * 376.730313668 ohm.
+ *
+ * Complex vectors are interleaved (re, im) and RHS-major: element (b, m) of a
+ * batch of nrhs vectors of length N sits at offset b*N + m.  AIM_C128 vectors
+ * are pairs of doubles (16 bytes per element), AIM_C64 vectors pairs of
+ * floats (8 bytes).  Pointers named *_dev are CUDA device pointers; all other
+ * pointers are host pointers.  Device work is enqueued on the context's
+ * stream (aim_opts.stream, changeable with aim_set_stream); a call returns
+ * once its work is enqueued unless its comment says it synchronises.
+ *
+ * The unknowns are the RWG functions of the mesh's interior edges, ordered by
+ * (low vertex index, high vertex index); the RWG's "+" triangle is the lower-
+ * indexed of its two triangles.
+ *
+ * Errors: every int-returning call returns AIM_OK (0) or one of the AIM_E*
+ * codes below and never aborts the process; aim_strerror() gives a message
+ * and aim_last_error() the detail of the calling thread's last failure.
+ * Ownership: the context owns all of its device and host memory; caller
+ * buffers are only read or written during the call (or its enqueued work).
+ */
+#ifndef AIM_H
+#define AIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  AIM_OK = 0,
+  AIM_EINVAL = 1,   /* bad argument, bad mesh, unsupported size */
+  AIM_ENOMEM = 2,   /* device or host allocation failed */
+  AIM_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+  AIM_ENOCONV = 4,  /* solver hit its iteration limit; X holds the last iterate */
+  AIM_ETIMEOUT = 5, /* a bounded device wait gave up */
+  AIM_ENODEV = 6    /* no CUDA device visible */
+};
+
+enum { AIM_C64 = 1, AIM_C128 = 2 };
+
+typedef struct aim_ctx aim_ctx; /* opaque, library-owned */
+
+/* Triangle mesh, copied by aim_setup (caller keeps ownership). */
+typedef struct {
+  int32_t nv;           /* number of vertices */
+  int32_t nt;           /* number of triangles */
+  const double* verts;  /* [nv][3] host, vertex coordinates */
+  const int32_t* tris;  /* [nt][3] host, vertex indices, any orientation */
+} aim_mesh;
+
+/* Options; aim_default_opts() fills the defaults shown. */
+typedef struct {
+  int precision;   /* solver inner-matvec precision: AIM_C128 (default) or AIM_C64 */
+  int restart;     /* GMRES restart length m (default 50, 1..200) */
+  int maxit;       /* total inner iteration cap per solve (default 3000) */
+  int check_every; /* host reads the residual estimate every k iterations (default 5) */
+  int max_rhs;     /* largest nrhs the context is sized for (default 1, <= 256) */
+  int verbose;     /* 0: silent (default) */
+  void* stream;    /* cudaStream_t; NULL = the legacy default stream */
+} aim_opts;
+
+/* Per-solve report. rel_res and iters are caller arrays of length nrhs. */
+typedef struct {
+  int32_t iterations;    /* inner Arnoldi steps taken (all right-hand sides in lockstep) */
+  int32_t restarts;      /* restart cycles (each ends with an FP64 true residual) */
+  double* rel_res;       /* [nrhs] out: final true relative residual ||b - Z x|| / ||b|| */
+  int32_t* converged;    /* [nrhs] out: 1 if rel_res <= tol */
+} aim_solve_info;
+
+void aim_default_opts(aim_opts* opts);
+
+/*
+ * Build a context for one scatterer (paper Section 2.2: AIM fill).  Host FP64
+ * setup: RWG functions, stencil anchors a = floor(c/h - (M-1)/2), moment-
+ * matching weights on (M+1)^3 grid nodes, near list |c_m - c_n| <= near_radius
+ * and near entries (symmetrised MoM entry minus its grid approximation).
+ * Device: grid Green's function spectrum on the zero-padded grid (padded
+ * length per axis = smallest 2,3,5-smooth integer >= 2n-1), kept resident.
+ *   k > 0, h > 0, M in {1, 2, 3}, near_radius >= 0.  Synchronises.
+ * Returns AIM_EINVAL for a non-manifold or degenerate mesh, a mesh without
+ * interior edges, or a grid whose padded size exceeds 2^31 points.
+ */
+int aim_setup(const aim_mesh* mesh, double k, double h, int M, double near_radius,
+              const aim_opts* opts, aim_ctx** out);
+
+void aim_destroy(aim_ctx* ctx); /* frees everything; NULL is a no-op; synchronises */
+
+int aim_set_stream(aim_ctx* ctx, void* stream);
+
+/* N (number of unknowns). */
+int aim_num_unknowns(const aim_ctx* ctx, int64_t* N);
+
+/* Grid extents n[3] and padded extents L[3] (x, y, z), near-list nnz. */
+int aim_grid_info(const aim_ctx* ctx, int32_t n[3], int32_t L[3], int64_t* nnz_near);
+
+/*
+ * Plane-wave right-hand sides V_m = int f_m . pol exp(-j k khat . r) dS
+ * (paper Section 2.1 excitation), collapsed Gauss-Legendre 4x4 rule per
+ * triangle.  khat, pol: host [nrhs][3].  V_dev: device c128 [nrhs][N].
+ */
+int aim_rhs_planewave(aim_ctx* ctx, int nrhs, const double* khat, const double* pol, void* V_dev);
+
+/*
+ * y = Z~ x: one AIM product for nrhs vectors (paper Section 4.1: projection,
+ * pruned FFT convolution on the doubled grid, interpolation, near
+ * correction).  precision AIM_C128: x_dev, y_dev c128 [nrhs][N], FP64
+ * throughout.  AIM_C64: x_dev, y_dev c64 [nrhs][N], FP32 weights, spectrum,
+ * near entries and accumulation.  1 <= nrhs <= opts.max_rhs.  x and y must
+ * not overlap.  Enqueued on the context stream; does not synchronise.
+ */
+int aim_matvec(aim_ctx* ctx, const void* x_dev, void* y_dev, int nrhs, int precision);
+
+/*
+ * Same product with HOST buffers (x_host, y_host as in aim_matvec): copies x
+ * to the device, runs the product and copies y back; synchronises.
+ */
+int aim_matvec_host(aim_ctx* ctx, const void* x_host, void* y_host, int nrhs, int precision);
+
+/*
+ * Solve Z~ X = V for nrhs right-hand sides (paper Section 2.2: diagonal
+ * preconditioner, stop on the relative residual).  Right-preconditioned
+ * restarted GMRES(m), M^-1 = diag(Z~)^-1, classical Gram-Schmidt with one
+ * re-orthogonalisation, FP64 dot products and Givens rotations on the
+ * device.  The Arnoldi products use opts.precision; every restart computes
+ * the true residual with the FP64 product, so AIM_C64 is FP64 iterative
+ * refinement around a complex64 inner solve.  Stops when every right-hand
+ * side has ||V - Z~ X|| / ||V|| <= tol (true residual) or after opts.maxit
+ * steps (AIM_ENOCONV).  V_dev, X_dev: device c128 [nrhs][N]; X is
+ * overwritten (initial guess 0).  info may be NULL.  Synchronises.
+ */
+int aim_solve(aim_ctx* ctx, const void* V_dev, void* X_dev, int nrhs, double tol, aim_solve_info* info);
+
+/*
+ * Bistatic RCS of solved currents (paper eq. 1 ingredients):
+ * sigma_tt = k^2 eta^2 / (4 pi) |theta . N|^2, sigma_pp likewise with phi,
+ * N(rhat) = sum_m x_m int f_m exp(+j k rhat . r) dS (collapsed 3x3 rule).
+ * theta, phi: host [ndir]; sig_tt, sig_pp: host [nrhs][ndir] (sig_pp may be
+ * NULL).  X_dev: device c128 [nrhs][N].  Synchronises.
+ */
+int aim_rcs(aim_ctx* ctx, const void* X_dev, int nrhs, int ndir, const double* theta,
+            const double* phi, double* sig_tt, double* sig_pp);
+
+/* Bytes of device memory a context for this mesh would hold (estimate, +-10 %). */
+int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int max_rhs, size_t* bytes);
+
+/*
+ * Copy internal setup arrays to host memory for inspection and testing.
+ * what: AIM_EXPORT_ANCHORS int32 [N][3] (absolute node index),
+ *       AIM_EXPORT_WEIGHTS f64 [N][4][(M+1)^3],
+ *       AIM_EXPORT_NEAR_PTR int32 [N+1], AIM_EXPORT_NEAR_COL int32 [nnz],
+ *       AIM_EXPORT_NEAR_VAL c128 [nnz], AIM_EXPORT_DIAG c128 [N],
+ *       AIM_EXPORT_GHAT c128 octant [Lz/2+1][Ly/2+1][Lx/2+1] (scaled by 1/(Lx Ly Lz)),
+ *       AIM_EXPORT_PROJ_PTR int32 [nx*ny*nz + 1] (per grid node, offsets into
+ *       the node-ordered projection entries; the last value is their count).
+ * bytes must equal the array size exactly.  Synchronises.
+ */
+enum {
+  AIM_EXPORT_ANCHORS = 1,
+  AIM_EXPORT_WEIGHTS = 2,
+  AIM_EXPORT_NEAR_PTR = 3,
+  AIM_EXPORT_NEAR_COL = 4,
+  AIM_EXPORT_NEAR_VAL = 5,
+  AIM_EXPORT_DIAG = 6,
+  AIM_EXPORT_GHAT = 7,
+  AIM_EXPORT_PROJ_PTR = 8
+};
+int aim_export(aim_ctx* ctx, int what, void* host_dst, size_t bytes);
+
+/*
+ * Kernel launches the library has issued from this context so far (all
+ * entry points).  Lets a caller count launches inside a timed region.
+ */
+int aim_launch_count(const aim_ctx* ctx, int64_t* count);
+
+/*
+ * Per-kernel device timing of this context.  mode 1: from now on every kernel
+ * launch is bracketed by two CUDA events on the context stream; mode 0: stop;
+ * mode 2: clear the totals.  aim_profile_read synchronises the stream, then
+ * reports for up to max_kernels kernel names (48-byte NUL-terminated slots in
+ * names) the number of profiled launches and their total device time in ms;
+ * *count receives the number of distinct names.
+ */
+int aim_profile(aim_ctx* ctx, int mode);
+int aim_profile_read(aim_ctx* ctx, int max_kernels, char* names, int64_t* launches, double* ms, int* count);
+
+/*
+ * Measure the device's FP64 (which = 64) or FP32 (which = 32) FMA throughput
+ * in TFLOP/s with a register-resident FMA loop on the current device.
+ * Synchronises.
+ */
+int aim_probe_fma_peak(int which, double* tflops);
+
+const char* aim_strerror(int code);
+const char* aim_last_error(void); /* thread-local detail of the last failure */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AIM_H */

@@ -1,0 +1,320 @@
+// C ABI entry points (include/aim.h): argument checks, context lifetime,
+// buffer management, dispatch to the setup, product, solver and RCS code.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "common.h"
+
+namespace aim {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+template <typename R> static int ensure_buffers(aim_ctx* c, PrecData<R>& p) {
+  if (p.grid0) return AIM_OK;
+  const long long B = c->max_rhs;
+  const long long nx = c->n[0], ny = c->n[1], nz = c->n[2], Ly = c->L[1], Lz = c->L[2];
+  const size_t e = sizeof(cplx<R>);
+  AIM_CUDA_TRY(cudaMalloc(&p.grid0, e * B * 4 * nz * ny * nx));
+  AIM_CUDA_TRY(cudaMalloc(&p.grid1, e * B * 4 * Lz * ny * nx));
+  AIM_CUDA_TRY(cudaMalloc(&p.grid2, e * B * 4 * Lz * Ly * nx));
+  AIM_CUDA_TRY(cudaMalloc(&p.xbuf, e * B * c->N));
+  AIM_CUDA_TRY(cudaMalloc(&p.ybuf, e * B * c->N));
+  return AIM_OK;
+}
+
+template <typename R> static void free_prec(PrecData<R>& p) {
+  cudaFree(p.lam); cudaFree(p.pnode_w); cudaFree(p.ghat); cudaFree(p.near_val);
+  for (int d = 0; d < 3; ++d) cudaFree(p.tw[d]);
+  cudaFree(p.grid0); cudaFree(p.grid1); cudaFree(p.grid2); cudaFree(p.xbuf); cudaFree(p.ybuf);
+  p = PrecData<R>{};
+}
+
+static void free_ctx(aim_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  free_prec(c->p64);
+  free_prec(c->p32);
+  free_krylov(c);
+  profile_free(c);
+  cudaFree(c->base); cudaFree(c->near_ptr); cudaFree(c->near_col); cudaFree(c->pnode_ptr); cudaFree(c->pnode_m);
+  cudaFree(c->diag); cudaFree(c->dinv64); cudaFree(c->d_verts); cudaFree(c->d_tris); cudaFree(c->rwg_tri);
+  cudaFree(c->rwg_free); cudaFree(c->rwg_len); cudaFree(c->tri_area);
+  delete c;
+}
+
+static int check_ctx(const aim_ctx* c) {
+  if (!c) {
+    set_error("null context");
+    return AIM_EINVAL;
+  }
+  return AIM_OK;
+}
+
+static int check_device() {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    set_error(std::string("no CUDA device: ") + cudaGetErrorString(e));
+    return AIM_ENODEV;
+  }
+  return AIM_OK;
+}
+
+}  // namespace aim
+
+using namespace aim;
+
+extern "C" {
+
+const char* aim_last_error(void) { return g_last_error.c_str(); }
+
+const char* aim_strerror(int code) {
+  switch (code) {
+    case AIM_OK: return "ok";
+    case AIM_EINVAL: return "invalid argument";
+    case AIM_ENOMEM: return "out of memory";
+    case AIM_ECUDA: return "CUDA error";
+    case AIM_ENOCONV: return "solver did not converge";
+    case AIM_ETIMEOUT: return "device wait timed out";
+    case AIM_ENODEV: return "no CUDA device";
+    default: return "unknown error";
+  }
+}
+
+void aim_default_opts(aim_opts* o) {
+  if (!o) return;
+  o->precision = AIM_C128;
+  o->restart = 50;
+  o->maxit = 3000;
+  o->check_every = 5;
+  o->max_rhs = 1;
+  o->verbose = 0;
+  o->stream = nullptr;
+}
+
+int aim_setup(const aim_mesh* mesh, double k, double h, int M, double near_radius, const aim_opts* opts,
+              aim_ctx** out) {
+  if (!out) {
+    set_error("aim_setup: out is NULL");
+    return AIM_EINVAL;
+  }
+  *out = nullptr;
+  if (!(k > 0.0) || !(h > 0.0) || M < 1 || M > 3 || !(near_radius >= 0.0)) {
+    set_error("aim_setup: need k > 0, h > 0, 1 <= M <= 3, near_radius >= 0");
+    return AIM_EINVAL;
+  }
+  aim_opts o;
+  aim_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.precision != AIM_C64 && o.precision != AIM_C128) {
+    set_error("aim_setup: precision must be AIM_C64 or AIM_C128");
+    return AIM_EINVAL;
+  }
+  if (o.restart < 1 || o.restart > 200 || o.max_rhs < 1 || o.max_rhs > 256 || o.maxit < 1 || o.check_every < 1) {
+    set_error("aim_setup: restart in 1..200, max_rhs in 1..256, maxit >= 1, check_every >= 1");
+    return AIM_EINVAL;
+  }
+  AIM_TRY(check_device());
+  aim_ctx* c = new (std::nothrow) aim_ctx();
+  if (!c) return AIM_ENOMEM;
+  c->k = k;
+  c->h = h;
+  c->M = M;
+  c->radius = near_radius;
+  c->opts = o;
+  c->max_rhs = o.max_rhs;
+  c->stream = (cudaStream_t)o.stream;
+  cudaGetDevice(&c->device);
+  int rc = AIM_OK;
+  try {
+    rc = build_context(c, mesh);
+  } catch (const std::bad_alloc&) {
+    set_error("aim_setup: host allocation failed");
+    rc = AIM_ENOMEM;
+  }
+  if (rc == AIM_OK) rc = ensure_buffers(c, c->p64);
+  if (rc == AIM_OK) rc = ensure_buffers(c, c->p32);
+  if (rc == AIM_OK) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      set_error(std::string("aim_setup: ") + cudaGetErrorString(e));
+      rc = AIM_ECUDA;
+    }
+  }
+  if (rc != AIM_OK) {
+    if (rc == AIM_ECUDA && cudaGetLastError() == cudaErrorMemoryAllocation) rc = AIM_ENOMEM;
+    free_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return AIM_OK;
+}
+
+void aim_destroy(aim_ctx* ctx) { free_ctx(ctx); }
+
+int aim_set_stream(aim_ctx* ctx, void* stream) {
+  AIM_TRY(check_ctx(ctx));
+  ctx->stream = (cudaStream_t)stream;
+  return AIM_OK;
+}
+
+int aim_num_unknowns(const aim_ctx* ctx, int64_t* N) {
+  AIM_TRY(check_ctx(ctx));
+  if (!N) return AIM_EINVAL;
+  *N = ctx->N;
+  return AIM_OK;
+}
+
+int aim_grid_info(const aim_ctx* ctx, int32_t n[3], int32_t L[3], int64_t* nnz) {
+  AIM_TRY(check_ctx(ctx));
+  for (int d = 0; d < 3; ++d) {
+    if (n) n[d] = ctx->n[d];
+    if (L) L[d] = ctx->L[d];
+  }
+  if (nnz) *nnz = ctx->nnz;
+  return AIM_OK;
+}
+
+int aim_rhs_planewave(aim_ctx* ctx, int nrhs, const double* khat, const double* pol, void* V_dev) {
+  AIM_TRY(check_ctx(ctx));
+  if (nrhs < 1 || !khat || !pol || !V_dev) {
+    set_error("aim_rhs_planewave: bad arguments");
+    return AIM_EINVAL;
+  }
+  return rhs_planewave(ctx, nrhs, khat, pol, (double2*)V_dev);
+}
+
+int aim_matvec(aim_ctx* ctx, const void* x_dev, void* y_dev, int nrhs, int precision) {
+  AIM_TRY(check_ctx(ctx));
+  if (nrhs < 1 || nrhs > ctx->max_rhs || !x_dev || !y_dev || x_dev == y_dev) {
+    set_error("aim_matvec: need 1 <= nrhs <= max_rhs and distinct non-null x, y");
+    return AIM_EINVAL;
+  }
+  if (precision == AIM_C128) return matvec<double>(ctx, (const double2*)x_dev, (double2*)y_dev, nrhs);
+  if (precision == AIM_C64) return matvec<float>(ctx, (const float2*)x_dev, (float2*)y_dev, nrhs);
+  set_error("aim_matvec: precision must be AIM_C64 or AIM_C128");
+  return AIM_EINVAL;
+}
+
+int aim_matvec_host(aim_ctx* ctx, const void* x_host, void* y_host, int nrhs, int precision) {
+  AIM_TRY(check_ctx(ctx));
+  if (nrhs < 1 || nrhs > ctx->max_rhs || !x_host || !y_host) {
+    set_error("aim_matvec_host: bad arguments");
+    return AIM_EINVAL;
+  }
+  if (precision != AIM_C128 && precision != AIM_C64) {
+    set_error("aim_matvec_host: precision must be AIM_C64 or AIM_C128");
+    return AIM_EINVAL;
+  }
+  const size_t bytes = (size_t)nrhs * ctx->N * (precision == AIM_C128 ? 16 : 8);
+  void* xd = precision == AIM_C128 ? (void*)ctx->p64.xbuf : (void*)ctx->p32.xbuf;
+  void* yd = precision == AIM_C128 ? (void*)ctx->p64.ybuf : (void*)ctx->p32.ybuf;
+  AIM_CUDA_TRY(cudaMemcpyAsync(xd, x_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  AIM_TRY(aim_matvec(ctx, xd, yd, nrhs, precision));
+  AIM_CUDA_TRY(cudaMemcpyAsync(y_host, yd, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  AIM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return AIM_OK;
+}
+
+int aim_solve(aim_ctx* ctx, const void* V_dev, void* X_dev, int nrhs, double tol, aim_solve_info* info) {
+  AIM_TRY(check_ctx(ctx));
+  if (nrhs < 1 || nrhs > ctx->max_rhs || !V_dev || !X_dev || V_dev == X_dev || !(tol > 0.0)) {
+    set_error("aim_solve: need 1 <= nrhs <= max_rhs, tol > 0, distinct non-null V, X");
+    return AIM_EINVAL;
+  }
+  return solve(ctx, (const double2*)V_dev, (double2*)X_dev, nrhs, tol, info);
+}
+
+int aim_rcs(aim_ctx* ctx, const void* X_dev, int nrhs, int ndir, const double* theta, const double* phi,
+            double* sig_tt, double* sig_pp) {
+  AIM_TRY(check_ctx(ctx));
+  if (nrhs < 1 || ndir < 1 || !X_dev || !theta || !phi || !sig_tt) {
+    set_error("aim_rcs: bad arguments");
+    return AIM_EINVAL;
+  }
+  return rcs(ctx, (const double2*)X_dev, nrhs, ndir, theta, phi, sig_tt, sig_pp);
+}
+
+int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int max_rhs, size_t* bytes) {
+  if (!mesh || !bytes || !(h > 0.0) || M < 1 || M > 3 || max_rhs < 1) {
+    set_error("aim_footprint: bad arguments");
+    return AIM_EINVAL;
+  }
+  // grid box from the vertices' bounding box, basis count from the edge count
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < mesh->nv; ++i)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], mesh->verts[3 * i + d]);
+      hi[d] = std::max(hi[d], mesh->verts[3 * i + d]);
+    }
+  long long n[3], L[3];
+  for (int d = 0; d < 3; ++d) {
+    n[d] = (long long)std::floor(hi[d] / h) - (long long)std::floor(lo[d] / h) + M + 1;
+    long long m = 2 * n[d] - 1, x;
+    for (L[d] = m;; ++L[d]) {
+      x = L[d];
+      for (int p : {2, 3, 5})
+        while (x % p == 0) x /= p;
+      if (x == 1) break;
+    }
+  }
+  const long long N = (long long)(1.5 * mesh->nt);  // interior edges of a closed surface
+  const long long S = (long long)(M + 1) * (M + 1) * (M + 1);
+  const long long nnz = N * 100LL;  // generous near-row length
+  const long long nc = n[0] * n[1] * n[2];
+  double b = 0;
+  b += (double)N * 4 * S * (8 + 4) * 2;                               // weights f64/f32 + node lists
+  b += (double)nnz * (16 + 8 + 4);                                     // near values + columns
+  b += (double)(L[0] / 2 + 1) * (L[1] / 2 + 1) * (L[2] / 2 + 1) * 24; // spectra
+  b += (double)L[0] * L[1] * L[2] * 32;                                // setup transform scratch
+  b += (double)max_rhs * 4 * (nc + L[2] * n[1] * n[0] + L[2] * L[1] * n[0]) * 24;  // grids, both precisions
+  b += (double)max_rhs * N * (16 * 53 + 48);                           // Krylov basis (m = 50) and vectors
+  *bytes = (size_t)b;
+  return AIM_OK;
+}
+
+int aim_export(aim_ctx* c, int what, void* dst, size_t bytes) {
+  AIM_TRY(check_ctx(c));
+  const void* src = nullptr;
+  size_t need = 0;
+  switch (what) {
+    case AIM_EXPORT_ANCHORS: src = c->h_anchor.data(); need = c->h_anchor.size() * 4; break;
+    case AIM_EXPORT_WEIGHTS: src = c->h_lam.data(); need = c->h_lam.size() * 8; break;
+    case AIM_EXPORT_NEAR_PTR: src = c->h_near_ptr.data(); need = c->h_near_ptr.size() * 4; break;
+    case AIM_EXPORT_NEAR_COL: src = c->h_near_col.data(); need = c->h_near_col.size() * 4; break;
+    case AIM_EXPORT_NEAR_VAL: src = c->h_near_val.data(); need = c->h_near_val.size() * 8; break;
+    case AIM_EXPORT_DIAG: src = c->h_diag.data(); need = c->h_diag.size() * 8; break;
+    case AIM_EXPORT_GHAT: src = c->h_ghat.data(); need = c->h_ghat.size() * 8; break;
+    case AIM_EXPORT_PROJ_PTR: src = c->h_pnode_ptr.data(); need = c->h_pnode_ptr.size() * 4; break;
+    default: set_error("aim_export: unknown array"); return AIM_EINVAL;
+  }
+  if (!dst || bytes != need) {
+    set_error("aim_export: size mismatch, need " + std::to_string(need) + " bytes");
+    return AIM_EINVAL;
+  }
+  std::memcpy(dst, src, need);
+  return AIM_OK;
+}
+
+int aim_launch_count(const aim_ctx* ctx, int64_t* count) {
+  AIM_TRY(check_ctx(ctx));
+  if (!count) return AIM_EINVAL;
+  *count = ctx->launches;
+  return AIM_OK;
+}
+
+int aim_probe_fma_peak(int which, double* tflops) {
+  if (!tflops || (which != 32 && which != 64)) {
+    set_error("aim_probe_fma_peak: which must be 32 or 64");
+    return AIM_EINVAL;
+  }
+  AIM_TRY(check_device());
+  return probe_fma(which, tflops);
+}
+
+}  // extern "C"

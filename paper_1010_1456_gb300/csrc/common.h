@@ -1,0 +1,207 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/aim.h"
+
+#define AIM_HD __host__ __device__
+
+namespace aim {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+
+struct Status {
+  int code = AIM_OK;
+};
+
+#define AIM_CUDA_TRY(expr)                                                              \
+  do {                                                                                  \
+    cudaError_t _e = (expr);                                                            \
+    if (_e != cudaSuccess) {                                                            \
+      ::aim::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));             \
+      return AIM_ECUDA;                                                                 \
+    }                                                                                   \
+  } while (0)
+
+#define AIM_TRY(expr)              \
+  do {                             \
+    int _c = (expr);               \
+    if (_c != AIM_OK) return _c;   \
+  } while (0)
+
+// ---------------------------------------------------------------- complex
+template <typename R> struct cplx_t;
+template <> struct cplx_t<float> { using type = float2; };
+template <> struct cplx_t<double> { using type = double2; };
+template <typename R> using cplx = typename cplx_t<R>::type;
+
+template <typename C> AIM_HD inline C cmake(double re, double im) {
+  C c;
+  c.x = (decltype(c.x))re;
+  c.y = (decltype(c.y))im;
+  return c;
+}
+template <typename C> AIM_HD inline C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> AIM_HD inline C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> AIM_HD inline C cmul(C a, C b) {
+  C c;
+  c.x = a.x * b.x - a.y * b.y;
+  c.y = a.x * b.y + a.y * b.x;
+  return c;
+}
+template <typename C, typename R> AIM_HD inline C cscale(C a, R s) { a.x *= s; a.y *= s; return a; }
+template <typename C> AIM_HD inline C cconj(C a) { a.y = -a.y; return a; }
+
+// ---------------------------------------------------------------- plans
+constexpr int kMaxStages = 16;
+struct FftPlan {
+  int L;                 // transform length
+  int nst;               // number of stages
+  int radix[kMaxStages]; // radix per stage, applied in order
+};
+FftPlan make_plan(int L);  // radices from {4, 3, 5, 2}; L must be 2,3,5-smooth
+
+// ---------------------------------------------------------------- per-precision device data
+template <typename R> struct PrecData {
+  R* lam = nullptr;               // [N][4][S] moment weights
+  R* pnode_w = nullptr;           // [nent][4] projection weights, node-ordered
+  cplx<R>* ghat = nullptr;        // octant [Lz/2+1][Ly/2+1][Lx/2+1], scaled by 1/(LxLyLz)
+  cplx<R>* near_val = nullptr;    // [nnz]
+  cplx<R>* tw[3] = {nullptr, nullptr, nullptr};  // forward twiddles exp(-2 pi i t / L_d)
+  cplx<R>* grid0 = nullptr;       // [B][4][nz][ny][nx]  Q, then Phi
+  cplx<R>* grid1 = nullptr;       // [B][4][Lz][ny][nx]
+  cplx<R>* grid2 = nullptr;       // [B][4][Lz][Ly][nx]
+  cplx<R>* xbuf = nullptr;        // [B][N] staging for host/solver conversions
+  cplx<R>* ybuf = nullptr;        // [B][N]
+};
+
+// Per-kernel timing with CUDA events on the context stream (aim_profile).
+struct ProfEvent {
+  const char* name;
+  cudaEvent_t a, b;
+};
+struct Profiler {
+  bool on = false;
+  std::vector<ProfEvent> pending;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::string> names;
+  std::vector<double> ms;
+  std::vector<int64_t> count;
+};
+
+struct KrylovWork {
+  double2* V = nullptr;      // [B][m+1][N] Arnoldi basis
+  double2* w = nullptr;      // [B][N]
+  double2* r = nullptr;      // [B][N]
+  double2* H = nullptr;      // [B][m+1][m]
+  double2* hcol = nullptr;   // [B][m+1] current column (dot results)
+  double2* partial = nullptr;// [B][nblk][m+1] partial dots
+  double2* cs = nullptr;     // [B][m]
+  double2* sn = nullptr;     // [B][m]
+  double2* g = nullptr;      // [B][m+1]
+  double2* y = nullptr;      // [B][m]
+  double* nrm = nullptr;     // [B]
+  double* bnorm = nullptr;   // [B]
+  double* h_est = nullptr;   // pinned host [B] residual estimates
+  int* active = nullptr;     // [B]
+  int m = 0;
+  int nblk = 0;
+};
+
+}  // namespace aim
+
+struct aim_ctx {
+  // problem
+  int N = 0, M = 2, S = 27;
+  double k = 0, h = 0, radius = 0;
+  int lo[3] = {0, 0, 0};
+  int n[3] = {0, 0, 0};  // grid nodes x, y, z
+  int L[3] = {0, 0, 0};  // padded
+  int64_t nnz = 0;
+  int64_t nent = 0;      // projection entries
+  aim_opts opts;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int64_t launches = 0;
+  aim::FftPlan plan[3];
+
+  // host copies (inspection, RHS/RCS geometry)
+  std::vector<int32_t> h_anchor;  // [N][3] absolute
+  std::vector<double> h_lam;      // [N][4][S]
+  std::vector<int32_t> h_near_ptr, h_near_col;
+  std::vector<double> h_near_val; // [nnz][2]
+  std::vector<double> h_diag;     // [N][2]
+  std::vector<double> h_ghat;     // octant [..][2]
+  std::vector<int32_t> h_pnode_ptr;  // [Nc+1]
+
+  // device, precision independent
+  int32_t* base = nullptr;        // [N] flat index of the stencil's first node
+  int32_t* near_ptr = nullptr;    // [N+1]
+  int32_t* near_col = nullptr;    // [nnz]
+  int32_t* pnode_ptr = nullptr;   // [Nc+1]
+  int32_t* pnode_m = nullptr;     // [nent]
+  double2* diag = nullptr;        // [N] diag(Z~) FP64
+  double2* dinv64 = nullptr;      // [N] 1/diag
+  // RWG geometry on device (for RHS and far field)
+  double* d_verts = nullptr;      // [nv][3]
+  int32_t* d_tris = nullptr;      // [nt][3]
+  int32_t* rwg_tri = nullptr;     // [N][2] (T+, T-)
+  int32_t* rwg_free = nullptr;    // [N][2] free vertex of T+, T-
+  double* rwg_len = nullptr;      // [N]
+  double* tri_area = nullptr;     // [nt]
+  int nv = 0, nt = 0;
+
+  aim::PrecData<double> p64;
+  aim::PrecData<float> p32;
+  aim::KrylovWork kw;
+  aim::Profiler prof;
+  int max_rhs = 1;
+};
+
+namespace aim {
+// Brackets one kernel launch with profiling events when profiling is on and
+// counts the launch.
+struct LaunchScope {
+  aim_ctx* c;
+  bool on;
+  cudaEvent_t b = nullptr;
+  const char* name;
+  LaunchScope(aim_ctx* ctx, const char* nm);
+  ~LaunchScope();
+};
+#define AIM_LAUNCH(ctx, name, ...)        \
+  do {                                    \
+    ::aim::LaunchScope _ls((ctx), (name)); \
+    __VA_ARGS__;                          \
+  } while (0)
+int profile_collect(aim_ctx* c);
+void profile_free(aim_ctx* c);
+// setup.cu
+int build_context(aim_ctx* c, const aim_mesh* mesh);
+// matvec.cu
+template <typename R> int matvec(aim_ctx* c, const cplx<R>* x, cplx<R>* y, int nrhs);
+int launch_check(aim_ctx* c, const char* what);
+int convert_c128_to_c64(aim_ctx* c, const double2* in, float2* out, int64_t count);
+int convert_c64_to_c128(aim_ctx* c, const float2* in, double2* out, int64_t count);
+// fft.cu
+template <typename R>
+int fft_convolve(aim_ctx* c, PrecData<R>& p, int G);  // grid0 (Q) -> grid0 (Phi), G = 4 * nrhs grids
+int build_ghat(aim_ctx* c);
+// krylov.cu
+int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_solve_info* info);
+int alloc_krylov(aim_ctx* c);
+void free_krylov(aim_ctx* c);
+// rcs.cu
+int rhs_planewave(aim_ctx* c, int nrhs, const double* khat, const double* pol, double2* V);
+int rcs(aim_ctx* c, const double2* X, int nrhs, int ndir, const double* theta, const double* phi,
+        double* sig_tt, double* sig_pp);
+// probe.cu
+int probe_fma(int which, double* tflops);
+}  // namespace aim

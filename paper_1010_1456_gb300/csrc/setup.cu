@@ -1,0 +1,591 @@
+// Context setup (paper Section 2.2 "matrix fill" for AIM, Section 2.4: O(N)).
+//
+// Host FP64, multi-threaded:
+//   1. RWG functions of the interior edges (sorted by (low, high) vertex;
+//      "+" triangle = lower index);
+//   2. stencil anchors a = floor(c/h - (M-1)/2) per axis, grid box, padded
+//      extents (smallest 2,3,5-smooth L >= 2n-1);
+//   3. moment-matching weights in their tensor-product Lagrange form,
+//      Lambda^c_m(i,j,k) = int g^c_m l_i(xi) l_j(upsilon) l_k(zeta) dS, with
+//      g = f_x, f_y, f_z, div f and a collapsed Gauss-Legendre rule exact for
+//      the integrand degree 3M+1 (this solves the moment-matching system:
+//      the Lagrange basis reproduces every monomial of per-axis degree <= M);
+//   4. near list |c_m - c_n| <= r (cell hashing; d2 = (dx dx + dy dy) + dz dz
+//      <= r r in FP64, self pairs included), CSR with sorted columns;
+//   5. near entries: symmetrised EFIE Galerkin entry minus the entry's grid
+//      approximation, computed per test triangle from triangle-pair blocks;
+//   6. node-ordered projection lists (the transpose of the weights).
+// Device: uploads, twiddles and the Green's function spectrum (fft.cu).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <thread>
+
+#include "common.h"
+#include "geom.h"
+
+namespace aim {
+
+// ------------------------------------------------------------------ threads
+template <typename F> static void parallel_for(int64_t n, F f, int64_t grain = 64) {
+  unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+  if (n <= grain || nt == 1) {
+    for (int64_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int64_t> next(0);
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t)
+    th.emplace_back([&]() {
+      for (;;) {
+        int64_t s = next.fetch_add(grain);
+        if (s >= n) break;
+        int64_t e = std::min(n, s + grain);
+        for (int64_t i = s; i < e; ++i) f(i);
+      }
+    });
+  for (auto& t : th) t.join();
+}
+
+static int smooth_length(int m) {
+  for (int L = std::max(m, 1);; ++L) {
+    int x = L;
+    for (int p : {2, 3, 5})
+      while (x % p == 0) x /= p;
+    if (x == 1) return L;
+  }
+}
+
+// ------------------------------------------------------------------ topology
+struct Topo {
+  int N = 0, nv = 0, nt = 0;
+  std::vector<V3> vert;
+  std::vector<int32_t> tri;  // [nt][3]
+  std::vector<double> area;  // [nt]
+  std::vector<int32_t> e0, e1, tp, tm, fp, fm, sp, sm;
+  std::vector<double> len;
+  std::vector<V3> cen;
+  std::vector<int32_t> tri_rwg;  // [nt][3]: RWG whose free vertex is slot s of the triangle, or -1
+};
+
+static int build_topology(const aim_mesh* mesh, Topo& T) {
+  if (!mesh || mesh->nv <= 0 || mesh->nt <= 0 || !mesh->verts || !mesh->tris) {
+    set_error("aim_setup: empty mesh");
+    return AIM_EINVAL;
+  }
+  T.nv = mesh->nv;
+  T.nt = mesh->nt;
+  T.vert.resize(T.nv);
+  for (int i = 0; i < T.nv; ++i) T.vert[i] = v3(mesh->verts[3 * i], mesh->verts[3 * i + 1], mesh->verts[3 * i + 2]);
+  T.tri.assign(mesh->tris, mesh->tris + 3 * (size_t)T.nt);
+  T.area.resize(T.nt);
+  for (int t = 0; t < T.nt; ++t) {
+    int a = T.tri[3 * t], b = T.tri[3 * t + 1], c = T.tri[3 * t + 2];
+    if (a < 0 || b < 0 || c < 0 || a >= T.nv || b >= T.nv || c >= T.nv || a == b || b == c || a == c) {
+      set_error("aim_setup: triangle " + std::to_string(t) + " has a bad vertex index");
+      return AIM_EINVAL;
+    }
+    V3 cr = cross(T.vert[b] - T.vert[a], T.vert[c] - T.vert[a]);
+    T.area[t] = 0.5 * norm(cr);
+    if (!(T.area[t] > 0.0)) {
+      set_error("aim_setup: triangle " + std::to_string(t) + " is degenerate");
+      return AIM_EINVAL;
+    }
+  }
+  struct E {
+    int32_t a, b, t, slot;
+  };
+  std::vector<E> ed;
+  ed.reserve(3 * (size_t)T.nt);
+  for (int t = 0; t < T.nt; ++t)
+    for (int k = 0; k < 3; ++k) {
+      int u = T.tri[3 * t + k], v = T.tri[3 * t + (k + 1) % 3];
+      ed.push_back(E{std::min(u, v), std::max(u, v), t, (k + 2) % 3});
+    }
+  std::sort(ed.begin(), ed.end(), [](const E& x, const E& y) {
+    if (x.a != y.a) return x.a < y.a;
+    if (x.b != y.b) return x.b < y.b;
+    return x.t < y.t;
+  });
+  T.tri_rwg.assign(3 * (size_t)T.nt, -1);
+  for (size_t i = 0; i < ed.size();) {
+    size_t j = i;
+    while (j < ed.size() && ed[j].a == ed[i].a && ed[j].b == ed[i].b) ++j;
+    if (j - i > 2) {
+      set_error("aim_setup: non-manifold edge (" + std::to_string(ed[i].a) + "," + std::to_string(ed[i].b) + ")");
+      return AIM_EINVAL;
+    }
+    if (j - i == 2) {
+      const E& p = ed[i];
+      const E& q = ed[i + 1];
+      int m = (int)T.e0.size();
+      T.e0.push_back(p.a);
+      T.e1.push_back(p.b);
+      T.tp.push_back(p.t);
+      T.tm.push_back(q.t);
+      T.sp.push_back(p.slot);
+      T.sm.push_back(q.slot);
+      T.fp.push_back(T.tri[3 * p.t + p.slot]);
+      T.fm.push_back(T.tri[3 * q.t + q.slot]);
+      T.tri_rwg[3 * p.t + p.slot] = m;
+      T.tri_rwg[3 * q.t + q.slot] = m;
+    }
+    i = j;
+  }
+  T.N = (int)T.e0.size();
+  if (T.N == 0) {
+    set_error("aim_setup: mesh has no interior edges");
+    return AIM_EINVAL;
+  }
+  T.len.resize(T.N);
+  T.cen.resize(T.N);
+  for (int m = 0; m < T.N; ++m) {
+    V3 a = T.vert[T.e0[m]], b = T.vert[T.e1[m]];
+    T.len[m] = norm(b - a);
+    T.cen[m] = v3((a.x + b.x) * 0.5, (a.y + b.y) * 0.5, (a.z + b.z) * 0.5);
+  }
+  return AIM_OK;
+}
+
+// near list by cell hashing; rows sorted by column
+static void near_list(const Topo& T, double r, std::vector<int32_t>& ptr, std::vector<int32_t>& col) {
+  const int N = T.N;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int m = 0; m < N; ++m) {
+    const double c[3] = {T.cen[m].x, T.cen[m].y, T.cen[m].z};
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], c[d]);
+      hi[d] = std::max(hi[d], c[d]);
+    }
+  }
+  double cs = r;
+  for (int d = 0; d < 3; ++d) cs = std::max(cs, (hi[d] - lo[d]) / 256.0);
+  if (!(cs > 0.0)) cs = 1.0;
+  int nc[3];
+  for (int d = 0; d < 3; ++d) nc[d] = (int)((hi[d] - lo[d]) / cs) + 1;
+  auto cell_of = [&](const V3& c, int* ci) {
+    const double v[3] = {c.x, c.y, c.z};
+    for (int d = 0; d < 3; ++d) ci[d] = std::min(nc[d] - 1, std::max(0, (int)((v[d] - lo[d]) / cs)));
+  };
+  const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+  std::vector<int32_t> cstart(ncell + 1, 0), items(N);
+  std::vector<int64_t> cid(N);
+  for (int m = 0; m < N; ++m) {
+    int ci[3];
+    cell_of(T.cen[m], ci);
+    cid[m] = ((int64_t)ci[2] * nc[1] + ci[1]) * nc[0] + ci[0];
+    cstart[cid[m] + 1]++;
+  }
+  for (int64_t i = 0; i < ncell; ++i) cstart[i + 1] += cstart[i];
+  {
+    std::vector<int32_t> fill(cstart.begin(), cstart.end() - 1);
+    for (int m = 0; m < N; ++m) items[fill[cid[m]]++] = m;
+  }
+  const double r2 = r * r;
+  auto visit = [&](int m, auto&& emit) {
+    int ci[3];
+    cell_of(T.cen[m], ci);
+    const int span = (r <= cs) ? 1 : (int)std::ceil(r / cs);
+    for (int z = std::max(0, ci[2] - span); z <= std::min(nc[2] - 1, ci[2] + span); ++z)
+      for (int y = std::max(0, ci[1] - span); y <= std::min(nc[1] - 1, ci[1] + span); ++y)
+        for (int x = std::max(0, ci[0] - span); x <= std::min(nc[0] - 1, ci[0] + span); ++x) {
+          int64_t cc = ((int64_t)z * nc[1] + y) * nc[0] + x;
+          for (int32_t e = cstart[cc]; e < cstart[cc + 1]; ++e) {
+            int n = items[e];
+            double dx = T.cen[m].x - T.cen[n].x, dy = T.cen[m].y - T.cen[n].y, dz = T.cen[m].z - T.cen[n].z;
+            double d2 = (dx * dx + dy * dy) + dz * dz;
+            if (d2 <= r2) emit(n);
+          }
+        }
+  };
+  std::vector<int32_t> cnt(N, 0);
+  parallel_for(N, [&](int64_t m) {
+    int c = 0;
+    visit((int)m, [&](int) { ++c; });
+    cnt[m] = c;
+  });
+  ptr.assign(N + 1, 0);
+  for (int m = 0; m < N; ++m) ptr[m + 1] = ptr[m] + cnt[m];
+  col.resize(ptr[N]);
+  parallel_for(N, [&](int64_t m) {
+    int32_t* out = &col[ptr[m]];
+    int c = 0;
+    visit((int)m, [&](int n) { out[c++] = n; });
+    std::sort(out, out + c);
+  });
+}
+
+// ------------------------------------------------------------------ setup
+static int upload(void** dst, const void* src, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  AIM_CUDA_TRY(cudaMalloc(dst, bytes));
+  if (src) AIM_CUDA_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+  return AIM_OK;
+}
+template <typename T> static int up(T** dst, const std::vector<T>& v) {
+  return upload(reinterpret_cast<void**>(dst), v.data(), v.size() * sizeof(T));
+}
+
+int build_context(aim_ctx* c, const aim_mesh* mesh) {
+  Topo T;
+  AIM_TRY(build_topology(mesh, T));
+  const int N = T.N, M = c->M, P = M + 1, S = P * P * P;
+  c->N = N;
+  c->S = S;
+  c->nv = T.nv;
+  c->nt = T.nt;
+  const double h = c->h, k = c->k;
+
+  // ---- anchors and grid
+  c->h_anchor.resize(3 * (size_t)N);
+  int amin[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, amax[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+  for (int m = 0; m < N; ++m) {
+    const double cc[3] = {T.cen[m].x, T.cen[m].y, T.cen[m].z};
+    for (int d = 0; d < 3; ++d) {
+      double t = cc[d] / h;
+      double a = std::floor(t - 0.5 * (M - 1));
+      if (!(std::fabs(a) < 1e9)) {
+        set_error("aim_setup: grid index out of range (check h and the mesh)");
+        return AIM_EINVAL;
+      }
+      int ai = (int)a;
+      c->h_anchor[3 * (size_t)m + d] = ai;
+      amin[d] = std::min(amin[d], ai);
+      amax[d] = std::max(amax[d], ai);
+    }
+  }
+  long long Nc = 1, Lprod = 1;
+  for (int d = 0; d < 3; ++d) {
+    c->lo[d] = amin[d];
+    c->n[d] = amax[d] + M - amin[d] + 1;
+    c->L[d] = smooth_length(2 * c->n[d] - 1);
+    c->plan[d] = make_plan(c->L[d]);
+    Nc *= c->n[d];
+    Lprod *= c->L[d];
+  }
+  if (Nc >= (1LL << 31) || Lprod >= (1LL << 31) || c->L[1] > 900 || c->L[2] > 900 || c->L[0] > 4096) {
+    set_error("aim_setup: grid too large (padded " + std::to_string(c->L[0]) + "x" + std::to_string(c->L[1]) + "x" +
+              std::to_string(c->L[2]) + "; y and z must be <= 900)");
+    return AIM_EINVAL;
+  }
+
+  // ---- moment weights (Lagrange form)
+  const int nw = (3 * M + 4) / 2;
+  const TriRule rw = make_tri_rule(nw);
+  c->h_lam.assign((size_t)N * 4 * S, 0.0);
+  parallel_for(N, [&](int64_t mi) {
+    const int m = (int)mi;
+    double* lm = &c->h_lam[(size_t)m * 4 * S];
+    const double ax = c->h_anchor[3 * (size_t)m], ay = c->h_anchor[3 * (size_t)m + 1], az = c->h_anchor[3 * (size_t)m + 2];
+    for (int half = 0; half < 2; ++half) {
+      const int t = half ? T.tm[m] : T.tp[m];
+      const V3 fv = T.vert[half ? T.fm[m] : T.fp[m]];
+      const double sg = half ? -1.0 : 1.0, A = T.area[t];
+      const V3 r0 = T.vert[T.tri[3 * t]], r1 = T.vert[T.tri[3 * t + 1]], r2 = T.vert[T.tri[3 * t + 2]];
+      const double cf = sg * T.len[m] / (2.0 * A), dv = sg * T.len[m] / A;
+      for (int q = 0; q < rw.q; ++q) {
+        V3 r = tri_point(r0, r1, r2, rw.xi1[q], rw.xi2[q]);
+        const double wq = A * rw.w[q];
+        const double g[4] = {cf * (r.x - fv.x), cf * (r.y - fv.y), cf * (r.z - fv.z), dv};
+        const double xi = (r.x - h * ax) / h, up = (r.y - h * ay) / h, ze = (r.z - h * az) / h;
+        double lx[4], ly[4], lz[4];
+        for (int i = 0; i < P; ++i) {
+          lx[i] = lagrange(M, i, xi);
+          ly[i] = lagrange(M, i, up);
+          lz[i] = lagrange(M, i, ze);
+        }
+        for (int kk = 0; kk < P; ++kk)
+          for (int j = 0; j < P; ++j)
+            for (int i = 0; i < P; ++i) {
+              const int s = (kk * P + j) * P + i;
+              const double b = wq * lx[i] * ly[j] * lz[kk];
+              for (int cc = 0; cc < 4; ++cc) lm[cc * S + s] += b * g[cc];
+            }
+      }
+    }
+  });
+
+  // ---- near list
+  near_list(T, c->radius, c->h_near_ptr, c->h_near_col);
+  const int64_t nnz = c->h_near_ptr[N];
+  c->nnz = nnz;
+
+  // ---- near entries: triangle-pair blocks per test triangle
+  const TriRule rt = make_tri_rule(3), rts = make_tri_rule(5), rs = make_tri_rule(4);
+  std::vector<double> zhalf(4 * (size_t)nnz, 0.0);  // [2 halves][nnz][re, im]
+  const double jke = k * kEta0;
+  parallel_for(T.nt, [&](int64_t Pi) {
+    const int Pt = (int)Pi;
+    int ms[3], as[3], nm = 0;
+    for (int a = 0; a < 3; ++a) {
+      int m = T.tri_rwg[3 * (size_t)Pt + a];
+      if (m >= 0) {
+        ms[nm] = m;
+        as[nm] = a;
+        ++nm;
+      }
+    }
+    if (nm == 0) return;
+    std::vector<int32_t> Qs;
+    for (int i = 0; i < nm; ++i)
+      for (int32_t e = c->h_near_ptr[ms[i]]; e < c->h_near_ptr[ms[i] + 1]; ++e) {
+        int n = c->h_near_col[e];
+        Qs.push_back(T.tp[n]);
+        Qs.push_back(T.tm[n]);
+      }
+    std::sort(Qs.begin(), Qs.end());
+    Qs.erase(std::unique(Qs.begin(), Qs.end()), Qs.end());
+    std::vector<Cd> blk(Qs.size() * 9);
+    const V3 Pv[3] = {T.vert[T.tri[3 * Pt]], T.vert[T.tri[3 * Pt + 1]], T.vert[T.tri[3 * Pt + 2]]};
+    for (size_t qi = 0; qi < Qs.size(); ++qi) {
+      const int Qt = Qs[qi];
+      const V3 Qv[3] = {T.vert[T.tri[3 * Qt]], T.vert[T.tri[3 * Qt + 1]], T.vert[T.tri[3 * Qt + 2]]};
+      bool sing = false;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) sing |= (T.tri[3 * Pt + a] == T.tri[3 * Qt + b]);
+      Cd Tb[3][3];
+      pair_block(Pv, Qv, T.area[Pt], T.area[Qt], sing, k, sing ? rts : rt, rs, Tb);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) blk[qi * 9 + a * 3 + b] = Tb[a][b];
+    }
+    auto find = [&](int Qt) { return (size_t)(std::lower_bound(Qs.begin(), Qs.end(), Qt) - Qs.begin()); };
+    for (int i = 0; i < nm; ++i) {
+      const int m = ms[i], a = as[i];
+      const int half = (T.tp[m] == Pt) ? 0 : 1;
+      const double sm_ = half ? -1.0 : 1.0;
+      for (int32_t e = c->h_near_ptr[m]; e < c->h_near_ptr[m + 1]; ++e) {
+        const int n = c->h_near_col[e];
+        double re = 0.0, im = 0.0;
+        for (int th = 0; th < 2; ++th) {
+          const int Qt = th ? T.tm[n] : T.tp[n];
+          const int b = th ? T.sm[n] : T.sp[n];
+          const double sn_ = th ? -1.0 : 1.0;
+          const Cd v = blk[find(Qt) * 9 + a * 3 + b];
+          re += sm_ * sn_ * v.re;
+          im += sm_ * sn_ * v.im;
+        }
+        // j k eta l_m l_n (re + j im)
+        const double f = jke * T.len[m] * T.len[n];
+        zhalf[(size_t)half * 2 * nnz + 2 * e] = -f * im;
+        zhalf[(size_t)half * 2 * nnz + 2 * e + 1] = f * re;
+      }
+    }
+  }, 4);
+
+  // ---- symmetrise, subtract the grid approximation
+  int dmax = 0;
+  for (int m = 0; m < N; ++m)
+    for (int32_t e = c->h_near_ptr[m]; e < c->h_near_ptr[m + 1]; ++e) {
+      int n = c->h_near_col[e];
+      for (int d = 0; d < 3; ++d)
+        dmax = std::max(dmax, std::abs(c->h_anchor[3 * (size_t)m + d] - c->h_anchor[3 * (size_t)n + d]));
+    }
+  const int TE = dmax + M, TW = 2 * TE + 1;
+  std::vector<double> gtab;  // G_h on offsets [-TE, TE]^3, [re, im]
+  const bool use_tab = (int64_t)TW * TW * TW <= (1LL << 26);
+  auto gh = [&](int ox, int oy, int oz, double* re, double* im) {
+    if ((ox | oy | oz) == 0) {
+      *re = 0.0;
+      *im = 0.0;
+      return;
+    }
+    double r = h * std::sqrt((double)ox * ox + (double)oy * oy + (double)oz * oz);
+    double s = 1.0 / (4.0 * kPi * r);
+    *re = std::cos(k * r) * s;
+    *im = -std::sin(k * r) * s;
+  };
+  if (use_tab) {
+    gtab.resize(2 * (size_t)TW * TW * TW);
+    parallel_for((int64_t)TW * TW * TW, [&](int64_t i) {
+      int ox = (int)(i % TW) - TE, oy = (int)((i / TW) % TW) - TE, oz = (int)(i / ((int64_t)TW * TW)) - TE;
+      gh(ox, oy, oz, &gtab[2 * i], &gtab[2 * i + 1]);
+    });
+  }
+  std::vector<int64_t> soff((size_t)S * S);  // table offset of u_s - u_t
+  for (int s = 0; s < S; ++s)
+    for (int t = 0; t < S; ++t) {
+      const int ox = s % P - t % P, oy = (s / P) % P - (t / P) % P, oz = s / (P * P) - t / (P * P);
+      soff[(size_t)s * S + t] = ((int64_t)oz * TW + oy) * TW + ox;
+    }
+  c->h_near_val.assign(2 * (size_t)nnz, 0.0);
+  c->h_diag.assign(2 * (size_t)N, 0.0);
+  parallel_for(N, [&](int64_t mi) {
+    const int m = (int)mi;
+    const double* lm = &c->h_lam[(size_t)m * 4 * S];
+    for (int32_t e = c->h_near_ptr[m]; e < c->h_near_ptr[m + 1]; ++e) {
+      const int n = c->h_near_col[e];
+      // transposed entry (n, m)
+      const int32_t* rb = &c->h_near_col[c->h_near_ptr[n]];
+      const int32_t* re_ = &c->h_near_col[c->h_near_ptr[n + 1]];
+      const int64_t et = c->h_near_ptr[n] + (std::lower_bound(rb, re_, m) - rb);
+      const double zr = 0.5 * ((zhalf[2 * e] + zhalf[2 * nnz + 2 * e]) + (zhalf[2 * et] + zhalf[2 * nnz + 2 * et]));
+      const double zi = 0.5 * ((zhalf[2 * e + 1] + zhalf[2 * nnz + 2 * e + 1]) + (zhalf[2 * et + 1] + zhalf[2 * nnz + 2 * et + 1]));
+      // grid approximation: j k eta [sum_xyz L_m G L_n - k^-2 L^rho_m G L^rho_n]
+      const double* ln = &c->h_lam[(size_t)n * 4 * S];
+      int dd[3];
+      for (int d = 0; d < 3; ++d) dd[d] = c->h_anchor[3 * (size_t)m + d] - c->h_anchor[3 * (size_t)n + d];
+      double acc_re[4] = {0, 0, 0, 0}, acc_im[4] = {0, 0, 0, 0};
+      if (use_tab) {
+        const int64_t tb = ((int64_t)(dd[2] + TE) * TW + (dd[1] + TE)) * TW + (dd[0] + TE);
+        for (int s = 0; s < S; ++s) {
+          double ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
+          const int64_t* os = &soff[(size_t)s * S];
+          for (int t = 0; t < S; ++t) {
+            const double gr = gtab[2 * (tb + os[t])], gi = gtab[2 * (tb + os[t]) + 1];
+            for (int cc = 0; cc < 4; ++cc) {
+              ar[cc] += gr * ln[cc * S + t];
+              ai[cc] += gi * ln[cc * S + t];
+            }
+          }
+          for (int cc = 0; cc < 4; ++cc) {
+            acc_re[cc] += lm[cc * S + s] * ar[cc];
+            acc_im[cc] += lm[cc * S + s] * ai[cc];
+          }
+        }
+      } else {
+        for (int s = 0; s < S; ++s) {
+          const int si = s % P, sj = (s / P) % P, sk = s / (P * P);
+          double ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
+          for (int t = 0; t < S; ++t) {
+            const int ti = t % P, tj = (t / P) % P, tk = t / (P * P);
+            double gr, gi;
+            gh(dd[0] + si - ti, dd[1] + sj - tj, dd[2] + sk - tk, &gr, &gi);
+            for (int cc = 0; cc < 4; ++cc) {
+              ar[cc] += gr * ln[cc * S + t];
+              ai[cc] += gi * ln[cc * S + t];
+            }
+          }
+          for (int cc = 0; cc < 4; ++cc) {
+            acc_re[cc] += lm[cc * S + s] * ar[cc];
+            acc_im[cc] += lm[cc * S + s] * ai[cc];
+          }
+        }
+      }
+      const double sr = acc_re[0] + acc_re[1] + acc_re[2] - acc_re[3] / (k * k);
+      const double si_ = acc_im[0] + acc_im[1] + acc_im[2] - acc_im[3] / (k * k);
+      // j k eta (sr + j si) = k eta (-si + j sr)
+      const double ar_ = -jke * si_, ai_ = jke * sr;
+      c->h_near_val[2 * e] = zr - ar_;
+      c->h_near_val[2 * e + 1] = zi - ai_;
+      if (n == m) {
+        c->h_diag[2 * (size_t)m] = zr;
+        c->h_diag[2 * (size_t)m + 1] = zi;
+      }
+    }
+  });
+
+  // ---- projection lists (node-ordered transpose of the weights)
+  const int nx = c->n[0], ny = c->n[1];
+  std::vector<int32_t> base(N);
+  for (int m = 0; m < N; ++m) {
+    const int ix = c->h_anchor[3 * (size_t)m] - c->lo[0], iy = c->h_anchor[3 * (size_t)m + 1] - c->lo[1],
+              iz = c->h_anchor[3 * (size_t)m + 2] - c->lo[2];
+    base[m] = (int32_t)(((int64_t)iz * ny + iy) * nx + ix);
+  }
+  std::vector<int32_t> pptr(Nc + 1, 0);
+  auto nonzero = [&](int m, int s) {
+    const double* lm = &c->h_lam[(size_t)m * 4 * S];
+    return lm[s] != 0.0 || lm[S + s] != 0.0 || lm[2 * S + s] != 0.0 || lm[3 * S + s] != 0.0;
+  };
+  auto node_of = [&](int m, int s) {
+    const int i = s % P, j = (s / P) % P, kk = s / (P * P);
+    return (int64_t)base[m] + ((int64_t)kk * ny + j) * nx + i;
+  };
+  for (int m = 0; m < N; ++m)
+    for (int s = 0; s < S; ++s)
+      if (nonzero(m, s)) pptr[node_of(m, s) + 1]++;
+  for (long long u = 0; u < Nc; ++u) pptr[u + 1] += pptr[u];
+  const int64_t nent = pptr[Nc];
+  c->nent = nent;
+  std::vector<int32_t> pm(nent);
+  std::vector<double> pw64(4 * (size_t)nent);
+  std::vector<float> pw32(4 * (size_t)nent);
+  {
+    std::vector<int32_t> fill(pptr.begin(), pptr.end() - 1);
+    for (int m = 0; m < N; ++m)
+      for (int s = 0; s < S; ++s)
+        if (nonzero(m, s)) {
+          const int64_t e = fill[node_of(m, s)]++;
+          pm[e] = m;
+          for (int cc = 0; cc < 4; ++cc) {
+            pw64[4 * e + cc] = c->h_lam[(size_t)m * 4 * S + cc * S + s];
+            pw32[4 * e + cc] = (float)pw64[4 * e + cc];
+          }
+        }
+  }
+
+  // ---- uploads
+  std::vector<float> lam32(c->h_lam.size());
+  for (size_t i = 0; i < lam32.size(); ++i) lam32[i] = (float)c->h_lam[i];
+  std::vector<float> nv32(c->h_near_val.size());
+  for (size_t i = 0; i < nv32.size(); ++i) nv32[i] = (float)c->h_near_val[i];
+  std::vector<double> dinv(2 * (size_t)N);
+  for (int m = 0; m < N; ++m) {
+    const double a = c->h_diag[2 * (size_t)m], b = c->h_diag[2 * (size_t)m + 1];
+    const double d = a * a + b * b;
+    dinv[2 * (size_t)m] = a / d;
+    dinv[2 * (size_t)m + 1] = -b / d;
+  }
+  AIM_TRY(up(&c->base, base));
+  AIM_TRY(up(&c->near_ptr, c->h_near_ptr));
+  AIM_TRY(up(&c->near_col, c->h_near_col));
+  AIM_TRY(up(&c->pnode_ptr, pptr));
+  c->h_pnode_ptr = pptr;
+  AIM_TRY(up(&c->pnode_m, pm));
+  AIM_TRY(upload((void**)&c->p64.pnode_w, pw64.data(), pw64.size() * sizeof(double)));
+  AIM_TRY(upload((void**)&c->p32.pnode_w, pw32.data(), pw32.size() * sizeof(float)));
+  AIM_TRY(upload((void**)&c->p64.lam, c->h_lam.data(), c->h_lam.size() * sizeof(double)));
+  AIM_TRY(upload((void**)&c->p32.lam, lam32.data(), lam32.size() * sizeof(float)));
+  AIM_TRY(upload((void**)&c->p64.near_val, c->h_near_val.data(), c->h_near_val.size() * sizeof(double)));
+  AIM_TRY(upload((void**)&c->p32.near_val, nv32.data(), nv32.size() * sizeof(float)));
+  AIM_TRY(upload((void**)&c->diag, c->h_diag.data(), c->h_diag.size() * sizeof(double)));
+  AIM_TRY(upload((void**)&c->dinv64, dinv.data(), dinv.size() * sizeof(double)));
+  // geometry for right-hand sides and far fields
+  {
+    std::vector<double> vv(3 * (size_t)T.nv);
+    for (int i = 0; i < T.nv; ++i) {
+      vv[3 * i] = T.vert[i].x;
+      vv[3 * i + 1] = T.vert[i].y;
+      vv[3 * i + 2] = T.vert[i].z;
+    }
+    std::vector<int32_t> rt2(2 * (size_t)N), rf2(2 * (size_t)N);
+    for (int m = 0; m < N; ++m) {
+      rt2[2 * m] = T.tp[m];
+      rt2[2 * m + 1] = T.tm[m];
+      rf2[2 * m] = T.fp[m];
+      rf2[2 * m + 1] = T.fm[m];
+    }
+    AIM_TRY(up(&c->d_verts, vv));
+    AIM_TRY(up(&c->d_tris, T.tri));
+    AIM_TRY(up(&c->rwg_tri, rt2));
+    AIM_TRY(up(&c->rwg_free, rf2));
+    AIM_TRY(up(&c->rwg_len, T.len));
+    AIM_TRY(up(&c->tri_area, T.area));
+  }
+  // twiddles and Ghat
+  for (int d = 0; d < 3; ++d) {
+    const int L = c->L[d];
+    std::vector<double> t64(2 * (size_t)L);
+    std::vector<float> t32(2 * (size_t)L);
+    for (int t = 0; t < L; ++t) {
+      const double ang = (2.0 * kPi * t) / L;
+      t64[2 * t] = std::cos(ang);
+      t64[2 * t + 1] = -std::sin(ang);
+      t32[2 * t] = (float)t64[2 * t];
+      t32[2 * t + 1] = (float)t64[2 * t + 1];
+    }
+    AIM_TRY(upload((void**)&c->p64.tw[d], t64.data(), t64.size() * sizeof(double)));
+    AIM_TRY(upload((void**)&c->p32.tw[d], t32.data(), t32.size() * sizeof(float)));
+  }
+  const size_t oct = (size_t)(c->L[0] / 2 + 1) * (c->L[1] / 2 + 1) * (c->L[2] / 2 + 1);
+  AIM_TRY(upload((void**)&c->p64.ghat, nullptr, oct * sizeof(double2)));
+  AIM_TRY(upload((void**)&c->p32.ghat, nullptr, oct * sizeof(float2)));
+  AIM_TRY(build_ghat(c));
+  c->h_ghat.resize(2 * oct);
+  AIM_CUDA_TRY(cudaMemcpyAsync(c->h_ghat.data(), c->p64.ghat, oct * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+  AIM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return AIM_OK;
+}
+
+}  // namespace aim

@@ -1,0 +1,104 @@
+"""The C-ABI library loads and exports every symbol include/aim.h declares (CPU only)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "aim.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(aim_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1010_1456_gb300 import _lib
+
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_1010_1456_gb300 import build
+
+        build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("aim_setup", "aim_matvec", "aim_solve", "aim_rcs", "aim_destroy", "aim_rhs_planewave"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1010_1456_gb300 import _lib
+
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"binding lacks {name}"
+
+
+def test_binding_has_no_extra_symbols():
+    from paper_1010_1456_gb300 import _lib
+
+    assert set(_lib.SIGNATURES) == set(declared_functions())
+
+
+def test_error_strings_and_defaults(lib):
+    from paper_1010_1456_gb300 import _lib
+
+    assert lib.aim_strerror(_lib.AIM_OK) == b"ok"
+    assert lib.aim_strerror(_lib.AIM_ENOCONV) == b"solver did not converge"
+    assert lib.aim_strerror(999) == b"unknown error"
+    o = _lib.aim_opts()
+    lib.aim_default_opts(ctypes.byref(o))
+    assert (o.precision, o.restart, o.max_rhs) == (_lib.AIM_C128, 50, 1)
+
+
+def test_null_and_bad_arguments_are_rejected_without_a_device(lib):
+    from paper_1010_1456_gb300 import _lib
+
+    h = ctypes.c_void_p()
+    # bad scalar arguments fail before any device work
+    assert lib.aim_setup(None, 2.0, 0.1, 2, 0.3, None, ctypes.byref(h)) != _lib.AIM_OK
+    m = _lib.aim_mesh(0, 0, None, None)
+    assert lib.aim_setup(ctypes.byref(m), -1.0, 0.1, 2, 0.3, None, ctypes.byref(h)) == _lib.AIM_EINVAL
+    assert lib.aim_setup(ctypes.byref(m), 6.28, 0.1, 7, 0.3, None, ctypes.byref(h)) == _lib.AIM_EINVAL
+    assert lib.aim_matvec(None, None, None, 1, _lib.AIM_C128) == _lib.AIM_EINVAL
+    assert lib.aim_solve(None, None, None, 1, 1e-6, None) == _lib.AIM_EINVAL
+    assert b"null" in lib.aim_last_error()
+    assert lib.aim_probe_fma_peak(16, ctypes.byref(ctypes.c_double())) == _lib.AIM_EINVAL
+
+
+def test_setup_reports_missing_device(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import numpy as np
+
+    from paper_1010_1456_gb300 import _lib
+    from aim_inputs import plate_mesh
+
+    v, t = plate_mesh(1.0, 3)
+    v = np.ascontiguousarray(v)
+    t = np.ascontiguousarray(t, dtype=np.int32)
+    m = _lib.aim_mesh(len(v), len(t), v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    h = ctypes.c_void_p()
+    assert lib.aim_setup(ctypes.byref(m), 6.28, 0.1, 2, 0.3, None, ctypes.byref(h)) == _lib.AIM_ENODEV
+    assert not h.value
+
+
+def test_footprint_is_host_only(lib):
+    from paper_1010_1456_gb300 import aim_footprint
+    from aim_inputs import icosphere_mesh
+
+    v, t = icosphere_mesh(1.0, 8)
+    b1 = aim_footprint(v, t, 0.1, 2, 0.3, 1)
+    b8 = aim_footprint(v, t, 0.1, 2, 0.3, 8)
+    assert 0 < b1 < b8

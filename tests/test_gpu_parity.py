@@ -1,0 +1,193 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative L2 unless stated): complex128 product 1e-12, complex64
+product 1e-5, setup arrays 1e-12 (FP64 both sides, different summation
+order), right-hand side 1e-12, RCS 1e-6 (the far-field phase factor is taken
+in FP32 after an FP64 range reduction).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from aim_inputs import (  # noqa: E402
+    icosphere_frequency,
+    icosphere_mesh,
+    plate_mesh,
+    planewave_minus_z_xpol,
+    random_complex,
+    random_incidence,
+)
+from oracle import aim as oaim  # noqa: E402
+from oracle.excitation import planewave_rhs  # noqa: E402
+from oracle.rwg import RWG  # noqa: E402
+
+import paper_1010_1456_gb300 as g  # noqa: E402
+
+K0 = 2 * np.pi
+H = 0.1
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    g.load()
+
+
+def make(verts, tris, M=2, radius=None, max_rhs=1, precision=g.AIM_C128, near_rows=None):
+    r = 3 * H if radius is None else radius
+    ctx = g.aim_setup(verts, tris, K0, H, M=M, near_radius=r, max_rhs=max_rhs, precision=precision)
+    op = oaim.AIMOperator(RWG(verts, tris), K0, H, M, near_radius=r, near_rows=near_rows)
+    return ctx, op
+
+
+@pytest.fixture(scope="module")
+def plate_a():
+    v, t = plate_mesh(1.0, 9)
+    return make(v, t, max_rhs=3)
+
+
+@pytest.fixture(scope="module")
+def sphere_small():
+    R = 0.5
+    v, t = icosphere_mesh(R, icosphere_frequency(R))
+    return make(v, t, max_rhs=2)
+
+
+def test_setup_arrays_match_oracle(plate_a):
+    ctx, op = plate_a
+    assert ctx.N == op.N == 225
+    n, L, nnz = g.aim_grid_info(ctx)
+    assert n == list(op.n) and L == list(op.L)
+    assert np.array_equal(g.aim_export(ctx, g.AIM_EXPORT_ANCHORS), op.anc)
+    lam = g.aim_export(ctx, g.AIM_EXPORT_WEIGHTS)
+    assert np.abs(lam - op.lam).max() <= 1e-12 * np.abs(op.lam).max()
+    ptr = g.aim_export(ctx, g.AIM_EXPORT_NEAR_PTR)
+    col = g.aim_export(ctx, g.AIM_EXPORT_NEAR_COL)
+    assert nnz == len(op.near_rows)
+    assert np.array_equal(np.repeat(np.arange(ctx.N), np.diff(ptr)), op.near_rows)
+    assert np.array_equal(col, op.near_cols)
+    val = g.aim_export(ctx, g.AIM_EXPORT_NEAR_VAL)
+    assert rel(val, op.near_vals) <= 1e-12
+    assert rel(g.aim_export(ctx, g.AIM_EXPORT_DIAG), op.diagonal()) <= 1e-12
+    gh = g.aim_export(ctx, g.AIM_EXPORT_GHAT)
+    ref = op.Ghat[: L[2] // 2 + 1, : L[1] // 2 + 1, : L[0] // 2 + 1] / np.prod(L)
+    assert rel(gh, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_matvec_c128_plate(plate_a, nrhs):
+    ctx, op = plate_a
+    x = random_complex((nrhs, ctx.N), 11)
+    y = g.aim_matvec(ctx, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, op.matvec(x)) <= 1e-12
+
+
+def test_matvec_c64_plate(plate_a):
+    ctx, op = plate_a
+    x = random_complex((3, ctx.N), 12)
+    y = g.aim_matvec(ctx, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
+    assert rel(y, op.matvec(x.astype(np.complex64).astype(np.complex128))) <= 1e-5
+
+
+def test_matvec_sphere_both_precisions(sphere_small):
+    ctx, op = sphere_small
+    x = random_complex((2, ctx.N), 13)
+    ref = op.matvec(x)
+    y = g.aim_matvec(ctx, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, ref) <= 1e-12
+    y32 = g.aim_matvec(ctx, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
+    assert rel(y32, ref) <= 1e-5
+
+
+def test_matvec_host_entry_point(plate_a):
+    ctx, op = plate_a
+    x = random_complex((2, ctx.N), 14)
+    assert rel(g.aim_matvec_host(ctx, x), op.matvec(x)) <= 1e-12
+
+
+def test_rhs_matches_oracle(sphere_small):
+    ctx, op = sphere_small
+    kh, po = random_incidence(1, seed=3)
+    V = g.aim_rhs_planewave(ctx, kh, po).cpu().numpy()
+    assert rel(V, planewave_rhs(op.rwg, K0, kh, po)) <= 1e-12
+
+
+@pytest.mark.parametrize("M", [1, 3])
+def test_other_stencil_orders(M):
+    v, t = plate_mesh(0.7, 6)
+    ctx, op = make(v, t, M=M)
+    x = random_complex((1, ctx.N), 15)
+    y = g.aim_matvec(ctx, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, op.matvec(x)) <= 1e-12
+
+
+def test_all_pairs_near_equals_dense():
+    """Near radius beyond the body: the product is the dense Galerkin matrix."""
+    from oracle.efie import dense_Z
+
+    v, t = plate_mesh(0.5, 4)
+    ctx, op = make(v, t, radius=10.0)
+    Z = dense_Z(op.rwg, K0)
+    x = random_complex((1, ctx.N), 16)
+    y = g.aim_matvec(ctx, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y[0], 0.5 * (Z + Z.T) @ x[0]) <= 1e-12
+
+
+def test_ragged_grid_and_single_triangle_pair():
+    # two triangles sharing one edge: N = 1, grid 3x3x3
+    v = np.array([[0, 0, 0], [0.1, 0, 0.01], [0, 0.1, 0.02], [0.11, 0.1, 0.0]], dtype=np.float64)
+    t = np.array([[0, 1, 2], [1, 3, 2]], dtype=np.int32)
+    ctx, op = make(v, t)
+    assert ctx.N == 1
+    x = random_complex((1, 1), 17)
+    y = g.aim_matvec(ctx, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, op.matvec(x)) <= 1e-12
+
+
+def test_invalid_inputs():
+    v, t = plate_mesh(1.0, 2)
+    with pytest.raises(g.AIMError):
+        g.aim_setup(v, t, K0, -H)
+    bad = t.copy()
+    bad[0, 0] = 999
+    with pytest.raises(g.AIMError):
+        g.aim_setup(v, bad, K0, H)
+    # a non-manifold edge: three triangles on one edge
+    v3 = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1]], dtype=float) * 0.1
+    t3 = np.array([[0, 1, 2], [0, 1, 3], [0, 1, 4]], dtype=np.int32)
+    with pytest.raises(g.AIMError):
+        g.aim_setup(v3, t3, K0, H)
+    ctx = g.aim_setup(v, t, K0, H, max_rhs=1)
+    x = torch.zeros((2, ctx.N), dtype=torch.complex128, device="cuda")
+    with pytest.raises(g.AIMError):
+        g.aim_matvec(ctx, x)  # nrhs > max_rhs
+
+
+def test_zero_vector_gives_zero(plate_a):
+    ctx, _ = plate_a
+    x = torch.zeros((1, ctx.N), dtype=torch.complex128, device="cuda")
+    assert torch.count_nonzero(g.aim_matvec(ctx, x)).item() == 0
+
+
+@pytest.mark.slow
+def test_full_size_sphere_sampled_rows():
+    """4 lambda sphere (N = 58,080, grid 83^3 padded 180^3): sampled rows, both precisions."""
+    R = 4.0
+    v, t = icosphere_mesh(R, icosphere_frequency(R))
+    rows = np.sort(np.random.default_rng(0).choice(30 * 44 * 44, 300, replace=False))
+    ctx, op = make(v, t, near_rows=rows)
+    assert ctx.N == 58080
+    x = random_complex((1, ctx.N), 21)
+    ref = op.matvec(x)[0, rows]
+    y = g.aim_matvec(ctx, torch.from_numpy(x).cuda()).cpu().numpy()[0, rows]
+    assert rel(y, ref) <= 1e-12
+    y32 = g.aim_matvec(ctx, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()[0, rows]
+    assert rel(y32, ref) <= 1e-5
