@@ -1,0 +1,90 @@
+"""Host-side logic of the request loop (CPU only): admission by footprint,
+slot limits, arrival order, failure isolation.  The solve itself is replaced
+by a fake that sleeps, so no GPU is touched."""
+
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_1010_1456_gb300 import serve
+
+
+class FakeServer(serve.Server):
+    def __init__(self, footprints, durations, fail=(), **kw):
+        super().__init__(**kw)
+        self.fps = footprints
+        self.durs = durations
+        self.fail = set(fail)
+        self.live = 0
+        self.live_lock = threading.Lock()
+        self.max_live = 0
+        self.order = []
+
+    def _make_stream(self):
+        return None
+
+    def _footprint(self, req):
+        return self.fps[req.rid]
+
+    def _run(self, req, fp, stream, admitted):
+        with self.live_lock:
+            self.live += 1
+            self.max_live = max(self.max_live, self.live)
+            self.order.append(req.rid)
+        time.sleep(self.durs[req.rid])
+        with self.live_lock:
+            self.live -= 1
+        if req.rid in self.fail:
+            return serve.Result(req.rid, None, None, 0, req.arrival, admitted, time.perf_counter() - self.t0, fp,
+                                error="injected")
+        return serve.Result(req.rid, np.zeros((1, 1)), np.array([0.0]), 1, req.arrival, admitted,
+                            time.perf_counter() - self.t0, fp)
+
+
+def reqs(n, gap=0.0):
+    v = np.zeros((3, 3))
+    t = np.zeros((1, 3), dtype=np.int32)
+    return [serve.Request(i, v, t, np.zeros((1, 3)), np.zeros((1, 3)), arrival=i * gap) for i in range(n)]
+
+
+def test_budget_and_slots_are_respected():
+    fps = [40, 40, 40, 70, 10, 10]
+    s = FakeServer(fps, [0.05] * 6, slots=3, mem_budget=100)
+    res, span = s.run(reqs(6), realtime=False)
+    assert all(r.error is None for r in res)
+    assert s.peak_claimed <= 100
+    assert s.max_live <= 3
+    assert s.peak_busy >= 2  # work overlapped
+
+
+def test_oversized_request_runs_alone():
+    s = FakeServer([500, 10], [0.02, 0.02], slots=2, mem_budget=100)
+    res, _ = s.run(reqs(2), realtime=False)
+    assert all(r.error is None for r in res)
+
+
+def test_small_requests_pass_a_blocked_large_one():
+    # request 1 does not fit while 0 runs; request 2 does and is admitted first
+    fps = [80, 50, 10]
+    s = FakeServer(fps, [0.2, 0.01, 0.01], slots=3, mem_budget=100)
+    res, _ = s.run(reqs(3), realtime=False)
+    assert s.order.index(2) < s.order.index(1)
+
+
+def test_failure_is_isolated_and_summarised():
+    s = FakeServer([1, 1, 1], [0.01] * 3, fail=[1], slots=2, mem_budget=100)
+    res, span = s.run(reqs(3), realtime=False)
+    summ = serve.summarize(res, span)
+    assert summ["solves"] == 2 and summ["failed"] == 1
+    assert summ["p50_s"] is not None and summ["p99_s"] >= summ["p50_s"]
+
+
+def test_poisson_stream_draws_are_seeded():
+    a = serve.make_stream(6, rate=2.0, seed=1, plate_sides=(1,), sphere_radii=(0.5,), max_rhs=3)
+    b = serve.make_stream(6, rate=2.0, seed=1, plate_sides=(1,), sphere_radii=(0.5,), max_rhs=3)
+    assert [r.arrival for r in a] == [r.arrival for r in b]
+    assert [r.label for r in a] == [r.label for r in b]
+    assert all(1 <= len(r.khat) <= 3 for r in a)
+    assert np.all(np.diff([r.arrival for r in a]) > 0)
