@@ -82,12 +82,19 @@ def kernel_models(N, n, L, nnz, nent, S, nrhs, e):
     return m
 
 
-def source_digest():
+KERNEL_SOURCES = {
+    "proj_gather": ("matvec.cu", "common.h"),
+    "interp_near": ("matvec.cu", "common.h"),
+}
+
+
+def source_digest(kernel):
+    """Hash of the source files a kernel is built from (fft.cu for the FFT passes)."""
+    files = KERNEL_SOURCES.get(kernel, ("fft.cu", "common.h"))
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1010_1456_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:12]
 
 
@@ -96,7 +103,7 @@ def ncu_traffic(workload, kernel):
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    dig = source_digest()
+    dig = source_digest(kernel)
     for line in open(path):
         p = line.split()
         if len(p) == 4 and p[0] == workload and p[1] == kernel and p[2] == dig:
@@ -122,6 +129,9 @@ class ClockSampler:
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.perf_counter()
+            while not self.rows and time.perf_counter() - t0 < 5.0:  # sampler is live before timing starts
+                time.sleep(0.02)
         except OSError:
             self.proc = None
         return self
@@ -194,6 +204,43 @@ def oracle_matvec_rate(verts, tris, nrhs, budget_s=20.0, sample_rows=192, seed=0
         "sample": f"{reps} oracle products (NumPy/SciPy FP64, scipy.fft workers={os.cpu_count()}); full grid part, "
                   f"near SpMV of {len(rows)} seeded rows scaled by N/{len(rows)}",
     }
+
+
+# ---------------------------------------------------------------- solves
+def solve_section(g, ctx, kind, size, nrhs, P0):
+    """Plain (complex128) and mixed (complex64 + FP64 refinement) solves of
+    the workload's excitation, tol 1e-6; err_thth of the mixed RCS against
+    the plain RCS by eq. (1)."""
+    import torch
+
+    from aim_inputs import planewave_minus_z_xpol, random_incidence
+
+    if nrhs == 1:
+        kh, po = planewave_minus_z_xpol()
+    else:
+        kh, po = random_incidence((nrhs + 1) // 2, seed=0)
+        kh, po = kh[:nrhs], po[:nrhs]
+    V = g.aim_rhs_planewave(ctx, kh, po)
+    ka = K0 * (size if kind == "sphere" else size / np.sqrt(2.0))
+    nth = max(64, 4 * int(np.ceil(ka)))
+    th, ph, w = g.rcs_direction_grid(nth)
+    out = {}
+    sig = {}
+    for name, P in (("plain_fp64", g.AIM_C128), ("mixed_c64_fp64_refined", g.AIM_C64)):
+        g.aim_set_precision(ctx, P)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        X, info = g.aim_solve(ctx, V, 1e-6, raise_on_noconv=False)
+        t = time.perf_counter() - t0
+        sig[name] = g.aim_rcs(ctx, X, th, ph)[0]
+        out[name] = {"time_s": t, "solves_per_s": 1.0 / t, "rhs_per_s": nrhs / t, "iterations": info["iterations"],
+                     "restarts": info["restarts"], "max_rel_res": float(info["rel_res"].max()),
+                     "converged": bool(info["converged"].all())}
+    g.aim_set_precision(ctx, P0)
+    out["err_thth_mixed_vs_plain"] = float(np.max(g.err_thth(sig["mixed_c64_fp64_refined"], sig["plain_fp64"], w)))
+    out["speedup_mixed_over_plain"] = out["plain_fp64"]["time_s"] / out["mixed_c64_fp64_refined"]["time_s"]
+    out["rcs_directions"] = int(len(th))
+    return out
 
 
 # ---------------------------------------------------------------- reference arm
@@ -281,6 +328,8 @@ def run_ours(args, rank, world, local_rank):
         total_ms = float(t.item())
     value = world * args.steps * nrhs / (total_ms * 1e-3)
 
+    solve = solve_section(g, ctx, kind, size, nrhs, P) if args.solve else None
+
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e_steps = max(3, args.steps)
     g.aim_matvec_host(ctx, xh, precision=P)
@@ -350,6 +399,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "kernels": kernels,
+        "solve": solve,
         "fp64_fma_tflops": alu64,
         "fp32_fma_tflops": alu32,
     }
@@ -364,11 +414,12 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve", type=int, default=1, help="1: also time plain and mixed solves")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -100,6 +100,9 @@ void aim_destroy(aim_ctx* ctx); /* frees everything; NULL is a no-op; synchronis
 
 int aim_set_stream(aim_ctx* ctx, void* stream);
 
+/* Change the solver's inner-product precision (AIM_C64 or AIM_C128) after setup. */
+int aim_set_precision(aim_ctx* ctx, int precision);
+
 /* N (number of unknowns). */
 int aim_num_unknowns(const aim_ctx* ctx, int64_t* N);
 

@@ -119,6 +119,11 @@ def aim_set_stream(ctx, stream):
     check(load().aim_set_stream(ctx.handle, C.c_void_p(int(stream))), "aim_set_stream")
 
 
+def aim_set_precision(ctx, precision):
+    check(load().aim_set_precision(ctx.handle, int(precision)), "aim_set_precision")
+    ctx.precision = precision
+
+
 def aim_num_unknowns(ctx):
     N = C.c_int64()
     check(load().aim_num_unknowns(ctx.handle, C.byref(N)), "aim_num_unknowns")
@@ -273,3 +278,22 @@ def aim_probe_fma_peak(which=64):
     t = C.c_double()
     check(load().aim_probe_fma_peak(int(which), C.byref(t)), "aim_probe_fma_peak")
     return float(t.value)
+
+
+def rcs_direction_grid(n_theta, n_phi=None):
+    """Directions and weights for eq. (1): Gauss-Legendre nodes in cos(theta),
+    uniform phi.  Returns (theta, phi, weight) flattened theta-major."""
+    n_phi = 2 * n_theta if n_phi is None else n_phi
+    mu, wmu = np.polynomial.legendre.leggauss(n_theta)
+    th = np.arccos(mu)
+    ph = (np.arange(n_phi) + 0.5) * (2.0 * np.pi / n_phi)
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    return T.ravel(), P.ravel(), np.repeat(wmu, n_phi) * (2.0 * np.pi / n_phi)
+
+
+def err_thth(sigma, sigma_ref, weight):
+    """Paper eq. (1): relative RMS difference of two bistatic RCS patterns over the sphere."""
+    sigma, sigma_ref = np.asarray(sigma), np.asarray(sigma_ref)
+    num = (np.abs(sigma - sigma_ref) ** 2 * weight).sum(axis=-1)
+    den = (np.abs(sigma_ref) ** 2 * weight).sum(axis=-1)
+    return np.sqrt(num / den)

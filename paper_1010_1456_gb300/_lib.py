@@ -48,6 +48,7 @@ SIGNATURES = {
                             C.POINTER(C.c_void_p)]),
     "aim_destroy": (None, [C.c_void_p]),
     "aim_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "aim_set_precision": (C.c_int, [C.c_void_p, C.c_int]),
     "aim_num_unknowns": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "aim_grid_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "aim_rhs_planewave": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),

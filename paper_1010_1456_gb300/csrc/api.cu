@@ -163,6 +163,16 @@ int aim_set_stream(aim_ctx* ctx, void* stream) {
   return AIM_OK;
 }
 
+int aim_set_precision(aim_ctx* ctx, int precision) {
+  AIM_TRY(check_ctx(ctx));
+  if (precision != AIM_C64 && precision != AIM_C128) {
+    set_error("aim_set_precision: precision must be AIM_C64 or AIM_C128");
+    return AIM_EINVAL;
+  }
+  ctx->opts.precision = precision;
+  return AIM_OK;
+}
+
 int aim_num_unknowns(const aim_ctx* ctx, int64_t* N) {
   AIM_TRY(check_ctx(ctx));
   if (!N) return AIM_EINVAL;

@@ -279,7 +279,8 @@ int alloc_krylov(aim_ctx* c) {
   if (k.V) return AIM_OK;
   const int B = c->max_rhs, m = c->opts.restart, N = c->N;
   k.m = m;
-  k.nblk = std::max(1, std::min(256, (N + 4095) / 4096));
+  // about four blocks per SM over all right-hand sides, at least 256 elements per block
+  k.nblk = std::max(1, std::min((4 * 152 + B - 1) / B, (N + 255) / 256));
   const size_t vec = (size_t)N * sizeof(double2);
   AIM_CUDA_TRY(cudaMalloc(&k.V, vec * B * (m + 1)));
   AIM_CUDA_TRY(cudaMalloc(&k.w, vec * B));
