@@ -36,13 +36,16 @@ K0 = 2.0 * np.pi
 H = 0.1
 
 WORKLOADS = {
-    # name: (kind, size, nrhs, precision)
+    # name: (kind, size, nrhs, precision); "c128" = FP64-accurate product with
+    # float-float FFT passes, "f64" = native FP64 throughout, "c64" = complex64
     "pec-sphere-r4lambda-fp64-1rhs": ("sphere", 4.0, 1, "c128"),
+    "pec-sphere-r4lambda-nativefp64-1rhs": ("sphere", 4.0, 1, "f64"),
     "pec-sphere-r4lambda-c64-1rhs": ("sphere", 4.0, 1, "c64"),
     "pec-plate-1lambda-fp64-1rhs": ("plate", 1.0, 1, "c128"),
     "pec-plate-32lambda-c64-64rhs": ("plate", 32.0, 64, "c64"),
     "pec-sphere-r16lambda-c64-8rhs": ("sphere", 16.0, 8, "c64"),
 }
+PRECISION = {"c128": 2, "f64": 3, "c64": 1}  # AIM_C128, AIM_C128_F64, AIM_C64
 DEFAULT = "pec-sphere-r4lambda-fp64-1rhs"
 
 
@@ -109,6 +112,18 @@ def ncu_traffic(workload, kernel):
         if len(p) == 4 and p[0] == workload and p[1] == kernel and p[2] == dig:
             return float(p[3])
     return None
+
+
+def aggregate(total_ms, steps, nrhs, world, device=None):
+    """Whole-job rate of independent replicas: every rank timed `steps` products
+    of `nrhs` vectors; the job time is the slowest rank's (max over ranks)."""
+    if world > 1:
+        import torch
+
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps * nrhs / (total_ms * 1e-3)
 
 
 # ---------------------------------------------------------------- clocks
@@ -226,7 +241,8 @@ def solve_section(g, ctx, kind, size, nrhs, P0):
     th, ph, w = g.rcs_direction_grid(nth)
     out = {}
     sig = {}
-    for name, P in (("plain_fp64", g.AIM_C128), ("mixed_c64_fp64_refined", g.AIM_C64)):
+    for name, P in (("plain_fp64", g.AIM_C128_F64), ("fp64_float_float_fft", g.AIM_C128),
+                    ("mixed_c64_fp64_refined", g.AIM_C64)):
         g.aim_set_precision(ctx, P)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -238,9 +254,65 @@ def solve_section(g, ctx, kind, size, nrhs, P0):
                      "converged": bool(info["converged"].all())}
     g.aim_set_precision(ctx, P0)
     out["err_thth_mixed_vs_plain"] = float(np.max(g.err_thth(sig["mixed_c64_fp64_refined"], sig["plain_fp64"], w)))
+    out["err_thth_float_float_vs_plain"] = float(np.max(g.err_thth(sig["fp64_float_float_fft"], sig["plain_fp64"], w)))
     out["speedup_mixed_over_plain"] = out["plain_fp64"]["time_s"] / out["mixed_c64_fp64_refined"]["time_s"]
     out["rcs_directions"] = int(len(th))
     return out
+
+
+# ---------------------------------------------------------------- serving
+SERVE_SIZES = {
+    # the stream of the serving configuration: plate sides / sphere radii in wavelengths
+    "paper": ((2, 4, 8, 16, 32), (1, 2, 4, 8)),
+    "small": ((1, 2, 4), (0.5, 1)),
+}
+
+
+def run_serve(args):
+    """Continuous-batching stream: capacity (closed loop), then Poisson arrivals at 0.7 x capacity."""
+    import torch
+
+    from paper_1010_1456_gb300 import serve
+
+    torch.cuda.set_device(0)
+    plates, spheres = SERVE_SIZES[args.serve_sizes]
+    cap_reqs = serve.make_stream(args.requests, rate=1.0, seed=2, plate_sides=plates, sphere_radii=spheres,
+                                 max_rhs=args.serve_max_rhs)
+    srv = serve.Server(slots=args.slots)
+    res, span = srv.run(cap_reqs, realtime=False)
+    cap = serve.summarize(res, span)
+    rate = 0.7 * cap["solves_per_s"]
+    reqs = serve.make_stream(args.requests, rate=rate, seed=1, plate_sides=plates, sphere_radii=spheres,
+                             max_rhs=args.serve_max_rhs)
+    srv = serve.Server(slots=args.slots)
+    t0 = time.perf_counter()
+    with ClockSampler(0) as clk:
+        res, span = srv.run(reqs, realtime=True)
+    wall = time.perf_counter() - t0
+    summ = serve.summarize(res, span)
+    line = {
+        "metric": "served solves/s (p50/p99 latency), complex64 AIM with FP64 refinement, tol 1e-6",
+        "value": summ["solves_per_s"],
+        "unit": "solves/s",
+        "n_gpus": 1,
+        "higher_is_better": True,
+        "data": "synthetic",
+        "config": {"workload": f"serving stream ({args.serve_sizes} sizes): plates {plates} lambda, spheres {spheres} "
+                               f"lambda, 1..{args.serve_max_rhs} RHS, Poisson seed 1 at 0.7 x capacity",
+                   "requests": args.requests, "slots": args.slots},
+        "p50_s": summ["p50_s"],
+        "p99_s": summ["p99_s"],
+        "rhs_per_s": summ["rhs_per_s"],
+        "capacity_solves_per_s": cap["solves_per_s"],
+        "arrival_rate_per_s": rate,
+        "failed": summ["failed"],
+        "max_rel_res": summ["max_rel_res"],
+        "peak_concurrent": srv.peak_busy,
+        "wall_s": wall,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 # ---------------------------------------------------------------- reference arm
@@ -282,9 +354,9 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     kind, size, nrhs, prec = WORKLOADS[args.workload]
     verts, tris = mesh_for(kind, size)
-    P = g.AIM_C128 if prec == "c128" else g.AIM_C64
-    cdt = torch.complex128 if prec == "c128" else torch.complex64
-    e = 16 if prec == "c128" else 8
+    P = PRECISION[prec]
+    wide = prec != "c64"
+    e = 16 if wide else 8
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
     ctx = g.aim_setup(verts, tris, K0, H, M=2, near_radius=3 * H, max_rhs=nrhs, precision=P,
@@ -294,7 +366,7 @@ def run_ours(args, rank, world, local_rank):
     N = ctx.N
     from aim_inputs import random_complex
 
-    xh = random_complex((nrhs, N), 1000 + rank).astype(np.complex128 if prec == "c128" else np.complex64)
+    xh = random_complex((nrhs, N), 1000 + rank).astype(np.complex128 if wide else np.complex64)
     x = torch.from_numpy(xh).to(dev)
     y = torch.empty_like(x)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -321,13 +393,29 @@ def run_ours(args, rank, world, local_rank):
     g.aim_profile(ctx, 0)
     prof = g.aim_profile_read(ctx)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * nrhs / (total_ms * 1e-3)
+    total_ms, value = aggregate(sum(step_ms), args.steps, nrhs, world, dev)
 
+    variants = {}
+    for vname, vprec in (("f64", "native FP64 product"), ("c128", "float-float FFT product"), ("c64", "complex64 product")):
+        if vname == prec or not args.variants:
+            continue
+        VP = PRECISION[vname]
+        xv = torch.from_numpy(xh.astype(np.complex64 if vname == "c64" else np.complex128)).to(dev)
+        yv = torch.empty_like(xv)
+        for _ in range(3):
+            g.aim_matvec(ctx, xv, yv, precision=VP)
+        torch.cuda.synchronize()
+        vsteps = max(10, args.steps // 4)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(vsteps)]
+        for i in range(vsteps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            g.aim_matvec(ctx, xv, yv, precision=VP)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        vms = sum(a.elapsed_time(b) for a, b in evs) / vsteps
+        variants[vname] = {"what": vprec, "matvec_per_s": nrhs * 1e3 / vms, "ms_per_step": vms, "steps": vsteps}
+        del xv, yv
     solve = solve_section(g, ctx, kind, size, nrhs, P) if args.solve else None
 
     # end to end through the host-buffer entry point (copies inside the timed region)
@@ -352,7 +440,7 @@ def run_ours(args, rank, world, local_rank):
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
     alu64 = g.aim_probe_fma_peak(64)
     alu32 = g.aim_probe_fma_peak(32)
-    alu = alu64 if prec == "c128" else alu32
+    alu = alu64 if prec == "f64" else alu32
     bytes_, flops = models.get(dom, (None, None))
     avg_s = kernels[dom]["avg_ms"] * 1e-3
     if bytes_ is not None:
@@ -360,7 +448,7 @@ def run_ours(args, rank, world, local_rank):
         ridge = alu * 1e12 / (hbm * 1e9)
         if intensity > ridge:
             roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": alu, "unit": "TFLOP/s",
-                    "peak_source": f"FP{'64' if prec == 'c128' else '32'} FMA probe (aim_probe_fma_peak), this run"}
+                    "peak_source": f"FP{'64' if prec == 'f64' else '32'} FMA probe (aim_probe_fma_peak), this run"}
         else:
             roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
                     "peak_source": hbm_src}
@@ -389,7 +477,8 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if prec == "c128" else "f32",
+        "dtype": {"f64": "f64", "c128": "f64 (FFT passes: f32 float-float pairs)", "c64": "f32"}[prec],
+        "variants": variants,
         "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "grid": n, "padded": L, "nnz_near": nnz, "nrhs": nrhs,
                    "M": 2, "h_lambda": H, "near_radius_h": 3, "l2": "flushed between steps (256 MB write)",
@@ -420,8 +509,16 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve", type=int, default=1, help="1: also time plain and mixed solves")
+    ap.add_argument("--variants", type=int, default=1, help="1: also time the other product precisions")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--serve", action="store_true", help="run the serving stream instead of the product benchmark")
+    ap.add_argument("--serve-sizes", choices=sorted(SERVE_SIZES), default="small")
+    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--serve-max-rhs", type=int, default=16)
     args = ap.parse_args()
+    if args.serve:
+        return run_serve(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))

@@ -49,7 +49,18 @@ enum {
   AIM_ENODEV = 6    /* no CUDA device visible */
 };
 
-enum { AIM_C64 = 1, AIM_C128 = 2 };
+/*
+ * Precisions of the product.  All three keep the setup arrays in FP64 and
+ * round them once where a lower precision is used.
+ *   AIM_C64      complex64 vectors; FP32 weights, spectrum, near entries,
+ *                grids and accumulation (the mixed-precision inner product).
+ *   AIM_C128     complex128 vectors; projection, interpolation and near SpMV
+ *                in FP64, FFT passes in float-float arithmetic (pairs of
+ *                FP32 numbers, about 48 significant bits) on the FP32 pipes.
+ *   AIM_C128_F64 complex128 vectors; every step in native FP64 (the plain
+ *                FP64 path; on GB300 its FFT is bound by the FP64 pipe).
+ */
+enum { AIM_C64 = 1, AIM_C128 = 2, AIM_C128_F64 = 3 };
 
 typedef struct aim_ctx aim_ctx; /* opaque, library-owned */
 
@@ -63,7 +74,7 @@ typedef struct {
 
 /* Options; aim_default_opts() fills the defaults shown. */
 typedef struct {
-  int precision;   /* solver inner-matvec precision: AIM_C128 (default) or AIM_C64 */
+  int precision;   /* solver inner-product precision: AIM_C128 (default), AIM_C128_F64 or AIM_C64 */
   int restart;     /* GMRES restart length m (default 50, 1..200) */
   int maxit;       /* total inner iteration cap per solve (default 3000) */
   int check_every; /* host reads the residual estimate every k iterations (default 5) */
@@ -119,10 +130,11 @@ int aim_rhs_planewave(aim_ctx* ctx, int nrhs, const double* khat, const double* 
 /*
  * y = Z~ x: one AIM product for nrhs vectors (paper Section 4.1: projection,
  * pruned FFT convolution on the doubled grid, interpolation, near
- * correction).  precision AIM_C128: x_dev, y_dev c128 [nrhs][N], FP64
- * throughout.  AIM_C64: x_dev, y_dev c64 [nrhs][N], FP32 weights, spectrum,
- * near entries and accumulation.  1 <= nrhs <= opts.max_rhs.  x and y must
- * not overlap.  Enqueued on the context stream; does not synchronise.
+ * correction).  precision AIM_C128 or AIM_C128_F64: x_dev, y_dev c128
+ * [nrhs][N]; AIM_C64: x_dev, y_dev c64 [nrhs][N] (see the precision enum).
+ * 1 <= nrhs <= opts.max_rhs.  x and y must not overlap.  Enqueued on the
+ * context stream; does not synchronise, except that the first product in a
+ * precision allocates that precision's grids (cudaMalloc).
  */
 int aim_matvec(aim_ctx* ctx, const void* x_dev, void* y_dev, int nrhs, int precision);
 
@@ -138,8 +150,9 @@ int aim_matvec_host(aim_ctx* ctx, const void* x_host, void* y_host, int nrhs, in
  * restarted GMRES(m), M^-1 = diag(Z~)^-1, classical Gram-Schmidt with one
  * re-orthogonalisation, FP64 dot products and Givens rotations on the
  * device.  The Arnoldi products use opts.precision; every restart computes
- * the true residual with the FP64 product, so AIM_C64 is FP64 iterative
- * refinement around a complex64 inner solve.  Stops when every right-hand
+ * the true residual with an FP64-accurate product (AIM_C128, or AIM_C128_F64
+ * when that is opts.precision), so AIM_C64 is FP64 iterative refinement
+ * around a complex64 inner solve.  Stops when every right-hand
  * side has ||V - Z~ X|| / ||V|| <= tol (true residual) or after opts.maxit
  * steps (AIM_ENOCONV).  V_dev, X_dev: device c128 [nrhs][N]; X is
  * overwritten (initial guess 0).  info may be NULL.  Synchronises.

@@ -16,6 +16,7 @@ import numpy as np
 from ._lib import (  # noqa: F401
     AIM_C64,
     AIM_C128,
+    AIM_C128_F64,
     AIM_EXPORT_ANCHORS,
     AIM_EXPORT_DIAG,
     AIM_EXPORT_GHAT,
@@ -164,7 +165,7 @@ def aim_matvec(ctx, x, y=None, precision=None):
     torch = _torch()
     if precision is None:
         precision = AIM_C128 if x.dtype == torch.complex128 else AIM_C64
-    dt = torch.complex128 if precision == AIM_C128 else torch.complex64
+    dt = torch.complex64 if precision == AIM_C64 else torch.complex128
     x2 = x.reshape(-1, ctx.N)
     if y is None:
         y = torch.empty_like(x2)
@@ -174,7 +175,7 @@ def aim_matvec(ctx, x, y=None, precision=None):
 
 def aim_matvec_host(ctx, x, precision=AIM_C128):
     """Same product with host (numpy) buffers, copies included; synchronises."""
-    dt = np.complex128 if precision == AIM_C128 else np.complex64
+    dt = np.complex64 if precision == AIM_C64 else np.complex128
     x = np.ascontiguousarray(np.atleast_2d(x), dtype=dt)
     y = np.empty_like(x)
     check(load().aim_matvec_host(ctx.handle, x.ctypes.data_as(C.c_void_p), y.ctypes.data_as(C.c_void_p),

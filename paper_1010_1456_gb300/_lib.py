@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libaim.so")
 
 AIM_OK, AIM_EINVAL, AIM_ENOMEM, AIM_ECUDA, AIM_ENOCONV, AIM_ETIMEOUT, AIM_ENODEV = range(7)
-AIM_C64, AIM_C128 = 1, 2
+AIM_C64, AIM_C128, AIM_C128_F64 = 1, 2, 3
 (AIM_EXPORT_ANCHORS, AIM_EXPORT_WEIGHTS, AIM_EXPORT_NEAR_PTR, AIM_EXPORT_NEAR_COL, AIM_EXPORT_NEAR_VAL,
  AIM_EXPORT_DIAG, AIM_EXPORT_GHAT, AIM_EXPORT_PROJ_PTR) = range(1, 9)
 

@@ -13,16 +13,12 @@ namespace aim {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+// staging vectors of a precision (grids are allocated on first use)
 template <typename R> static int ensure_buffers(aim_ctx* c, PrecData<R>& p) {
-  if (p.grid0) return AIM_OK;
-  const long long B = c->max_rhs;
-  const long long nx = c->n[0], ny = c->n[1], nz = c->n[2], Ly = c->L[1], Lz = c->L[2];
+  if (p.xbuf) return AIM_OK;
   const size_t e = sizeof(cplx<R>);
-  AIM_CUDA_TRY(cudaMalloc(&p.grid0, e * B * 4 * nz * ny * nx));
-  AIM_CUDA_TRY(cudaMalloc(&p.grid1, e * B * 4 * Lz * ny * nx));
-  AIM_CUDA_TRY(cudaMalloc(&p.grid2, e * B * 4 * Lz * Ly * nx));
-  AIM_CUDA_TRY(cudaMalloc(&p.xbuf, e * B * c->N));
-  AIM_CUDA_TRY(cudaMalloc(&p.ybuf, e * B * c->N));
+  AIM_CUDA_TRY(cudaMalloc(&p.xbuf, e * c->max_rhs * c->N));
+  AIM_CUDA_TRY(cudaMalloc(&p.ybuf, e * c->max_rhs * c->N));
   return AIM_OK;
 }
 
@@ -38,6 +34,10 @@ static void free_ctx(aim_ctx* c) {
   cudaDeviceSynchronize();
   free_prec(c->p64);
   free_prec(c->p32);
+  cudaFree(c->pff.ghat);
+  for (int d = 0; d < 3; ++d) cudaFree(c->pff.tw[d]);
+  cudaFree(c->pff.grid0); cudaFree(c->pff.grid1); cudaFree(c->pff.grid2);
+  cudaFree(c->plan_dev);
   free_krylov(c);
   profile_free(c);
   cudaFree(c->base); cudaFree(c->near_ptr); cudaFree(c->near_col); cudaFree(c->pnode_ptr); cudaFree(c->pnode_m);
@@ -111,8 +111,8 @@ int aim_setup(const aim_mesh* mesh, double k, double h, int M, double near_radiu
   aim_opts o;
   aim_default_opts(&o);
   if (opts) o = *opts;
-  if (o.precision != AIM_C64 && o.precision != AIM_C128) {
-    set_error("aim_setup: precision must be AIM_C64 or AIM_C128");
+  if (o.precision != AIM_C64 && o.precision != AIM_C128 && o.precision != AIM_C128_F64) {
+    set_error("aim_setup: precision must be AIM_C64, AIM_C128 or AIM_C128_F64");
     return AIM_EINVAL;
   }
   if (o.restart < 1 || o.restart > 200 || o.max_rhs < 1 || o.max_rhs > 256 || o.maxit < 1 || o.check_every < 1) {
@@ -165,8 +165,8 @@ int aim_set_stream(aim_ctx* ctx, void* stream) {
 
 int aim_set_precision(aim_ctx* ctx, int precision) {
   AIM_TRY(check_ctx(ctx));
-  if (precision != AIM_C64 && precision != AIM_C128) {
-    set_error("aim_set_precision: precision must be AIM_C64 or AIM_C128");
+  if (precision != AIM_C64 && precision != AIM_C128 && precision != AIM_C128_F64) {
+    set_error("aim_set_precision: precision must be AIM_C64, AIM_C128 or AIM_C128_F64");
     return AIM_EINVAL;
   }
   ctx->opts.precision = precision;
@@ -205,10 +205,11 @@ int aim_matvec(aim_ctx* ctx, const void* x_dev, void* y_dev, int nrhs, int preci
     set_error("aim_matvec: need 1 <= nrhs <= max_rhs and distinct non-null x, y");
     return AIM_EINVAL;
   }
-  if (precision == AIM_C128) return matvec<double>(ctx, (const double2*)x_dev, (double2*)y_dev, nrhs);
-  if (precision == AIM_C64) return matvec<float>(ctx, (const float2*)x_dev, (float2*)y_dev, nrhs);
-  set_error("aim_matvec: precision must be AIM_C64 or AIM_C128");
-  return AIM_EINVAL;
+  if (precision != AIM_C64 && precision != AIM_C128 && precision != AIM_C128_F64) {
+    set_error("aim_matvec: precision must be AIM_C64, AIM_C128 or AIM_C128_F64");
+    return AIM_EINVAL;
+  }
+  return matvec(ctx, x_dev, y_dev, nrhs, precision);
 }
 
 int aim_matvec_host(aim_ctx* ctx, const void* x_host, void* y_host, int nrhs, int precision) {
@@ -217,13 +218,14 @@ int aim_matvec_host(aim_ctx* ctx, const void* x_host, void* y_host, int nrhs, in
     set_error("aim_matvec_host: bad arguments");
     return AIM_EINVAL;
   }
-  if (precision != AIM_C128 && precision != AIM_C64) {
-    set_error("aim_matvec_host: precision must be AIM_C64 or AIM_C128");
+  if (precision != AIM_C64 && precision != AIM_C128 && precision != AIM_C128_F64) {
+    set_error("aim_matvec_host: precision must be AIM_C64, AIM_C128 or AIM_C128_F64");
     return AIM_EINVAL;
   }
-  const size_t bytes = (size_t)nrhs * ctx->N * (precision == AIM_C128 ? 16 : 8);
-  void* xd = precision == AIM_C128 ? (void*)ctx->p64.xbuf : (void*)ctx->p32.xbuf;
-  void* yd = precision == AIM_C128 ? (void*)ctx->p64.ybuf : (void*)ctx->p32.ybuf;
+  const bool wide = precision != AIM_C64;
+  const size_t bytes = (size_t)nrhs * ctx->N * (wide ? 16 : 8);
+  void* xd = wide ? (void*)ctx->p64.xbuf : (void*)ctx->p32.xbuf;
+  void* yd = wide ? (void*)ctx->p64.ybuf : (void*)ctx->p32.ybuf;
   AIM_CUDA_TRY(cudaMemcpyAsync(xd, x_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
   AIM_TRY(aim_matvec(ctx, xd, yd, nrhs, precision));
   AIM_CUDA_TRY(cudaMemcpyAsync(y_host, yd, bytes, cudaMemcpyDeviceToHost, ctx->stream));

@@ -60,13 +60,20 @@ template <typename C, typename R> AIM_HD inline C cscale(C a, R s) { a.x *= s; a
 template <typename C> AIM_HD inline C cconj(C a) { a.y = -a.y; return a; }
 
 // ---------------------------------------------------------------- plans
+// Exact floor(n / d) for 0 <= n < 2^31 as (umulhi(n, m) + n) >> l.
+struct Div32 {
+  uint32_t m, l, d;
+};
 constexpr int kMaxStages = 16;
 struct FftPlan {
-  int L;                 // transform length
-  int nst;               // number of stages
-  int radix[kMaxStages]; // radix per stage, applied in order
+  int L;                  // transform length
+  int nst;                // number of stages (-1: L is not 2,3,5-smooth)
+  int rad[kMaxStages];    // radix per stage, applied in order
+  int Ns[kMaxStages];     // product of the radices of the earlier stages
+  Div32 dNs[kMaxStages];  // division by Ns
+  Div32 dnb[kMaxStages];  // division by L / rad
 };
-FftPlan make_plan(int L);  // radices from {4, 3, 5, 2}; L must be 2,3,5-smooth
+FftPlan make_plan(int L);  // radices from {4, 3, 5, 2}
 
 // ---------------------------------------------------------------- per-precision device data
 template <typename R> struct PrecData {
@@ -80,6 +87,16 @@ template <typename R> struct PrecData {
   cplx<R>* grid2 = nullptr;       // [B][4][Lz][Ly][nx]
   cplx<R>* xbuf = nullptr;        // [B][N] staging for host/solver conversions
   cplx<R>* ybuf = nullptr;        // [B][N]
+};
+
+// Grids, spectrum and twiddles of the float-float path (AIM_C128); its
+// weights, near entries and vectors are the complex128 ones.
+struct FFData {
+  float4* ghat = nullptr;
+  float4* tw[3] = {nullptr, nullptr, nullptr};
+  float4* grid0 = nullptr;
+  float4* grid1 = nullptr;
+  float4* grid2 = nullptr;
 };
 
 // Per-kernel timing with CUDA events on the context stream (aim_profile).
@@ -131,6 +148,7 @@ struct aim_ctx {
   int device = 0;
   int64_t launches = 0;
   aim::FftPlan plan[3];
+  aim::FftPlan* plan_dev = nullptr;  // device copy of plan[3]
 
   // host copies (inspection, RHS/RCS geometry)
   std::vector<int32_t> h_anchor;  // [N][3] absolute
@@ -160,6 +178,7 @@ struct aim_ctx {
 
   aim::PrecData<double> p64;
   aim::PrecData<float> p32;
+  aim::FFData pff;
   aim::KrylovWork kw;
   aim::Profiler prof;
   int max_rhs = 1;
@@ -185,14 +204,19 @@ int profile_collect(aim_ctx* c);
 void profile_free(aim_ctx* c);
 // setup.cu
 int build_context(aim_ctx* c, const aim_mesh* mesh);
-// matvec.cu
-template <typename R> int matvec(aim_ctx* c, const cplx<R>* x, cplx<R>* y, int nrhs);
+// matvec.cu: y = Z~ x; precision AIM_C64 (float2 vectors) or AIM_C128 /
+// AIM_C128_F64 (double2 vectors).  Allocates the grids of a precision on its
+// first use.
+int matvec(aim_ctx* c, const void* x, void* y, int nrhs, int precision);
+int ensure_grids(aim_ctx* c, int precision);
 int launch_check(aim_ctx* c, const char* what);
 int convert_c128_to_c64(aim_ctx* c, const double2* in, float2* out, int64_t count);
 int convert_c64_to_c128(aim_ctx* c, const float2* in, double2* out, int64_t count);
 // fft.cu
-template <typename R>
-int fft_convolve(aim_ctx* c, PrecData<R>& p, int G);  // grid0 (Q) -> grid0 (Phi), G = 4 * nrhs grids
+// grid0 (Q) -> grid0 (Phi) of each precision, G = 4 * nrhs grids
+int fft_convolve_c64(aim_ctx* c, int G);
+int fft_convolve_c128(aim_ctx* c, int G);
+int fft_convolve_ff(aim_ctx* c, int G);
 int build_ghat(aim_ctx* c);
 // krylov.cu
 int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_solve_info* info);

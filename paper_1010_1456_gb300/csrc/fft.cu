@@ -20,12 +20,29 @@
 // that every global access is a contiguous run of TX complex values.  Ghat is
 // stored as one octant (it is even in each axis) and pre-scaled by 1/(LxLyLz),
 // so the inverse transforms are unnormalised.
+//
+// The butterflies are written once over an arithmetic policy:
+//   P32 complex64 (float2), P64 complex128 (double2) and PFF complex
+//   float-float (float4 = re.hi, re.lo, im.hi, im.lo; about 48 bits, on the
+//   FP32 pipes; see ff.h).  Per-stage index arithmetic uses precomputed
+//   multiply-shift division, so no integer division runs in the kernels.
 #include <cmath>
+#include <cstdint>
 
 #include "common.h"
+#include "ff.h"
 #include "geom.h"
 
 namespace aim {
+
+// ------------------------------------------------------------------ plans
+static Div32 make_div(uint32_t d) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  const uint64_t m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+  return Div32{(uint32_t)m, l, d};
+}
+__device__ __forceinline__ uint32_t qdiv(uint32_t n, const Div32& D) { return (__umulhi(n, D.m) + n) >> D.l; }
 
 FftPlan make_plan(int L) {
   FftPlan p{};
@@ -34,126 +51,186 @@ FftPlan make_plan(int L) {
   int x = L;
   const int order[4] = {4, 3, 5, 2};
   for (int oi = 0; oi < 4; ++oi) {
-    int r = order[oi];
-    while (x % r == 0) {
-      p.radix[p.nst++] = r;
+    const int r = order[oi];
+    while (x % r == 0 && p.nst < kMaxStages) {
+      p.rad[p.nst++] = r;
       x /= r;
     }
   }
-  if (x != 1) p.nst = -1;  // not 2,3,5-smooth
+  if (x != 1) {
+    p.nst = -1;  // not 2,3,5-smooth
+    return p;
+  }
+  int Ns = 1;
+  for (int s = 0; s < p.nst; ++s) {
+    p.Ns[s] = Ns;
+    p.dNs[s] = make_div((uint32_t)Ns);
+    p.dnb[s] = make_div((uint32_t)(L / p.rad[s]));
+    Ns *= p.rad[s];
+  }
   return p;
 }
 
+// ------------------------------------------------------------------ arithmetic policies
+// Real constants are passed as (double value, float hi, float lo) so every
+// policy sees the constant at its own precision, folded at compile time.
+#define AIM_RC(c) (c), (float)(c), (float)((c) - (double)(float)(c))
+
+struct P32 {
+  using S = float2;  // storage
+  using T = float2;  // work
+  static constexpr int kTX = 16;
+  __device__ static T ld(const S& s) { return s; }
+  __device__ static S st(const T& t) { return t; }
+  __device__ static T zero() { return make_float2(0.f, 0.f); }
+  __device__ static T add(T a, T b) { return make_float2(a.x + b.x, a.y + b.y); }
+  __device__ static T sub(T a, T b) { return make_float2(a.x - b.x, a.y - b.y); }
+  __device__ static T mul(T a, T b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+  __device__ static T mulr(T a, double, float c, float) { return make_float2(a.x * c, a.y * c); }
+  __device__ static T half(T a) { return make_float2(0.5f * a.x, 0.5f * a.y); }
+  template <bool INV> __device__ static T mul_mi(T a) { return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x); }
+  __device__ static T conj_if(T w, bool c) { return c ? make_float2(w.x, -w.y) : w; }
+};
+
+struct P64 {
+  using S = double2;
+  using T = double2;
+  static constexpr int kTX = 8;
+  __device__ static T ld(const S& s) { return s; }
+  __device__ static S st(const T& t) { return t; }
+  __device__ static T zero() { return make_double2(0.0, 0.0); }
+  __device__ static T add(T a, T b) { return make_double2(a.x + b.x, a.y + b.y); }
+  __device__ static T sub(T a, T b) { return make_double2(a.x - b.x, a.y - b.y); }
+  __device__ static T mul(T a, T b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+  __device__ static T mulr(T a, double c, float, float) { return make_double2(a.x * c, a.y * c); }
+  __device__ static T half(T a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
+  template <bool INV> __device__ static T mul_mi(T a) { return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x); }
+  __device__ static T conj_if(T w, bool c) { return c ? make_double2(w.x, -w.y) : w; }
+};
+
+struct PFF {
+  using S = float4;
+  using T = cff;
+  static constexpr int kTX = 8;
+  __device__ static T ld(const S& s) { return cff{ff{s.x, s.y}, ff{s.z, s.w}}; }
+  __device__ static S st(const T& t) { return make_float4(t.re.hi, t.re.lo, t.im.hi, t.im.lo); }
+  __device__ static T zero() { return cff{ff{0.f, 0.f}, ff{0.f, 0.f}}; }
+  __device__ static T add(T a, T b) { return cff{ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
+  __device__ static T sub(T a, T b) { return cff{ff_sub(a.re, b.re), ff_sub(a.im, b.im)}; }
+  __device__ static T mul(T a, T b) {
+    return cff{ff_dot2(a.re, b.re, ff_neg(a.im), b.im), ff_dot2(a.re, b.im, a.im, b.re)};
+  }
+  __device__ static T mulr(T a, double, float ch, float cl) {
+    const ff c{ch, cl};
+    return cff{ff_mul(a.re, c), ff_mul(a.im, c)};
+  }
+  __device__ static T half(T a) { return cff{ff{0.5f * a.re.hi, 0.5f * a.re.lo}, ff{0.5f * a.im.hi, 0.5f * a.im.lo}}; }
+  template <bool INV> __device__ static T mul_mi(T a) { return INV ? cff{ff_neg(a.im), a.re} : cff{a.im, ff_neg(a.re)}; }
+  __device__ static T conj_if(T w, bool c) { return c ? cff{w.re, ff_neg(w.im)} : w; }
+};
+
 // ------------------------------------------------------------------ butterflies
-template <typename C, bool INV> __device__ __forceinline__ C mul_mi(C a) {
-  // forward: multiply by -i; inverse: by +i
-  C r;
-  if (!INV) { r.x = a.y; r.y = -a.x; }
-  else { r.x = -a.y; r.y = a.x; }
-  return r;
+template <class P, bool INV> __device__ __forceinline__ void dft2(typename P::T* v) {
+  const typename P::T a = v[0], b = v[1];
+  v[0] = P::add(a, b);
+  v[1] = P::sub(a, b);
+}
+template <class P, bool INV> __device__ __forceinline__ void dft3(typename P::T* v) {
+  using T = typename P::T;
+  const T a = v[0], s = P::add(v[1], v[2]), d = P::sub(v[1], v[2]);
+  const T m = P::sub(a, P::half(s));
+  const T t = P::template mul_mi<INV>(P::mulr(d, AIM_RC(0.86602540378443864676)));  // sin(2 pi / 3)
+  v[0] = P::add(a, s);
+  v[1] = P::add(m, t);
+  v[2] = P::sub(m, t);
+}
+template <class P, bool INV> __device__ __forceinline__ void dft4(typename P::T* v) {
+  using T = typename P::T;
+  const T s02 = P::add(v[0], v[2]), d02 = P::sub(v[0], v[2]);
+  const T s13 = P::add(v[1], v[3]), d13 = P::template mul_mi<INV>(P::sub(v[1], v[3]));
+  v[0] = P::add(s02, s13);
+  v[2] = P::sub(s02, s13);
+  v[1] = P::add(d02, d13);
+  v[3] = P::sub(d02, d13);
+}
+template <class P, bool INV> __device__ __forceinline__ void dft5(typename P::T* v) {
+  using T = typename P::T;
+  const T a0 = v[0];
+  const T t1 = P::add(v[1], v[4]), t2 = P::add(v[2], v[3]);
+  const T t3 = P::sub(v[1], v[4]), t4 = P::sub(v[2], v[3]);
+  // cos(2pi/5), cos(4pi/5), sin(2pi/5), sin(4pi/5)
+  const T b1 = P::add(a0, P::add(P::mulr(t1, AIM_RC(0.30901699437494742410)), P::mulr(t2, AIM_RC(-0.80901699437494742410))));
+  const T b2 = P::add(a0, P::add(P::mulr(t1, AIM_RC(-0.80901699437494742410)), P::mulr(t2, AIM_RC(0.30901699437494742410))));
+  const T u1 = P::add(P::mulr(t3, AIM_RC(0.95105651629515357212)), P::mulr(t4, AIM_RC(0.58778525229247312917)));
+  const T u2 = P::sub(P::mulr(t3, AIM_RC(0.58778525229247312917)), P::mulr(t4, AIM_RC(0.95105651629515357212)));
+  const T e1 = P::template mul_mi<INV>(u1), e2 = P::template mul_mi<INV>(u2);
+  v[0] = P::add(a0, P::add(t1, t2));
+  v[1] = P::add(b1, e1);
+  v[4] = P::sub(b1, e1);
+  v[2] = P::add(b2, e2);
+  v[3] = P::sub(b2, e2);
 }
 
-template <typename R, bool INV> __device__ __forceinline__ void dft2(cplx<R>* v) {
-  cplx<R> a = v[0], b = v[1];
-  v[0] = cadd(a, b);
-  v[1] = csub(a, b);
-}
-template <typename R, bool INV> __device__ __forceinline__ void dft3(cplx<R>* v) {
-  const R h = (R)0.86602540378443864676;  // sin(2 pi / 3)
-  cplx<R> a = v[0], s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
-  cplx<R> m = a;
-  m.x -= (R)0.5 * s.x;
-  m.y -= (R)0.5 * s.y;
-  cplx<R> t = mul_mi<cplx<R>, INV>(cscale(d, h));
-  v[0] = cadd(a, s);
-  v[1] = cadd(m, t);
-  v[2] = csub(m, t);
-}
-template <typename R, bool INV> __device__ __forceinline__ void dft4(cplx<R>* v) {
-  cplx<R> s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-  cplx<R> s13 = cadd(v[1], v[3]), d13 = mul_mi<cplx<R>, INV>(csub(v[1], v[3]));
-  v[0] = cadd(s02, s13);
-  v[2] = csub(s02, s13);
-  v[1] = cadd(d02, d13);
-  v[3] = csub(d02, d13);
-}
-template <typename R, bool INV> __device__ __forceinline__ void dft5(cplx<R>* v) {
-  const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;  // cos(2pi/5), cos(4pi/5)
-  const R s1 = (R)0.95105651629515357212, s2 = (R)0.58778525229247312917;   // sin(2pi/5), sin(4pi/5)
-  cplx<R> a0 = v[0];
-  cplx<R> t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
-  cplx<R> t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
-  cplx<R> b1, b2, e1, e2;
-  b1.x = a0.x + c1 * t1.x + c2 * t2.x;
-  b1.y = a0.y + c1 * t1.y + c2 * t2.y;
-  b2.x = a0.x + c2 * t1.x + c1 * t2.x;
-  b2.y = a0.y + c2 * t1.y + c1 * t2.y;
-  cplx<R> u1, u2;
-  u1.x = s1 * t3.x + s2 * t4.x;
-  u1.y = s1 * t3.y + s2 * t4.y;
-  u2.x = s2 * t3.x - s1 * t4.x;
-  u2.y = s2 * t3.y - s1 * t4.y;
-  e1 = mul_mi<cplx<R>, INV>(u1);
-  e2 = mul_mi<cplx<R>, INV>(u2);
-  v[0] = cadd(a0, cadd(t1, t2));
-  v[1] = cadd(b1, e1);
-  v[4] = csub(b1, e1);
-  v[2] = cadd(b2, e2);
-  v[3] = csub(b2, e2);
-}
-
-// One Stockham stage over `count` independent pencils of length L.
-// Element p of pencil c lives at buf[idx(p, c)] with idx = p*pstride + c*cstride.
-template <typename R, bool INV, int RAD>
-__device__ __forceinline__ void stage_r(const cplx<R>* __restrict__ src, cplx<R>* __restrict__ dst, int L, int Ns,
-                                        int count, int pstride, int cstride, const cplx<R>* __restrict__ tw) {
+// One Stockham stage over `count` pencils of length L in shared memory.
+// COLS: element p of pencil c at buf[p * kTX + c] (column tiles, count = kTX);
+// otherwise at buf[c * L + p] (row tiles).
+template <class P, bool INV, int RAD, bool COLS>
+__device__ __forceinline__ void stage_r(const typename P::S* __restrict__ src, typename P::S* __restrict__ dst,
+                                        const FftPlan& pl, int s, int count, const typename P::S* __restrict__ tw) {
+  using T = typename P::T;
+  const int L = pl.L;
   const int nb = L / RAD;
+  const int Ns = pl.Ns[s];
   const int tstep = L / (Ns * RAD);
-  for (int item = threadIdx.x; item < nb * count; item += blockDim.x) {
+  const Div32 dNs = pl.dNs[s], dnb = pl.dnb[s];
+  const int total = nb * count;
+  for (int item = threadIdx.x; item < total; item += blockDim.x) {
     int c, j;
-    if (cstride == 1) { c = item % count; j = item / count; }  // column tiles: adjacent threads adjacent columns
-    else { j = item % nb; c = item / nb; }                     // row tiles: adjacent threads adjacent j
-    const int k = j % Ns;
-    cplx<R> v[RAD];
+    if (COLS) {
+      c = item & (P::kTX - 1);  // count == kTX, a power of two
+      j = item / P::kTX;
+    } else {
+      c = (int)qdiv((uint32_t)item, dnb);
+      j = item - c * nb;
+    }
+    const int q = (int)qdiv((uint32_t)j, dNs);
+    const int k = j - q * Ns;
+    T v[RAD];
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
-      cplx<R> a = src[(j + r * nb) * pstride + c * cstride];
-      if (r > 0 && Ns > 1) {
-        cplx<R> w = tw[r * k * tstep];  // r k tstep < L
-        if (INV) w.y = -w.y;
-        a = cmul(a, w);
-      }
+      const int p = j + r * nb;
+      T a = P::ld(src[COLS ? p * P::kTX + c : c * L + p]);
+      if (r > 0 && Ns > 1) a = P::mul(a, P::conj_if(P::ld(tw[r * k * tstep]), INV));  // r k tstep < L
       v[r] = a;
     }
-    if (RAD == 2) dft2<R, INV>(v);
-    if (RAD == 3) dft3<R, INV>(v);
-    if (RAD == 4) dft4<R, INV>(v);
-    if (RAD == 5) dft5<R, INV>(v);
-    const int idxD = (j / Ns) * Ns * RAD + k;
+    if (RAD == 2) dft2<P, INV>(v);
+    if (RAD == 3) dft3<P, INV>(v);
+    if (RAD == 4) dft4<P, INV>(v);
+    if (RAD == 5) dft5<P, INV>(v);
+    const int idxD = q * Ns * RAD + k;
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) dst[(idxD + r * Ns) * pstride + c * cstride] = v[r];
+    for (int r = 0; r < RAD; ++r) {
+      const int p = idxD + r * Ns;
+      dst[COLS ? p * P::kTX + c : c * L + p] = P::st(v[r]);
+    }
   }
 }
 
 // Full transform in shared memory; returns the buffer that holds the result.
-template <typename R, bool INV>
-__device__ cplx<R>* stockham(cplx<R>* b0, cplx<R>* b1, const FftPlan& plan, int count, int pstride, int cstride,
-                             const cplx<R>* __restrict__ tw) {
-  int Ns = 1;
-  const int L = plan.L;
-  for (int s = 0; s < plan.nst; ++s) {
-    const int rad = plan.radix[s];
-    switch (rad) {
-      case 2: stage_r<R, INV, 2>(b0, b1, L, Ns, count, pstride, cstride, tw); break;
-      case 3: stage_r<R, INV, 3>(b0, b1, L, Ns, count, pstride, cstride, tw); break;
-      case 4: stage_r<R, INV, 4>(b0, b1, L, Ns, count, pstride, cstride, tw); break;
-      default: stage_r<R, INV, 5>(b0, b1, L, Ns, count, pstride, cstride, tw); break;
+template <class P, bool INV, bool COLS>
+__device__ typename P::S* stockham(typename P::S* b0, typename P::S* b1, const FftPlan& pl, int count,
+                                   const typename P::S* __restrict__ tw) {
+  for (int s = 0; s < pl.nst; ++s) {
+    switch (pl.rad[s]) {
+      case 2: stage_r<P, INV, 2, COLS>(b0, b1, pl, s, count, tw); break;
+      case 3: stage_r<P, INV, 3, COLS>(b0, b1, pl, s, count, tw); break;
+      case 4: stage_r<P, INV, 4, COLS>(b0, b1, pl, s, count, tw); break;
+      default: stage_r<P, INV, 5, COLS>(b0, b1, pl, s, count, tw); break;
     }
     __syncthreads();
-    cplx<R>* t = b0;
+    typename P::S* t = b0;
     b0 = b1;
     b1 = t;
-    Ns *= rad;
   }
   return b0;
 }
@@ -164,183 +241,188 @@ struct StridedArgs {
   int X, A;         // contiguous extent, other-axis extent
   long long sG_in, sA_in, sP_in;
   long long sG_out, sA_out, sP_out;
-  FftPlan plan;
 };
 
-template <typename R> AIM_HD constexpr int tile_x() { return sizeof(R) == 4 ? 16 : 8; }
-
-template <typename R, bool INV>
-__global__ void __launch_bounds__(256) fft_strided(const cplx<R>* __restrict__ in, cplx<R>* __restrict__ out,
-                                                   StridedArgs a, const cplx<R>* __restrict__ tw) {
-  constexpr int TX = tile_x<R>();
+template <class P, bool INV>
+__global__ void __launch_bounds__(256) fft_strided(const typename P::S* __restrict__ in, typename P::S* __restrict__ out,
+                                                   StridedArgs a, const FftPlan* __restrict__ plan,
+                                                   const typename P::S* __restrict__ tw) {
+  using S = typename P::S;
+  constexpr int TX = P::kTX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* b0 = reinterpret_cast<cplx<R>*>(smem_raw);
-  const int L = a.plan.L;
-  cplx<R>* b1 = b0 + L * TX;
+  const FftPlan& pl = *plan;
+  S* b0 = reinterpret_cast<S*>(smem_raw);
+  const int L = pl.L;
+  S* b1 = b0 + L * TX;
   const int x0 = blockIdx.x * TX;
   const int ia = blockIdx.y;
   const long long g = blockIdx.z;
-  const cplx<R>* src = in + g * a.sG_in + ia * a.sA_in + x0;
+  const S* src = in + g * a.sG_in + ia * a.sA_in + x0;
   for (int e = threadIdx.x; e < L * TX; e += blockDim.x) {
-    int p = e / TX, c = e % TX;
-    cplx<R> v = cmake<cplx<R>>(0.0, 0.0);
+    const int p = e / TX, c = e & (TX - 1);
+    S v = P::st(P::zero());
     if (p < a.n_in && x0 + c < a.X) v = src[p * a.sP_in + c];
     b0[e] = v;
   }
   __syncthreads();
-  cplx<R>* res = stockham<R, INV>(b0, b1, a.plan, TX, TX, 1, tw);
-  cplx<R>* dst = out + g * a.sG_out + ia * a.sA_out + x0;
+  S* res = stockham<P, INV, true>(b0, b1, pl, TX, tw);
+  S* dst = out + g * a.sG_out + ia * a.sA_out + x0;
   for (int e = threadIdx.x; e < a.n_out * TX; e += blockDim.x) {
-    int p = e / TX, c = e % TX;
+    const int p = e / TX, c = e & (TX - 1);
     if (x0 + c < a.X) dst[p * a.sP_out + c] = res[e];
   }
 }
 
 // ------------------------------------------------------------------ x pass
 struct XArgs {
-  int nx;        // samples per row kept (read and written)
-  int rows_y;    // Ly
-  int rows_z;    // Lz
-  int G;         // grids
-  int TG;        // grids per shared-memory tile
-  long long sG;  // grid stride (elements)
+  int nx;          // samples per row kept (read and written)
+  int rows_y;      // Ly
+  int rows_z;      // Lz
+  int G;           // grids
+  int TG;          // grids per shared-memory tile
+  long long sG;    // grid stride (elements)
   int hx, hy, hz;  // octant extents of Ghat
-  FftPlan plan;
 };
 
-// mode 0: forward, times Ghat, inverse (keep nx); mode 1: forward only on full rows.
-template <typename R, int MODE>
-__global__ void __launch_bounds__(256) fft_x(cplx<R>* __restrict__ buf, XArgs a, const cplx<R>* __restrict__ ghat,
-                                             const cplx<R>* __restrict__ tw) {
+// MODE 0: forward, times Ghat, inverse (keep nx); MODE 1: forward only on full rows.
+template <class P, int MODE>
+__global__ void __launch_bounds__(256) fft_x(typename P::S* __restrict__ buf, XArgs a, const FftPlan* __restrict__ plan,
+                                             const typename P::S* __restrict__ ghat, const typename P::S* __restrict__ tw) {
+  using S = typename P::S;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = a.plan.L;
-  cplx<R>* gr = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* b0 = gr + L;
-  cplx<R>* b1 = b0 + a.TG * L;
+  const FftPlan& pl = *plan;
+  const int L = pl.L;
+  S* gr = reinterpret_cast<S*>(smem_raw);
+  S* b0 = gr + L;
+  S* b1 = b0 + a.TG * L;
   const int ky = blockIdx.x, kz = blockIdx.y;
   const long long row = ((long long)kz * a.rows_y + ky) * a.nx;
   if (MODE == 0) {
     const int iy = min(ky, a.rows_y - ky), iz = min(kz, a.rows_z - kz);
-    const cplx<R>* grow = ghat + ((long long)iz * a.hy + iy) * a.hx;
+    const S* grow = ghat + ((long long)iz * a.hy + iy) * a.hx;
     for (int e = threadIdx.x; e < L; e += blockDim.x) gr[e] = grow[min(e, L - e)];
   }
   for (int g0 = 0; g0 < a.G; g0 += a.TG) {
     const int ng = min(a.TG, a.G - g0);
     __syncthreads();
-    for (int e = threadIdx.x; e < ng * L; e += blockDim.x) {
-      int c = e / L, p = e % L;
-      cplx<R> v = cmake<cplx<R>>(0.0, 0.0);
-      if (p < a.nx) v = buf[(g0 + c) * a.sG + row + p];
-      b0[e] = v;
-    }
+    for (int c = 0; c < ng; ++c)
+      for (int p = threadIdx.x; p < L; p += blockDim.x) {
+        S v = P::st(P::zero());
+        if (p < a.nx) v = buf[(g0 + c) * a.sG + row + p];
+        b0[c * L + p] = v;
+      }
     __syncthreads();
-    cplx<R>* res = stockham<R, false>(b0, b1, a.plan, ng, 1, L, tw);
+    S* res = stockham<P, false, false>(b0, b1, pl, ng, tw);
     if (MODE == 0) {
-      cplx<R>* oth = (res == b0) ? b1 : b0;
-      for (int e = threadIdx.x; e < ng * L; e += blockDim.x) res[e] = cmul(res[e], gr[e % L]);
+      S* oth = (res == b0) ? b1 : b0;
+      for (int c = 0; c < ng; ++c)
+        for (int p = threadIdx.x; p < L; p += blockDim.x) res[c * L + p] = P::st(P::mul(P::ld(res[c * L + p]), P::ld(gr[p])));
       __syncthreads();
-      res = stockham<R, true>(res, oth, a.plan, ng, 1, L, tw);
+      res = stockham<P, true, false>(res, oth, pl, ng, tw);
     }
-    for (int e = threadIdx.x; e < ng * a.nx; e += blockDim.x) {
-      int c = e / a.nx, p = e % a.nx;
-      buf[(g0 + c) * a.sG + row + p] = res[c * L + p];
-    }
+    for (int c = 0; c < ng; ++c)
+      for (int p = threadIdx.x; p < a.nx; p += blockDim.x) buf[(g0 + c) * a.sG + row + p] = res[c * L + p];
   }
 }
 
 // ------------------------------------------------------------------ drivers
-template <typename R> static size_t strided_smem(int L) { return 2ull * L * tile_x<R>() * sizeof(cplx<R>); }
-
-template <typename R, bool INV>
-static int launch_strided(aim_ctx* c, const char* name, const cplx<R>* in, cplx<R>* out, const StridedArgs& a, int G,
-                          const cplx<R>* tw) {
-  constexpr int TX = tile_x<R>();
-  size_t sm = strided_smem<R>(a.plan.L);
+template <class P, bool INV>
+static int launch_strided(aim_ctx* c, const char* name, const typename P::S* in, typename P::S* out,
+                          const StridedArgs& a, int G, const FftPlan* plan_dev, int L, const typename P::S* tw) {
+  constexpr int TX = P::kTX;
+  const size_t sm = 2ull * L * TX * sizeof(typename P::S);
+  if (sm > 227 * 1024) {
+    set_error(std::string(name) + ": padded length too large for shared memory");
+    return AIM_EINVAL;
+  }
   // once per template instance (thread-safe static initialisation)
   static const cudaError_t attr =
-      cudaFuncSetAttribute(fft_strided<R, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(fft_strided<P, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   AIM_CUDA_TRY(attr);
   dim3 grid((a.X + TX - 1) / TX, a.A, G);
-  AIM_LAUNCH(c, name, fft_strided<R, INV><<<grid, 256, sm, c->stream>>>(in, out, a, tw));
-  return launch_check(c, "fft_strided");
+  AIM_LAUNCH(c, name, fft_strided<P, INV><<<grid, 256, sm, c->stream>>>(in, out, a, plan_dev, tw));
+  return launch_check(c, name);
 }
 
-template <typename R, int MODE>
-static int launch_x(aim_ctx* c, const char* name, cplx<R>* buf, XArgs a, const cplx<R>* ghat, const cplx<R>* tw) {
-  const int L = a.plan.L;
+template <class P, int MODE>
+static int launch_x(aim_ctx* c, const char* name, typename P::S* buf, XArgs a, const FftPlan* plan_dev, int L,
+                    const typename P::S* ghat, const typename P::S* tw) {
+  using S = typename P::S;
   // grids per tile: keep shared memory under ~100 KB so two blocks fit an SM
-  int TG = (int)((100 * 1024) / (2ull * L * sizeof(cplx<R>)) );
+  int TG = (int)((100 * 1024) / (2ull * L * sizeof(S)));
   TG = TG < 1 ? 1 : TG;
   TG = TG > a.G ? a.G : TG;
   TG = TG > 16 ? 16 : TG;
   a.TG = TG;
-  size_t sm = (size_t)(2 * TG + 1) * L * sizeof(cplx<R>);
+  const size_t sm = (size_t)(2 * TG + 1) * L * sizeof(S);
   if (sm > 227 * 1024) {
-    set_error("fft_x: padded x length too large for shared memory");
+    set_error(std::string(name) + ": padded x length too large for shared memory");
     return AIM_EINVAL;
   }
   static const cudaError_t attr =
-      cudaFuncSetAttribute(fft_x<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(fft_x<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   AIM_CUDA_TRY(attr);
   dim3 grid(a.rows_y, a.rows_z);
-  AIM_LAUNCH(c, name, fft_x<R, MODE><<<grid, 256, sm, c->stream>>>(buf, a, ghat, tw));
-  return launch_check(c, "fft_x");
+  AIM_LAUNCH(c, name, fft_x<P, MODE><<<grid, 256, sm, c->stream>>>(buf, a, plan_dev, ghat, tw));
+  return launch_check(c, name);
 }
 
-template <typename R>
-int fft_convolve(aim_ctx* c, PrecData<R>& p, int G) {
+template <class P>
+static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P::S* g2, const typename P::S* ghat,
+                    typename P::S* const* tw, int G) {
   const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
   const int Lx = c->L[0], Ly = c->L[1], Lz = c->L[2];
-  // z forward: grid0 [G][nz][ny][nx] -> grid1 [G][Lz][ny][nx]
-  {
+  const FftPlan* pd = c->plan_dev;
+  {  // z forward: g0 [G][nz][ny][nx] -> g1 [G][Lz][ny][nx]
     StridedArgs a{};
     a.n_in = nz; a.n_out = Lz; a.X = nx; a.A = ny;
     a.sG_in = (long long)nz * ny * nx; a.sA_in = nx; a.sP_in = (long long)ny * nx;
     a.sG_out = (long long)Lz * ny * nx; a.sA_out = nx; a.sP_out = (long long)ny * nx;
-    a.plan = c->plan[2];
-    AIM_TRY((launch_strided<R, false>(c, "fft_z_fwd", p.grid0, p.grid1, a, G, p.tw[2])));
+    AIM_TRY((launch_strided<P, false>(c, "fft_z_fwd", g0, g1, a, G, pd + 2, Lz, tw[2])));
   }
-  // y forward: grid1 [G][Lz][ny][nx] -> grid2 [G][Lz][Ly][nx]
-  {
+  {  // y forward: g1 [G][Lz][ny][nx] -> g2 [G][Lz][Ly][nx]
     StridedArgs a{};
     a.n_in = ny; a.n_out = Ly; a.X = nx; a.A = Lz;
     a.sG_in = (long long)Lz * ny * nx; a.sA_in = (long long)ny * nx; a.sP_in = nx;
     a.sG_out = (long long)Lz * Ly * nx; a.sA_out = (long long)Ly * nx; a.sP_out = nx;
-    a.plan = c->plan[1];
-    AIM_TRY((launch_strided<R, false>(c, "fft_y_fwd", p.grid1, p.grid2, a, G, p.tw[1])));
+    AIM_TRY((launch_strided<P, false>(c, "fft_y_fwd", g1, g2, a, G, pd + 1, Ly, tw[1])));
   }
-  // x: forward, times Ghat, inverse, in place on grid2
-  {
+  {  // x: forward, times Ghat, inverse, in place on g2
     XArgs a{};
     a.nx = nx; a.rows_y = Ly; a.rows_z = Lz; a.G = G;
     a.sG = (long long)Lz * Ly * nx;
     a.hx = Lx / 2 + 1; a.hy = Ly / 2 + 1; a.hz = Lz / 2 + 1;
-    a.plan = c->plan[0];
-    AIM_TRY((launch_x<R, 0>(c, "fft_x_conv", p.grid2, a, p.ghat, p.tw[0])));
+    AIM_TRY((launch_x<P, 0>(c, "fft_x_conv", g2, a, pd + 0, Lx, ghat, tw[0])));
   }
-  // y inverse: grid2 -> grid1 [G][Lz][ny][nx]
-  {
+  {  // y inverse: g2 -> g1 [G][Lz][ny][nx]
     StridedArgs a{};
     a.n_in = Ly; a.n_out = ny; a.X = nx; a.A = Lz;
     a.sG_in = (long long)Lz * Ly * nx; a.sA_in = (long long)Ly * nx; a.sP_in = nx;
     a.sG_out = (long long)Lz * ny * nx; a.sA_out = (long long)ny * nx; a.sP_out = nx;
-    a.plan = c->plan[1];
-    AIM_TRY((launch_strided<R, true>(c, "fft_y_inv", p.grid2, p.grid1, a, G, p.tw[1])));
+    AIM_TRY((launch_strided<P, true>(c, "fft_y_inv", g2, g1, a, G, pd + 1, Ly, tw[1])));
   }
-  // z inverse: grid1 -> grid0 [G][nz][ny][nx]
-  {
+  {  // z inverse: g1 -> g0 [G][nz][ny][nx]
     StridedArgs a{};
     a.n_in = Lz; a.n_out = nz; a.X = nx; a.A = ny;
     a.sG_in = (long long)Lz * ny * nx; a.sA_in = nx; a.sP_in = (long long)ny * nx;
     a.sG_out = (long long)nz * ny * nx; a.sA_out = nx; a.sP_out = (long long)ny * nx;
-    a.plan = c->plan[2];
-    AIM_TRY((launch_strided<R, true>(c, "fft_z_inv", p.grid1, p.grid0, a, G, p.tw[2])));
+    AIM_TRY((launch_strided<P, true>(c, "fft_z_inv", g1, g0, a, G, pd + 2, Lz, tw[2])));
   }
   return AIM_OK;
 }
 
-template int fft_convolve<float>(aim_ctx*, PrecData<float>&, int);
-template int fft_convolve<double>(aim_ctx*, PrecData<double>&, int);
+int fft_convolve_c64(aim_ctx* c, int G) {
+  PrecData<float>& p = c->p32;
+  return convolve<P32>(c, p.grid0, p.grid1, p.grid2, p.ghat, p.tw, G);
+}
+int fft_convolve_c128(aim_ctx* c, int G) {
+  PrecData<double>& p = c->p64;
+  return convolve<P64>(c, p.grid0, p.grid1, p.grid2, p.ghat, p.tw, G);
+}
+int fft_convolve_ff(aim_ctx* c, int G) {
+  FFData& p = c->pff;
+  return convolve<PFF>(c, p.grid0, p.grid1, p.grid2, p.ghat, p.tw, G);
+}
 
 // ------------------------------------------------------------------ Ghat
 // Circulant embedding of G_h on the padded grid: per axis, index i maps to
@@ -366,7 +448,8 @@ __global__ void sample_green(double2* g, int Lx, int Ly, int Lz, int nx, int ny,
   }
 }
 
-__global__ void extract_octant(const double2* full, double2* oct64, float2* oct32, int Lx, int Ly, int Lz, double scale) {
+__global__ void extract_octant(const double2* full, double2* oct64, float2* oct32, float4* octff, int Lx, int Ly,
+                               int Lz, double scale) {
   int hx = Lx / 2 + 1, hy = Ly / 2 + 1, hz = Lz / 2 + 1;
   long long total = (long long)hx * hy * hz;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
@@ -378,6 +461,8 @@ __global__ void extract_octant(const double2* full, double2* oct64, float2* oct3
     v.y *= scale;
     oct64[e] = v;
     oct32[e] = make_float2((float)v.x, (float)v.y);
+    const ff re = ff_from_double(v.x), im = ff_from_double(v.y);
+    octff[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
   }
 }
 
@@ -387,26 +472,26 @@ int build_ghat(aim_ctx* c) {
   double2 *a = nullptr, *b = nullptr;
   AIM_CUDA_TRY(cudaMallocAsync(&a, total * sizeof(double2), c->stream));
   AIM_CUDA_TRY(cudaMallocAsync(&b, total * sizeof(double2), c->stream));
-  AIM_LAUNCH(c, "sample_green", sample_green<<<1024, 256, 0, c->stream>>>(a, Lx, Ly, Lz, c->n[0], c->n[1], c->n[2], c->k, c->h));
+  AIM_LAUNCH(c, "sample_green",
+             sample_green<<<1024, 256, 0, c->stream>>>(a, Lx, Ly, Lz, c->n[0], c->n[1], c->n[2], c->k, c->h));
   AIM_TRY(launch_check(c, "sample_green"));
-  // z: full transform a -> b ; y: b -> a ; x: rows of a in place
+  // z: full transform a -> b ; y: b -> a ; x: rows of a in place (FP64)
   StridedArgs s{};
   s.n_in = Lz; s.n_out = Lz; s.X = Lx; s.A = Ly;
   s.sG_in = total; s.sA_in = Lx; s.sP_in = (long long)Ly * Lx;
   s.sG_out = total; s.sA_out = Lx; s.sP_out = (long long)Ly * Lx;
-  s.plan = c->plan[2];
-  AIM_TRY((launch_strided<double, false>(c, "ghat_z", a, b, s, 1, c->p64.tw[2])));
+  AIM_TRY((launch_strided<P64, false>(c, "ghat_z", a, b, s, 1, c->plan_dev + 2, Lz, c->p64.tw[2])));
   s.n_in = Ly; s.n_out = Ly; s.X = Lx; s.A = Lz;
   s.sA_in = (long long)Ly * Lx; s.sP_in = Lx;
   s.sA_out = (long long)Ly * Lx; s.sP_out = Lx;
-  s.plan = c->plan[1];
-  AIM_TRY((launch_strided<double, false>(c, "ghat_y", b, a, s, 1, c->p64.tw[1])));
+  AIM_TRY((launch_strided<P64, false>(c, "ghat_y", b, a, s, 1, c->plan_dev + 1, Ly, c->p64.tw[1])));
   XArgs x{};
   x.nx = Lx; x.rows_y = Ly; x.rows_z = Lz; x.G = 1; x.sG = total;
   x.hx = Lx / 2 + 1; x.hy = Ly / 2 + 1; x.hz = Lz / 2 + 1;
-  x.plan = c->plan[0];
-  AIM_TRY((launch_x<double, 1>(c, "ghat_x", a, x, nullptr, c->p64.tw[0])));
-  AIM_LAUNCH(c, "extract_octant", extract_octant<<<1024, 256, 0, c->stream>>>(a, c->p64.ghat, c->p32.ghat, Lx, Ly, Lz, 1.0 / (double)total));
+  AIM_TRY((launch_x<P64, 1>(c, "ghat_x", a, x, c->plan_dev + 0, Lx, nullptr, c->p64.tw[0])));
+  AIM_LAUNCH(c, "extract_octant",
+             extract_octant<<<1024, 256, 0, c->stream>>>(a, c->p64.ghat, c->p32.ghat, c->pff.ghat, Lx, Ly, Lz,
+                                                         1.0 / (double)total));
   AIM_TRY(launch_check(c, "extract_octant"));
   AIM_CUDA_TRY(cudaFreeAsync(a, c->stream));
   AIM_CUDA_TRY(cudaFreeAsync(b, c->stream));

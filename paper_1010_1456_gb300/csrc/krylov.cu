@@ -337,12 +337,12 @@ struct Solver {
     if (precision == AIM_C64) {
       AIM_LAUNCH(c, "k_precond", k_precond<float><<<vgrid(), 256, 0, st>>>(Vcol(j), c->dinv64, c->p32.xbuf, N, ldV()));
       AIM_TRY(chk("k_precond"));
-      AIM_TRY(matvec<float>(c, c->p32.xbuf, c->p32.ybuf, B));
+      AIM_TRY(matvec(c, c->p32.xbuf, c->p32.ybuf, B, AIM_C64));
       return convert_c64_to_c128(c, c->p32.ybuf, k.w, (int64_t)B * N);
     }
     AIM_LAUNCH(c, "k_precond", k_precond<double><<<vgrid(), 256, 0, st>>>(Vcol(j), c->dinv64, c->p64.xbuf, N, ldV()));
     AIM_TRY(chk("k_precond"));
-    return matvec<double>(c, c->p64.xbuf, k.w, B);
+    return matvec(c, c->p64.xbuf, k.w, B, precision);
   }
 
   int orthogonalise(int j) {
@@ -369,6 +369,7 @@ int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_so
   KrylovWork& k = c->kw;
   const int N = c->N, m = k.m;
   const int prec = c->opts.precision;
+  const int exact = prec == AIM_C128_F64 ? AIM_C128_F64 : AIM_C128;  // FP64-accurate product for true residuals
   const int check = std::max(1, c->opts.check_every);
   std::vector<int> act(nrhs, 1);
   std::vector<double> bn(nrhs), rel(nrhs, 1.0);
@@ -390,7 +391,7 @@ int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_so
       AIM_LAUNCH(c, "k_residual", k_residual<<<s.vgrid(), 256, 0, c->stream>>>(V, X, k.r, N, k.active));  // X = 0: r = V
       AIM_TRY(s.chk("k_residual"));
     } else {
-      AIM_TRY(matvec<double>(c, X, k.w, nrhs));
+      AIM_TRY(matvec(c, X, k.w, nrhs, exact));
       AIM_LAUNCH(c, "k_residual", k_residual<<<s.vgrid(), 256, 0, c->stream>>>(V, k.w, k.r, N, k.active));
       AIM_TRY(s.chk("k_residual"));
     }

@@ -11,9 +11,15 @@
 // entries, built at setup, so it needs no atomics and is deterministic.  The
 // interpolation and the near row of a basis function are handled by one
 // 8-lane group: the lanes split the stencil nodes and the near entries and
-// reduce with warp shuffles.  FP32 (complex64) or FP64 (complex128) end to
-// end, accumulating in the same precision.
+// reduce with warp shuffles.
+//
+// Modes: M32 (complex64, FP32 accumulation), M64 (complex128 throughout) and
+// MFF (complex128 vectors, FP64 weights and accumulation, grids stored as
+// float-float for the FFT passes).
+#include <algorithm>
+
 #include "common.h"
+#include "ff.h"
 #include "geom.h"
 
 namespace aim {
@@ -26,6 +32,30 @@ int launch_check(aim_ctx* c, const char* what) {
   }
   return AIM_OK;
 }
+
+struct M32 {
+  using R = float;
+  using S = float2;
+  __device__ static S put(float2 v) { return v; }
+  __device__ static float2 get(const S& s) { return s; }
+};
+struct M64 {
+  using R = double;
+  using S = double2;
+  __device__ static S put(double2 v) { return v; }
+  __device__ static double2 get(const S& s) { return s; }
+};
+struct MFF {
+  using R = double;
+  using S = float4;
+  __device__ static S put(double2 v) {
+    const ff re = ff_from_double(v.x), im = ff_from_double(v.y);
+    return make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+  __device__ static double2 get(const S& s) {
+    return make_double2((double)s.x + (double)s.y, (double)s.z + (double)s.w);
+  }
+};
 
 // Four projection weights of one entry (x, y, z, charge).
 template <typename R> struct W4 {
@@ -41,39 +71,46 @@ __device__ __forceinline__ W4<double> load_w4(const double* p, int e) {
   return W4<double>{a.x, a.y, b.x, b.y};
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256) proj_gather(const cplx<R>* __restrict__ x, cplx<R>* __restrict__ Q,
+template <class MD>
+__global__ void __launch_bounds__(256) proj_gather(const cplx<typename MD::R>* __restrict__ x, typename MD::S* __restrict__ Q,
                                                    const int32_t* __restrict__ ptr, const int32_t* __restrict__ mm,
-                                                   const R* __restrict__ w, int N, long long Nc, int nrhs) {
+                                                   const typename MD::R* __restrict__ w, int N, long long Nc, int nrhs) {
+  using R = typename MD::R;
+  using C = cplx<R>;
   for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < Nc; u += (long long)gridDim.x * blockDim.x) {
     const int e0 = ptr[u], e1 = ptr[u + 1];
     for (int b = 0; b < nrhs; ++b) {
-      cplx<R> a0 = cmake<cplx<R>>(0, 0), a1 = a0, a2 = a0, a3 = a0;
-      const cplx<R>* xb = x + (long long)b * N;
+      C a0 = cmake<C>(0, 0), a1 = a0, a2 = a0, a3 = a0;
+      const C* xb = x + (long long)b * N;
       for (int e = e0; e < e1; ++e) {
         const W4<R> ww = load_w4(w, e);
-        const cplx<R> xv = xb[mm[e]];
+        const C xv = xb[mm[e]];
         a0.x += ww.x * xv.x; a0.y += ww.x * xv.y;
         a1.x += ww.y * xv.x; a1.y += ww.y * xv.y;
         a2.x += ww.z * xv.x; a2.y += ww.z * xv.y;
         a3.x += ww.w * xv.x; a3.y += ww.w * xv.y;
       }
-      cplx<R>* Qb = Q + (long long)b * 4 * Nc;
-      Qb[u] = a0;
-      Qb[Nc + u] = a1;
-      Qb[2 * Nc + u] = a2;
-      Qb[3 * Nc + u] = a3;
+      typename MD::S* Qb = Q + (long long)b * 4 * Nc;
+      Qb[u] = MD::put(a0);
+      Qb[Nc + u] = MD::put(a1);
+      Qb[2 * Nc + u] = MD::put(a2);
+      Qb[3 * Nc + u] = MD::put(a3);
     }
   }
 }
 
 // 8 lanes per basis function.
-template <typename R, int M>
-__global__ void __launch_bounds__(256) interp_near(const cplx<R>* __restrict__ Phi, const cplx<R>* __restrict__ x,
-                                                   cplx<R>* __restrict__ y, const R* __restrict__ lam,
+template <class MD, int M>
+__global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restrict__ Phi,
+                                                   const cplx<typename MD::R>* __restrict__ x,
+                                                   cplx<typename MD::R>* __restrict__ y,
+                                                   const typename MD::R* __restrict__ lam,
                                                    const int32_t* __restrict__ base, const int32_t* __restrict__ nptr,
-                                                   const int32_t* __restrict__ ncol, const cplx<R>* __restrict__ nval,
-                                                   int N, long long Nc, int nx, int ny, int nrhs, R fvec, R frho) {
+                                                   const int32_t* __restrict__ ncol,
+                                                   const cplx<typename MD::R>* __restrict__ nval, int N, long long Nc,
+                                                   int nx, int ny, int nrhs, typename MD::R fvec, typename MD::R frho) {
+  using R = typename MD::R;
+  using C = cplx<R>;
   constexpr int P = M + 1;
   constexpr int S = P * P * P;
   const int lane = threadIdx.x & 7;
@@ -84,29 +121,30 @@ __global__ void __launch_bounds__(256) interp_near(const cplx<R>* __restrict__ P
   const R* lm = lam + (long long)mm * 4 * S;
   const int r0 = nptr[mm], r1 = nptr[mm + 1];
   for (int b = 0; b < nrhs; ++b) {
-    const cplx<R>* Pb = Phi + (long long)b * 4 * Nc;
-    cplx<R> av = cmake<cplx<R>>(0, 0), ar = av, an = av;
+    const typename MD::S* Pb = Phi + (long long)b * 4 * Nc;
+    C av = cmake<C>(0, 0), ar = av, an = av;
     for (int s = lane; s < S; s += 8) {
       const int i = s % P, j = (s / P) % P, kk = s / (P * P);
       const long long node = b0 + ((long long)kk * ny + j) * nx + i;
-      const cplx<R> px = Pb[node], py = Pb[Nc + node], pz = Pb[2 * Nc + node], pr = Pb[3 * Nc + node];
+      const C px = MD::get(Pb[node]), py = MD::get(Pb[Nc + node]), pz = MD::get(Pb[2 * Nc + node]),
+              pr = MD::get(Pb[3 * Nc + node]);
       const R wx = lm[s], wy = lm[S + s], wz = lm[2 * S + s], wr = lm[3 * S + s];
       av.x += wx * px.x + wy * py.x + wz * pz.x;
       av.y += wx * px.y + wy * py.y + wz * pz.y;
       ar.x += wr * pr.x;
       ar.y += wr * pr.y;
     }
-    const cplx<R>* xb = x + (long long)b * N;
+    const C* xb = x + (long long)b * N;
     for (int e = r0 + lane; e < r1; e += 8) {
-      const cplx<R> v = nval[e], xv = xb[ncol[e]];
+      const C v = nval[e], xv = xb[ncol[e]];
       an.x += v.x * xv.x - v.y * xv.y;
       an.y += v.x * xv.y + v.y * xv.x;
     }
     // grid part: j (fvec av - frho ar)  with fvec = k eta, frho = eta / k
-    cplx<R> t;
+    C t;
     t.x = fvec * av.x - frho * ar.x;
     t.y = fvec * av.y - frho * ar.y;
-    cplx<R> out;
+    C out;
     out.x = an.x - t.y;
     out.y = an.y + t.x;
 #pragma unroll
@@ -118,45 +156,79 @@ __global__ void __launch_bounds__(256) interp_near(const cplx<R>* __restrict__ P
   }
 }
 
-template <typename R> static PrecData<R>& prec(aim_ctx* c);
-template <> PrecData<float>& prec<float>(aim_ctx* c) { return c->p32; }
-template <> PrecData<double>& prec<double>(aim_ctx* c) { return c->p64; }
-
-template <typename R>
-int matvec(aim_ctx* c, const cplx<R>* x, cplx<R>* y, int nrhs) {
-  PrecData<R>& p = prec<R>(c);
+template <class MD>
+static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename MD::R>* y, int nrhs,
+                       typename MD::S* grid0, const typename MD::R* pw, const typename MD::R* lam,
+                       const cplx<typename MD::R>* nval, int (*convolve)(aim_ctx*, int)) {
+  using R = typename MD::R;
   const long long Nc = (long long)c->n[0] * c->n[1] * c->n[2];
   {
-    int blocks = (int)std::min<long long>((Nc + 255) / 256, 152LL * 16);
-    AIM_LAUNCH(c, "proj_gather", proj_gather<R><<<blocks, 256, 0, c->stream>>>(x, p.grid0, c->pnode_ptr, c->pnode_m, p.pnode_w, c->N, Nc, nrhs));
+    const int blocks = (int)std::min<long long>((Nc + 255) / 256, 152LL * 16);
+    AIM_LAUNCH(c, "proj_gather",
+               proj_gather<MD><<<blocks, 256, 0, c->stream>>>(x, grid0, c->pnode_ptr, c->pnode_m, pw, c->N, Nc, nrhs));
     AIM_TRY(launch_check(c, "proj_gather"));
   }
-  AIM_TRY(fft_convolve<R>(c, p, 4 * nrhs));
+  AIM_TRY(convolve(c, 4 * nrhs));
   {
-    long long threads = (long long)c->N * 8;
-    int blocks = (int)((threads + 255) / 256);
+    const long long threads = (long long)c->N * 8;
+    const int blocks = (int)((threads + 255) / 256);
     const R fvec = (R)(c->k * kEta0), frho = (R)(kEta0 / c->k);
+#define AIM_INTERP(MM)                                                                                          \
+  AIM_LAUNCH(c, "interp_near",                                                                                  \
+             (interp_near<MD, MM><<<blocks, 256, 0, c->stream>>>(grid0, x, y, lam, c->base, c->near_ptr,        \
+                                                                 c->near_col, nval, c->N, Nc, c->n[0], c->n[1], \
+                                                                 nrhs, fvec, frho)))
     switch (c->M) {
-      case 1:
-        AIM_LAUNCH(c, "interp_near", interp_near<R, 1><<<blocks, 256, 0, c->stream>>>(p.grid0, x, y, p.lam, c->base, c->near_ptr, c->near_col,
-                                                         p.near_val, c->N, Nc, c->n[0], c->n[1], nrhs, fvec, frho));
-        break;
-      case 2:
-        AIM_LAUNCH(c, "interp_near", interp_near<R, 2><<<blocks, 256, 0, c->stream>>>(p.grid0, x, y, p.lam, c->base, c->near_ptr, c->near_col,
-                                                         p.near_val, c->N, Nc, c->n[0], c->n[1], nrhs, fvec, frho));
-        break;
-      default:
-        AIM_LAUNCH(c, "interp_near", interp_near<R, 3><<<blocks, 256, 0, c->stream>>>(p.grid0, x, y, p.lam, c->base, c->near_ptr, c->near_col,
-                                                         p.near_val, c->N, Nc, c->n[0], c->n[1], nrhs, fvec, frho));
-        break;
+      case 1: AIM_INTERP(1); break;
+      case 2: AIM_INTERP(2); break;
+      default: AIM_INTERP(3); break;
     }
+#undef AIM_INTERP
     AIM_TRY(launch_check(c, "interp_near"));
   }
   return AIM_OK;
 }
 
-template int matvec<float>(aim_ctx*, const float2*, float2*, int);
-template int matvec<double>(aim_ctx*, const double2*, double2*, int);
+int ensure_grids(aim_ctx* c, int precision) {
+  const long long B = c->max_rhs;
+  const long long nx = c->n[0], ny = c->n[1], nz = c->n[2], Ly = c->L[1], Lz = c->L[2];
+  const long long e0 = B * 4 * nz * ny * nx, e1 = B * 4 * Lz * ny * nx, e2 = B * 4 * Lz * Ly * nx;
+  if (precision == AIM_C64) {
+    PrecData<float>& p = c->p32;
+    if (!p.grid0) {
+      AIM_CUDA_TRY(cudaMalloc(&p.grid0, sizeof(float2) * e0));
+      AIM_CUDA_TRY(cudaMalloc(&p.grid1, sizeof(float2) * e1));
+      AIM_CUDA_TRY(cudaMalloc(&p.grid2, sizeof(float2) * e2));
+    }
+  } else if (precision == AIM_C128_F64) {
+    PrecData<double>& p = c->p64;
+    if (!p.grid0) {
+      AIM_CUDA_TRY(cudaMalloc(&p.grid0, sizeof(double2) * e0));
+      AIM_CUDA_TRY(cudaMalloc(&p.grid1, sizeof(double2) * e1));
+      AIM_CUDA_TRY(cudaMalloc(&p.grid2, sizeof(double2) * e2));
+    }
+  } else {
+    FFData& p = c->pff;
+    if (!p.grid0) {
+      AIM_CUDA_TRY(cudaMalloc(&p.grid0, sizeof(float4) * e0));
+      AIM_CUDA_TRY(cudaMalloc(&p.grid1, sizeof(float4) * e1));
+      AIM_CUDA_TRY(cudaMalloc(&p.grid2, sizeof(float4) * e2));
+    }
+  }
+  return AIM_OK;
+}
+
+int matvec(aim_ctx* c, const void* x, void* y, int nrhs, int precision) {
+  AIM_TRY(ensure_grids(c, precision));
+  if (precision == AIM_C64)
+    return run_product<M32>(c, (const float2*)x, (float2*)y, nrhs, c->p32.grid0, c->p32.pnode_w, c->p32.lam,
+                            c->p32.near_val, fft_convolve_c64);
+  if (precision == AIM_C128_F64)
+    return run_product<M64>(c, (const double2*)x, (double2*)y, nrhs, c->p64.grid0, c->p64.pnode_w, c->p64.lam,
+                            c->p64.near_val, fft_convolve_c128);
+  return run_product<MFF>(c, (const double2*)x, (double2*)y, nrhs, c->pff.grid0, c->p64.pnode_w, c->p64.lam,
+                          c->p64.near_val, fft_convolve_ff);
+}
 
 __global__ void k_c128_to_c64(const double2* __restrict__ in, float2* __restrict__ out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)

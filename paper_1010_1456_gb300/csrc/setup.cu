@@ -563,24 +563,35 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
     AIM_TRY(up(&c->rwg_len, T.len));
     AIM_TRY(up(&c->tri_area, T.area));
   }
-  // twiddles and Ghat
+  // FFT plans, twiddles and Ghat
+  AIM_TRY(upload((void**)&c->plan_dev, c->plan, sizeof(c->plan)));
   for (int d = 0; d < 3; ++d) {
+    if (c->plan[d].nst < 0) {
+      set_error("aim_setup: padded length is not 2,3,5-smooth");
+      return AIM_EINVAL;
+    }
     const int L = c->L[d];
     std::vector<double> t64(2 * (size_t)L);
-    std::vector<float> t32(2 * (size_t)L);
+    std::vector<float> t32(2 * (size_t)L), tff(4 * (size_t)L);
     for (int t = 0; t < L; ++t) {
       const double ang = (2.0 * kPi * t) / L;
       t64[2 * t] = std::cos(ang);
       t64[2 * t + 1] = -std::sin(ang);
-      t32[2 * t] = (float)t64[2 * t];
-      t32[2 * t + 1] = (float)t64[2 * t + 1];
+      for (int q = 0; q < 2; ++q) {
+        const float hi = (float)t64[2 * t + q];
+        t32[2 * t + q] = hi;
+        tff[4 * t + 2 * q] = hi;
+        tff[4 * t + 2 * q + 1] = (float)(t64[2 * t + q] - (double)hi);
+      }
     }
     AIM_TRY(upload((void**)&c->p64.tw[d], t64.data(), t64.size() * sizeof(double)));
     AIM_TRY(upload((void**)&c->p32.tw[d], t32.data(), t32.size() * sizeof(float)));
+    AIM_TRY(upload((void**)&c->pff.tw[d], tff.data(), tff.size() * sizeof(float)));
   }
   const size_t oct = (size_t)(c->L[0] / 2 + 1) * (c->L[1] / 2 + 1) * (c->L[2] / 2 + 1);
   AIM_TRY(upload((void**)&c->p64.ghat, nullptr, oct * sizeof(double2)));
   AIM_TRY(upload((void**)&c->p32.ghat, nullptr, oct * sizeof(float2)));
+  AIM_TRY(upload((void**)&c->pff.ghat, nullptr, oct * sizeof(float4)));
   AIM_TRY(build_ghat(c));
   c->h_ghat.resize(2 * oct);
   AIM_CUDA_TRY(cudaMemcpyAsync(c->h_ghat.data(), c->p64.ghat, oct * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));

@@ -82,11 +82,15 @@ def test_setup_arrays_match_oracle(plate_a):
     assert rel(gh, ref) <= 1e-13
 
 
+WIDE = [g.AIM_C128, g.AIM_C128_F64]  # float-float FFT and native FP64
+
+
+@pytest.mark.parametrize("prec", WIDE)
 @pytest.mark.parametrize("nrhs", [1, 3])
-def test_matvec_c128_plate(plate_a, nrhs):
+def test_matvec_c128_plate(plate_a, nrhs, prec):
     ctx, op = plate_a
     x = random_complex((nrhs, ctx.N), 11)
-    y = g.aim_matvec(ctx, torch.from_numpy(x).cuda()).cpu().numpy()
+    y = g.aim_matvec(ctx, torch.from_numpy(x).cuda(), precision=prec).cpu().numpy()
     assert rel(y, op.matvec(x)) <= 1e-12
 
 
@@ -97,12 +101,13 @@ def test_matvec_c64_plate(plate_a):
     assert rel(y, op.matvec(x.astype(np.complex64).astype(np.complex128))) <= 1e-5
 
 
-def test_matvec_sphere_both_precisions(sphere_small):
+def test_matvec_sphere_all_precisions(sphere_small):
     ctx, op = sphere_small
     x = random_complex((2, ctx.N), 13)
     ref = op.matvec(x)
-    y = g.aim_matvec(ctx, torch.from_numpy(x).cuda()).cpu().numpy()
-    assert rel(y, ref) <= 1e-12
+    for prec in WIDE:
+        y = g.aim_matvec(ctx, torch.from_numpy(x).cuda(), precision=prec).cpu().numpy()
+        assert rel(y, ref) <= 1e-12
     y32 = g.aim_matvec(ctx, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
     assert rel(y32, ref) <= 1e-5
 
@@ -110,7 +115,10 @@ def test_matvec_sphere_both_precisions(sphere_small):
 def test_matvec_host_entry_point(plate_a):
     ctx, op = plate_a
     x = random_complex((2, ctx.N), 14)
-    assert rel(g.aim_matvec_host(ctx, x), op.matvec(x)) <= 1e-12
+    for prec in WIDE:
+        assert rel(g.aim_matvec_host(ctx, x, precision=prec), op.matvec(x)) <= 1e-12
+    y32 = g.aim_matvec_host(ctx, x.astype(np.complex64), precision=g.AIM_C64)
+    assert rel(y32, op.matvec(x.astype(np.complex64).astype(np.complex128))) <= 1e-5
 
 
 def test_rhs_matches_oracle(sphere_small):
@@ -125,8 +133,9 @@ def test_other_stencil_orders(M):
     v, t = plate_mesh(0.7, 6)
     ctx, op = make(v, t, M=M)
     x = random_complex((1, ctx.N), 15)
-    y = g.aim_matvec(ctx, torch.from_numpy(x).cuda()).cpu().numpy()
-    assert rel(y, op.matvec(x)) <= 1e-12
+    for prec in WIDE:
+        y = g.aim_matvec(ctx, torch.from_numpy(x).cuda(), precision=prec).cpu().numpy()
+        assert rel(y, op.matvec(x)) <= 1e-12
 
 
 def test_all_pairs_near_equals_dense():
@@ -187,7 +196,32 @@ def test_full_size_sphere_sampled_rows():
     assert ctx.N == 58080
     x = random_complex((1, ctx.N), 21)
     ref = op.matvec(x)[0, rows]
-    y = g.aim_matvec(ctx, torch.from_numpy(x).cuda()).cpu().numpy()[0, rows]
-    assert rel(y, ref) <= 1e-12
+    for prec in WIDE:
+        y = g.aim_matvec(ctx, torch.from_numpy(x).cuda(), precision=prec).cpu().numpy()[0, rows]
+        assert rel(y, ref) <= 1e-12
     y32 = g.aim_matvec(ctx, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()[0, rows]
     assert rel(y32, ref) <= 1e-5
+
+
+@pytest.mark.slow
+def test_full_size_plate_32_lambda_multi_rhs_sampled_rows():
+    """32 lambda plate (N = 248,256, grid 321x321x3 padded 648x648x5), 4 RHS, sampled rows."""
+    v, t = plate_mesh(32.0, 288)
+    rows = np.sort(np.random.default_rng(1).choice(248256, 200, replace=False))
+    ctx, op = make(v, t, max_rhs=4, near_rows=rows)
+    assert ctx.N == 248256
+    x = random_complex((4, ctx.N), 22)
+    ref = op.matvec(x)[:, rows]
+    y = g.aim_matvec(ctx, torch.from_numpy(x).cuda(), precision=g.AIM_C128).cpu().numpy()[:, rows]
+    assert rel(y, ref) <= 1e-12
+    y32 = g.aim_matvec(ctx, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()[:, rows]
+    assert rel(y32, ref) <= 1e-5
+
+
+def test_float_float_accuracy_beats_complex64_by_far(sphere_small):
+    """The float-float product sits within a few 1e-14 of the native FP64 one."""
+    ctx, op = sphere_small
+    x = torch.from_numpy(random_complex((1, ctx.N), 23)).cuda()
+    a = g.aim_matvec(ctx, x, precision=g.AIM_C128).cpu().numpy()
+    b = g.aim_matvec(ctx, x, precision=g.AIM_C128_F64).cpu().numpy()
+    assert rel(a, b) <= 1e-13

@@ -41,7 +41,7 @@ def true_res(op, V, X):
     return np.linalg.norm(V - op.matvec(X), axis=1) / np.linalg.norm(V, axis=1)
 
 
-@pytest.mark.parametrize("prec", [g.AIM_C128, g.AIM_C64])
+@pytest.mark.parametrize("prec", [g.AIM_C128, g.AIM_C128_F64, g.AIM_C64])
 def test_solve_plate_reaches_tolerance(prec):
     v, t = plate_mesh(1.0, 9)
     op = oaim.AIMOperator(RWG(v, t), K0, H, 2)
@@ -78,7 +78,7 @@ def test_rcs_parity_and_mixed_accuracy(sphere):
     th, ph, w = orcs.direction_grid(n, 2 * n)
     kh, po = planewave_minus_z_xpol()
     errs = {}
-    for prec in (g.AIM_C128, g.AIM_C64):
+    for prec in (g.AIM_C128_F64, g.AIM_C128, g.AIM_C64):
         ctx = g.aim_setup(v, t, K0, H, precision=prec)
         V = g.aim_rhs_planewave(ctx, kh, po)
         X, info = g.aim_solve(ctx, V, TOL)
@@ -86,8 +86,9 @@ def test_rcs_parity_and_mixed_accuracy(sphere):
         ref = orcs.sigma_thth(op.rwg, K0, X.cpu().numpy(), th, ph)
         assert np.linalg.norm(stt - ref) <= 1e-6 * np.linalg.norm(ref)
         errs[prec] = orcs.err_thth(stt[0], mie.sigma_thth_minus_z(R, th, ph), w)
-    assert errs[g.AIM_C64] <= errs[g.AIM_C128] + 1e-3
-    assert errs[g.AIM_C128] < 0.1
+    assert errs[g.AIM_C64] <= errs[g.AIM_C128_F64] + 1e-3
+    assert abs(errs[g.AIM_C128] - errs[g.AIM_C128_F64]) <= 1e-6
+    assert errs[g.AIM_C128_F64] < 0.1
 
 
 def test_zero_rhs_returns_zero():
