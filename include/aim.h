@@ -219,6 +219,28 @@ int aim_profile_read(aim_ctx* ctx, int max_kernels, char* names, int64_t* launch
  */
 int aim_probe_fma_peak(int which, double* tflops);
 
+/*
+ * Complex64 AIM product (same result as aim_matvec with AIM_C64) that
+ * allocates no device memory.  The paper has no counterpart: this serves
+ * callers that cannot let the library call cudaMalloc, because their device
+ * memory belongs to another allocator or pool, or because an allocation
+ * (which can synchronise the device) is not allowed in their loop.
+ *   x_dev, y_dev: device c64 [nrhs][N], 1 <= nrhs <= opts.max_rhs, distinct.
+ * The pass grids live in one fixed 64 MiB device array compiled into the
+ * library (held by every GPU that loads the library until the process
+ * exits); a product needs 8 * 4 * nrhs * (nx*ny*nz + Lz*ny*nx + Lz*Ly*nx)
+ * bytes (each part rounded up to 256), and larger requests return
+ * AIM_EINVAL with the size in aim_last_error().  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; with lazy module loading the driver maps the array at
+ * that moment, so the device's free memory drops by 64 MiB on the first call
+ * and stays there until exit.  Make that first call before any stream
+ * capture.  All
+ * calls share the array: calls whose work overlaps on the GPU race and must
+ * be ordered by the caller.  The context itself is built by aim_setup.
+ */
+int aim_matvec_c64_noalloc(aim_ctx* ctx, const void* x_dev, void* y_dev, int nrhs);
+
 const char* aim_strerror(int code);
 const char* aim_last_error(void); /* thread-local detail of the last failure */
 

@@ -217,6 +217,9 @@ int convert_c64_to_c128(aim_ctx* c, const float2* in, double2* out, int64_t coun
 int fft_convolve_c64(aim_ctx* c, int G);
 int fft_convolve_c128(aim_ctx* c, int G);
 int fft_convolve_ff(aim_ctx* c, int G);
+// complex64 product and convolution on caller-provided grids (noalloc.cu)
+int fft_convolve_c64_bufs(aim_ctx* c, int G, float2* g0, float2* g1, float2* g2);
+int matvec_c64_bufs(aim_ctx* c, const float2* x, float2* y, int nrhs, float2* g0, float2* g1, float2* g2);
 int build_ghat(aim_ctx* c);
 // krylov.cu
 int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_solve_info* info);

@@ -499,3 +499,11 @@ int build_ghat(aim_ctx* c) {
 }
 
 }  // namespace aim
+
+namespace aim {
+// Complex64 convolution on caller-provided pass buffers (used by the
+// product variant that allocates nothing; same kernels and launch shapes).
+int fft_convolve_c64_bufs(aim_ctx* c, int G, float2* g0, float2* g1, float2* g2) {
+  return convolve<P32>(c, g0, g1, g2, c->p32.ghat, c->p32.tw, G);
+}
+}  // namespace aim

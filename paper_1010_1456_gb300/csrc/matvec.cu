@@ -251,3 +251,38 @@ int convert_c64_to_c128(aim_ctx* c, const float2* in, double2* out, int64_t coun
 }
 
 }  // namespace aim
+
+namespace aim {
+// The complex64 product on caller-provided grids g0 [B][4][nz][ny][nx],
+// g1 [B][4][Lz][ny][nx], g2 [B][4][Lz][Ly][nx]: the launches of the
+// complex64 path of matvec() without its grid allocation.
+int matvec_c64_bufs(aim_ctx* c, const float2* x, float2* y, int nrhs, float2* g0, float2* g1, float2* g2) {
+  const long long Nc = (long long)c->n[0] * c->n[1] * c->n[2];
+  {
+    const int blocks = (int)std::min<long long>((Nc + 255) / 256, 152LL * 16);
+    AIM_LAUNCH(c, "proj_gather",
+               proj_gather<M32><<<blocks, 256, 0, c->stream>>>(x, g0, c->pnode_ptr, c->pnode_m, c->p32.pnode_w, c->N,
+                                                              Nc, nrhs));
+    AIM_TRY(launch_check(c, "proj_gather"));
+  }
+  AIM_TRY(fft_convolve_c64_bufs(c, 4 * nrhs, g0, g1, g2));
+  {
+    const long long threads = (long long)c->N * 8;
+    const int blocks = (int)((threads + 255) / 256);
+    const float fvec = (float)(c->k * kEta0), frho = (float)(kEta0 / c->k);
+#define AIM_INTERP32(MM)                                                                                      \
+  AIM_LAUNCH(c, "interp_near",                                                                                \
+             (interp_near<M32, MM><<<blocks, 256, 0, c->stream>>>(g0, x, y, c->p32.lam, c->base, c->near_ptr, \
+                                                                  c->near_col, c->p32.near_val, c->N, Nc,     \
+                                                                  c->n[0], c->n[1], nrhs, fvec, frho)))
+    switch (c->M) {
+      case 1: AIM_INTERP32(1); break;
+      case 2: AIM_INTERP32(2); break;
+      default: AIM_INTERP32(3); break;
+    }
+#undef AIM_INTERP32
+    AIM_TRY(launch_check(c, "interp_near"));
+  }
+  return AIM_OK;
+}
+}  // namespace aim
