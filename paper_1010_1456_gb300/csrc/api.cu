@@ -36,7 +36,7 @@ static void free_ctx(aim_ctx* c) {
   free_prec(c->p32);
   cudaFree(c->pff.ghat);
   for (int d = 0; d < 3; ++d) cudaFree(c->pff.tw[d]);
-  cudaFree(c->pff.grid0); cudaFree(c->pff.grid1); cudaFree(c->pff.grid2);
+  cudaFree(c->pff.grid0); cudaFree(c->pff.grid1); cudaFree(c->pff.grid2); cudaFree(c->pff.phi64);
   cudaFree(c->plan_dev);
   free_krylov(c);
   profile_free(c);

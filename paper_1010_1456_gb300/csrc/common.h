@@ -97,6 +97,7 @@ struct FFData {
   float4* grid0 = nullptr;
   float4* grid1 = nullptr;
   float4* grid2 = nullptr;
+  double2* phi64 = nullptr;  // [B][4][nz][ny][nx] Phi in FP64, read by the interpolation
 };
 
 // Per-kernel timing with CUDA events on the context stream (aim_profile).

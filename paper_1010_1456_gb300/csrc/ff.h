@@ -41,8 +41,20 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
   return ff_fast_two_sum(s.hi, e);
 }
 
+// Addition without the closing renormalisation: hi is the rounded sum of the
+// high parts and lo collects that rounding error plus both low parts, so
+// hi + lo still carries the sum to about 2^-47 (|a| + |b|) but |lo| may
+// exceed ulp(hi)/2 by a few units.  Later TwoSum/TwoProduct steps accept
+// such pairs; used inside FFT butterflies, where every value feeds further
+// arithmetic.
+__device__ __forceinline__ ff ff_add_lazy(ff a, ff b) {
+  const ff s = ff_two_sum(a.hi, b.hi);
+  return ff{s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
+}
+
 __device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_sub_lazy(ff a, ff b) { return ff_add_lazy(a, ff_neg(b)); }
 
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {
   const float p = __fmul_rn(a.hi, b.hi);

@@ -28,6 +28,7 @@
 //   multiply-shift division, so no integer division runs in the kernels.
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "common.h"
 #include "ff.h"
@@ -115,8 +116,8 @@ struct PFF {
   __device__ static T ld(const S& s) { return cff{ff{s.x, s.y}, ff{s.z, s.w}}; }
   __device__ static S st(const T& t) { return make_float4(t.re.hi, t.re.lo, t.im.hi, t.im.lo); }
   __device__ static T zero() { return cff{ff{0.f, 0.f}, ff{0.f, 0.f}}; }
-  __device__ static T add(T a, T b) { return cff{ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
-  __device__ static T sub(T a, T b) { return cff{ff_sub(a.re, b.re), ff_sub(a.im, b.im)}; }
+  __device__ static T add(T a, T b) { return cff{ff_add_lazy(a.re, b.re), ff_add_lazy(a.im, b.im)}; }
+  __device__ static T sub(T a, T b) { return cff{ff_sub_lazy(a.re, b.re), ff_sub_lazy(a.im, b.im)}; }
   __device__ static T mul(T a, T b) {
     return cff{ff_dot2(a.re, b.re, ff_neg(a.im), b.im), ff_dot2(a.re, b.im, a.im, b.re)};
   }
@@ -174,9 +175,13 @@ template <class P, bool INV> __device__ __forceinline__ void dft5(typename P::T*
 // One Stockham stage over `count` pencils of length L in shared memory.
 // COLS: element p of pencil c at buf[p * kTX + c] (column tiles, count = kTX);
 // otherwise at buf[c * L + p] (row tiles).
+// nvalid: samples p >= nvalid of every pencil are zero (only used by the
+// first stage, where Ns = 1: a radix-4 butterfly whose two upper inputs are
+// zero costs half the additions).
 template <class P, bool INV, int RAD, bool COLS>
 __device__ __forceinline__ void stage_r(const typename P::S* __restrict__ src, typename P::S* __restrict__ dst,
-                                        const FftPlan& pl, int s, int count, const typename P::S* __restrict__ tw) {
+                                        const FftPlan& pl, int s, int count, const typename P::S* __restrict__ tw,
+                                        int nvalid) {
   using T = typename P::T;
   const int L = pl.L;
   const int nb = L / RAD;
@@ -196,6 +201,22 @@ __device__ __forceinline__ void stage_r(const typename P::S* __restrict__ src, t
     const int q = (int)qdiv((uint32_t)j, dNs);
     const int k = j - q * Ns;
     T v[RAD];
+    if (RAD == 4 && s == 0 && j + 2 * nb >= nvalid) {
+      // first stage (Ns = 1, idxD = 4 j): inputs 2 and 3 are zero
+      const T a = P::ld(src[COLS ? j * P::kTX + c : c * L + j]);
+      const T b = (j + nb < nvalid) ? P::ld(src[COLS ? (j + nb) * P::kTX + c : c * L + j + nb]) : P::zero();
+      const T ib = P::template mul_mi<INV>(b);
+      v[0] = P::add(a, b);
+      v[1] = P::add(a, ib);
+      v[2] = P::sub(a, b);
+      v[3] = P::sub(a, ib);
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) {
+        const int p = 4 * j + r;
+        dst[COLS ? p * P::kTX + c : c * L + p] = P::st(v[r]);
+      }
+      continue;
+    }
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
       const int p = j + r * nb;
@@ -219,13 +240,13 @@ __device__ __forceinline__ void stage_r(const typename P::S* __restrict__ src, t
 // Full transform in shared memory; returns the buffer that holds the result.
 template <class P, bool INV, bool COLS>
 __device__ typename P::S* stockham(typename P::S* b0, typename P::S* b1, const FftPlan& pl, int count,
-                                   const typename P::S* __restrict__ tw) {
+                                   const typename P::S* __restrict__ tw, int nvalid) {
   for (int s = 0; s < pl.nst; ++s) {
     switch (pl.rad[s]) {
-      case 2: stage_r<P, INV, 2, COLS>(b0, b1, pl, s, count, tw); break;
-      case 3: stage_r<P, INV, 3, COLS>(b0, b1, pl, s, count, tw); break;
-      case 4: stage_r<P, INV, 4, COLS>(b0, b1, pl, s, count, tw); break;
-      default: stage_r<P, INV, 5, COLS>(b0, b1, pl, s, count, tw); break;
+      case 2: stage_r<P, INV, 2, COLS>(b0, b1, pl, s, count, tw, nvalid); break;
+      case 3: stage_r<P, INV, 3, COLS>(b0, b1, pl, s, count, tw, nvalid); break;
+      case 4: stage_r<P, INV, 4, COLS>(b0, b1, pl, s, count, tw, nvalid); break;
+      default: stage_r<P, INV, 5, COLS>(b0, b1, pl, s, count, tw, nvalid); break;
     }
     __syncthreads();
     typename P::S* t = b0;
@@ -243,8 +264,18 @@ struct StridedArgs {
   long long sG_out, sA_out, sP_out;
 };
 
-template <class P, bool INV>
-__global__ void __launch_bounds__(256) fft_strided(const typename P::S* __restrict__ in, typename P::S* __restrict__ out,
+// Output element conversion of a pass (identity, or float-float -> FP64).
+template <class S, class O> struct OutConv {
+  __device__ static O f(const S& s) { return s; }
+};
+template <> struct OutConv<float4, double2> {
+  __device__ static double2 f(const float4& s) {
+    return make_double2((double)s.x + (double)s.y, (double)s.z + (double)s.w);
+  }
+};
+
+template <class P, bool INV, class O>
+__global__ void __launch_bounds__(256) fft_strided(const typename P::S* __restrict__ in, O* __restrict__ out,
                                                    StridedArgs a, const FftPlan* __restrict__ plan,
                                                    const typename P::S* __restrict__ tw) {
   using S = typename P::S;
@@ -265,11 +296,11 @@ __global__ void __launch_bounds__(256) fft_strided(const typename P::S* __restri
     b0[e] = v;
   }
   __syncthreads();
-  S* res = stockham<P, INV, true>(b0, b1, pl, TX, tw);
-  S* dst = out + g * a.sG_out + ia * a.sA_out + x0;
+  S* res = stockham<P, INV, true>(b0, b1, pl, TX, tw, a.n_in);
+  O* dst = out + g * a.sG_out + ia * a.sA_out + x0;
   for (int e = threadIdx.x; e < a.n_out * TX; e += blockDim.x) {
     const int p = e / TX, c = e & (TX - 1);
-    if (x0 + c < a.X) dst[p * a.sP_out + c] = res[e];
+    if (x0 + c < a.X) dst[p * a.sP_out + c] = OutConv<S, O>::f(res[e]);
   }
 }
 
@@ -312,13 +343,13 @@ __global__ void __launch_bounds__(256) fft_x(typename P::S* __restrict__ buf, XA
         b0[c * L + p] = v;
       }
     __syncthreads();
-    S* res = stockham<P, false, false>(b0, b1, pl, ng, tw);
+    S* res = stockham<P, false, false>(b0, b1, pl, ng, tw, a.nx);
     if (MODE == 0) {
       S* oth = (res == b0) ? b1 : b0;
       for (int c = 0; c < ng; ++c)
         for (int p = threadIdx.x; p < L; p += blockDim.x) res[c * L + p] = P::st(P::mul(P::ld(res[c * L + p]), P::ld(gr[p])));
       __syncthreads();
-      res = stockham<P, true, false>(res, oth, pl, ng, tw);
+      res = stockham<P, true, false>(res, oth, pl, ng, tw, L);
     }
     for (int c = 0; c < ng; ++c)
       for (int p = threadIdx.x; p < a.nx; p += blockDim.x) buf[(g0 + c) * a.sG + row + p] = res[c * L + p];
@@ -326,9 +357,9 @@ __global__ void __launch_bounds__(256) fft_x(typename P::S* __restrict__ buf, XA
 }
 
 // ------------------------------------------------------------------ drivers
-template <class P, bool INV>
-static int launch_strided(aim_ctx* c, const char* name, const typename P::S* in, typename P::S* out,
-                          const StridedArgs& a, int G, const FftPlan* plan_dev, int L, const typename P::S* tw) {
+template <class P, bool INV, class O = typename P::S>
+static int launch_strided(aim_ctx* c, const char* name, const typename P::S* in, O* out, const StridedArgs& a, int G,
+                          const FftPlan* plan_dev, int L, const typename P::S* tw) {
   constexpr int TX = P::kTX;
   const size_t sm = 2ull * L * TX * sizeof(typename P::S);
   if (sm > 227 * 1024) {
@@ -337,10 +368,10 @@ static int launch_strided(aim_ctx* c, const char* name, const typename P::S* in,
   }
   // once per template instance (thread-safe static initialisation)
   static const cudaError_t attr =
-      cudaFuncSetAttribute(fft_strided<P, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(fft_strided<P, INV, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   AIM_CUDA_TRY(attr);
   dim3 grid((a.X + TX - 1) / TX, a.A, G);
-  AIM_LAUNCH(c, name, fft_strided<P, INV><<<grid, 256, sm, c->stream>>>(in, out, a, plan_dev, tw));
+  AIM_LAUNCH(c, name, fft_strided<P, INV, O><<<grid, 256, sm, c->stream>>>(in, out, a, plan_dev, tw));
   return launch_check(c, name);
 }
 
@@ -367,9 +398,11 @@ static int launch_x(aim_ctx* c, const char* name, typename P::S* buf, XArgs a, c
   return launch_check(c, name);
 }
 
+// phi64: when non-null (float-float policy only), the last inverse pass writes
+// Phi there in FP64 instead of back into g0.
 template <class P>
 static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P::S* g2, const typename P::S* ghat,
-                    typename P::S* const* tw, int G) {
+                    typename P::S* const* tw, int G, double2* phi64 = nullptr) {
   const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
   const int Lx = c->L[0], Ly = c->L[1], Lz = c->L[2];
   const FftPlan* pd = c->plan_dev;
@@ -406,6 +439,9 @@ static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P
     a.n_in = Lz; a.n_out = nz; a.X = nx; a.A = ny;
     a.sG_in = (long long)Lz * ny * nx; a.sA_in = nx; a.sP_in = (long long)ny * nx;
     a.sG_out = (long long)nz * ny * nx; a.sA_out = nx; a.sP_out = (long long)ny * nx;
+    if constexpr (std::is_same<P, PFF>::value) {
+      if (phi64) return launch_strided<P, true, double2>(c, "fft_z_inv", g1, phi64, a, G, pd + 2, Lz, tw[2]);
+    }
     AIM_TRY((launch_strided<P, true>(c, "fft_z_inv", g1, g0, a, G, pd + 2, Lz, tw[2])));
   }
   return AIM_OK;
@@ -421,7 +457,7 @@ int fft_convolve_c128(aim_ctx* c, int G) {
 }
 int fft_convolve_ff(aim_ctx* c, int G) {
   FFData& p = c->pff;
-  return convolve<PFF>(c, p.grid0, p.grid1, p.grid2, p.ghat, p.tw, G);
+  return convolve<PFF>(c, p.grid0, p.grid1, p.grid2, p.ghat, p.tw, G, p.phi64);
 }
 
 // ------------------------------------------------------------------ Ghat

@@ -71,18 +71,26 @@ __device__ __forceinline__ W4<double> load_w4(const double* p, int e) {
   return W4<double>{a.x, a.y, b.x, b.y};
 }
 
+// 4 lanes per grid node: the lanes take every fourth entry of the node's list
+// (adjacent lanes read adjacent entries) and combine with warp shuffles.
 template <class MD>
 __global__ void __launch_bounds__(256) proj_gather(const cplx<typename MD::R>* __restrict__ x, typename MD::S* __restrict__ Q,
                                                    const int32_t* __restrict__ ptr, const int32_t* __restrict__ mm,
                                                    const typename MD::R* __restrict__ w, int N, long long Nc, int nrhs) {
   using R = typename MD::R;
   using C = cplx<R>;
-  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < Nc; u += (long long)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 3;
+  const long long stride = ((long long)gridDim.x * blockDim.x) >> 2;
+  for (long long u0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 2;; u0 += stride) {
+    // the warp leaves together, so every lane takes part in the shuffles below
+    const bool live = u0 < Nc;
+    if (!__any_sync(0xffffffffu, live)) break;
+    const long long u = live ? u0 : Nc - 1;
     const int e0 = ptr[u], e1 = ptr[u + 1];
     for (int b = 0; b < nrhs; ++b) {
       C a0 = cmake<C>(0, 0), a1 = a0, a2 = a0, a3 = a0;
       const C* xb = x + (long long)b * N;
-      for (int e = e0; e < e1; ++e) {
+      for (int e = e0 + lane; e < e1; e += 4) {
         const W4<R> ww = load_w4(w, e);
         const C xv = xb[mm[e]];
         a0.x += ww.x * xv.x; a0.y += ww.x * xv.y;
@@ -90,11 +98,19 @@ __global__ void __launch_bounds__(256) proj_gather(const cplx<typename MD::R>* _
         a2.x += ww.z * xv.x; a2.y += ww.z * xv.y;
         a3.x += ww.w * xv.x; a3.y += ww.w * xv.y;
       }
-      typename MD::S* Qb = Q + (long long)b * 4 * Nc;
-      Qb[u] = MD::put(a0);
-      Qb[Nc + u] = MD::put(a1);
-      Qb[2 * Nc + u] = MD::put(a2);
-      Qb[3 * Nc + u] = MD::put(a3);
+#pragma unroll
+      for (int o = 1; o < 4; o <<= 1) {
+        a0.x += __shfl_xor_sync(0xffffffffu, a0.x, o, 4); a0.y += __shfl_xor_sync(0xffffffffu, a0.y, o, 4);
+        a1.x += __shfl_xor_sync(0xffffffffu, a1.x, o, 4); a1.y += __shfl_xor_sync(0xffffffffu, a1.y, o, 4);
+        a2.x += __shfl_xor_sync(0xffffffffu, a2.x, o, 4); a2.y += __shfl_xor_sync(0xffffffffu, a2.y, o, 4);
+        a3.x += __shfl_xor_sync(0xffffffffu, a3.x, o, 4); a3.y += __shfl_xor_sync(0xffffffffu, a3.y, o, 4);
+      }
+      if (live) {
+        typename MD::S* Qb = Q + (long long)b * 4 * Nc;
+        // lane c writes component c (one conversion per value)
+        const C val = lane == 0 ? a0 : lane == 1 ? a1 : lane == 2 ? a2 : a3;
+        Qb[(long long)lane * Nc + u] = MD::put(val);
+      }
     }
   }
 }
@@ -156,14 +172,15 @@ __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restr
   }
 }
 
-template <class MD>
+// MD: storage of the projected grid; MI: storage of Phi read by the interpolation.
+template <class MD, class MI>
 static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename MD::R>* y, int nrhs,
-                       typename MD::S* grid0, const typename MD::R* pw, const typename MD::R* lam,
-                       const cplx<typename MD::R>* nval, int (*convolve)(aim_ctx*, int)) {
+                       typename MD::S* grid0, const typename MI::S* phi, const typename MD::R* pw,
+                       const typename MD::R* lam, const cplx<typename MD::R>* nval, int (*convolve)(aim_ctx*, int)) {
   using R = typename MD::R;
   const long long Nc = (long long)c->n[0] * c->n[1] * c->n[2];
   {
-    const int blocks = (int)std::min<long long>((Nc + 255) / 256, 152LL * 16);
+    const int blocks = (int)std::min<long long>((4 * Nc + 255) / 256, 152LL * 16);
     AIM_LAUNCH(c, "proj_gather",
                proj_gather<MD><<<blocks, 256, 0, c->stream>>>(x, grid0, c->pnode_ptr, c->pnode_m, pw, c->N, Nc, nrhs));
     AIM_TRY(launch_check(c, "proj_gather"));
@@ -175,7 +192,7 @@ static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename 
     const R fvec = (R)(c->k * kEta0), frho = (R)(kEta0 / c->k);
 #define AIM_INTERP(MM)                                                                                          \
   AIM_LAUNCH(c, "interp_near",                                                                                  \
-             (interp_near<MD, MM><<<blocks, 256, 0, c->stream>>>(grid0, x, y, lam, c->base, c->near_ptr,        \
+             (interp_near<MI, MM><<<blocks, 256, 0, c->stream>>>(phi, x, y, lam, c->base, c->near_ptr,          \
                                                                  c->near_col, nval, c->N, Nc, c->n[0], c->n[1], \
                                                                  nrhs, fvec, frho)))
     switch (c->M) {
@@ -213,6 +230,7 @@ int ensure_grids(aim_ctx* c, int precision) {
       AIM_CUDA_TRY(cudaMalloc(&p.grid0, sizeof(float4) * e0));
       AIM_CUDA_TRY(cudaMalloc(&p.grid1, sizeof(float4) * e1));
       AIM_CUDA_TRY(cudaMalloc(&p.grid2, sizeof(float4) * e2));
+      AIM_CUDA_TRY(cudaMalloc(&p.phi64, sizeof(double2) * e0));
     }
   }
   return AIM_OK;
@@ -221,13 +239,13 @@ int ensure_grids(aim_ctx* c, int precision) {
 int matvec(aim_ctx* c, const void* x, void* y, int nrhs, int precision) {
   AIM_TRY(ensure_grids(c, precision));
   if (precision == AIM_C64)
-    return run_product<M32>(c, (const float2*)x, (float2*)y, nrhs, c->p32.grid0, c->p32.pnode_w, c->p32.lam,
-                            c->p32.near_val, fft_convolve_c64);
+    return run_product<M32, M32>(c, (const float2*)x, (float2*)y, nrhs, c->p32.grid0, c->p32.grid0, c->p32.pnode_w,
+                                 c->p32.lam, c->p32.near_val, fft_convolve_c64);
   if (precision == AIM_C128_F64)
-    return run_product<M64>(c, (const double2*)x, (double2*)y, nrhs, c->p64.grid0, c->p64.pnode_w, c->p64.lam,
-                            c->p64.near_val, fft_convolve_c128);
-  return run_product<MFF>(c, (const double2*)x, (double2*)y, nrhs, c->pff.grid0, c->p64.pnode_w, c->p64.lam,
-                          c->p64.near_val, fft_convolve_ff);
+    return run_product<M64, M64>(c, (const double2*)x, (double2*)y, nrhs, c->p64.grid0, c->p64.grid0,
+                                 c->p64.pnode_w, c->p64.lam, c->p64.near_val, fft_convolve_c128);
+  return run_product<MFF, M64>(c, (const double2*)x, (double2*)y, nrhs, c->pff.grid0, c->pff.phi64, c->p64.pnode_w,
+                               c->p64.lam, c->p64.near_val, fft_convolve_ff);
 }
 
 __global__ void k_c128_to_c64(const double2* __restrict__ in, float2* __restrict__ out, long long n) {
