@@ -148,6 +148,7 @@ struct aim_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
   int64_t launches = 0;
+  bool fourstep = true;  // four-step FFT kernels for the lengths that have them
   aim::FftPlan plan[3];
   aim::FftPlan* plan_dev = nullptr;  // device copy of plan[3]
 

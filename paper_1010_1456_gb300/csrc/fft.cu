@@ -32,6 +32,8 @@
 
 #include "common.h"
 #include "ff.h"
+#include "fft4.cuh"
+#include "fft_policy.h"
 #include "geom.h"
 
 namespace aim {
@@ -70,106 +72,6 @@ FftPlan make_plan(int L) {
     Ns *= p.rad[s];
   }
   return p;
-}
-
-// ------------------------------------------------------------------ arithmetic policies
-// Real constants are passed as (double value, float hi, float lo) so every
-// policy sees the constant at its own precision, folded at compile time.
-#define AIM_RC(c) (c), (float)(c), (float)((c) - (double)(float)(c))
-
-struct P32 {
-  using S = float2;  // storage
-  using T = float2;  // work
-  static constexpr int kTX = 16;
-  __device__ static T ld(const S& s) { return s; }
-  __device__ static S st(const T& t) { return t; }
-  __device__ static T zero() { return make_float2(0.f, 0.f); }
-  __device__ static T add(T a, T b) { return make_float2(a.x + b.x, a.y + b.y); }
-  __device__ static T sub(T a, T b) { return make_float2(a.x - b.x, a.y - b.y); }
-  __device__ static T mul(T a, T b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-  __device__ static T mulr(T a, double, float c, float) { return make_float2(a.x * c, a.y * c); }
-  __device__ static T half(T a) { return make_float2(0.5f * a.x, 0.5f * a.y); }
-  template <bool INV> __device__ static T mul_mi(T a) { return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x); }
-  __device__ static T conj_if(T w, bool c) { return c ? make_float2(w.x, -w.y) : w; }
-};
-
-struct P64 {
-  using S = double2;
-  using T = double2;
-  static constexpr int kTX = 8;
-  __device__ static T ld(const S& s) { return s; }
-  __device__ static S st(const T& t) { return t; }
-  __device__ static T zero() { return make_double2(0.0, 0.0); }
-  __device__ static T add(T a, T b) { return make_double2(a.x + b.x, a.y + b.y); }
-  __device__ static T sub(T a, T b) { return make_double2(a.x - b.x, a.y - b.y); }
-  __device__ static T mul(T a, T b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-  __device__ static T mulr(T a, double c, float, float) { return make_double2(a.x * c, a.y * c); }
-  __device__ static T half(T a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
-  template <bool INV> __device__ static T mul_mi(T a) { return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x); }
-  __device__ static T conj_if(T w, bool c) { return c ? make_double2(w.x, -w.y) : w; }
-};
-
-struct PFF {
-  using S = float4;
-  using T = cff;
-  static constexpr int kTX = 8;
-  __device__ static T ld(const S& s) { return cff{ff{s.x, s.y}, ff{s.z, s.w}}; }
-  __device__ static S st(const T& t) { return make_float4(t.re.hi, t.re.lo, t.im.hi, t.im.lo); }
-  __device__ static T zero() { return cff{ff{0.f, 0.f}, ff{0.f, 0.f}}; }
-  __device__ static T add(T a, T b) { return cff{ff_add_lazy(a.re, b.re), ff_add_lazy(a.im, b.im)}; }
-  __device__ static T sub(T a, T b) { return cff{ff_sub_lazy(a.re, b.re), ff_sub_lazy(a.im, b.im)}; }
-  __device__ static T mul(T a, T b) {
-    return cff{ff_dot2(a.re, b.re, ff_neg(a.im), b.im), ff_dot2(a.re, b.im, a.im, b.re)};
-  }
-  __device__ static T mulr(T a, double, float ch, float cl) {
-    const ff c{ch, cl};
-    return cff{ff_mul(a.re, c), ff_mul(a.im, c)};
-  }
-  __device__ static T half(T a) { return cff{ff{0.5f * a.re.hi, 0.5f * a.re.lo}, ff{0.5f * a.im.hi, 0.5f * a.im.lo}}; }
-  template <bool INV> __device__ static T mul_mi(T a) { return INV ? cff{ff_neg(a.im), a.re} : cff{a.im, ff_neg(a.re)}; }
-  __device__ static T conj_if(T w, bool c) { return c ? cff{w.re, ff_neg(w.im)} : w; }
-};
-
-// ------------------------------------------------------------------ butterflies
-template <class P, bool INV> __device__ __forceinline__ void dft2(typename P::T* v) {
-  const typename P::T a = v[0], b = v[1];
-  v[0] = P::add(a, b);
-  v[1] = P::sub(a, b);
-}
-template <class P, bool INV> __device__ __forceinline__ void dft3(typename P::T* v) {
-  using T = typename P::T;
-  const T a = v[0], s = P::add(v[1], v[2]), d = P::sub(v[1], v[2]);
-  const T m = P::sub(a, P::half(s));
-  const T t = P::template mul_mi<INV>(P::mulr(d, AIM_RC(0.86602540378443864676)));  // sin(2 pi / 3)
-  v[0] = P::add(a, s);
-  v[1] = P::add(m, t);
-  v[2] = P::sub(m, t);
-}
-template <class P, bool INV> __device__ __forceinline__ void dft4(typename P::T* v) {
-  using T = typename P::T;
-  const T s02 = P::add(v[0], v[2]), d02 = P::sub(v[0], v[2]);
-  const T s13 = P::add(v[1], v[3]), d13 = P::template mul_mi<INV>(P::sub(v[1], v[3]));
-  v[0] = P::add(s02, s13);
-  v[2] = P::sub(s02, s13);
-  v[1] = P::add(d02, d13);
-  v[3] = P::sub(d02, d13);
-}
-template <class P, bool INV> __device__ __forceinline__ void dft5(typename P::T* v) {
-  using T = typename P::T;
-  const T a0 = v[0];
-  const T t1 = P::add(v[1], v[4]), t2 = P::add(v[2], v[3]);
-  const T t3 = P::sub(v[1], v[4]), t4 = P::sub(v[2], v[3]);
-  // cos(2pi/5), cos(4pi/5), sin(2pi/5), sin(4pi/5)
-  const T b1 = P::add(a0, P::add(P::mulr(t1, AIM_RC(0.30901699437494742410)), P::mulr(t2, AIM_RC(-0.80901699437494742410))));
-  const T b2 = P::add(a0, P::add(P::mulr(t1, AIM_RC(-0.80901699437494742410)), P::mulr(t2, AIM_RC(0.30901699437494742410))));
-  const T u1 = P::add(P::mulr(t3, AIM_RC(0.95105651629515357212)), P::mulr(t4, AIM_RC(0.58778525229247312917)));
-  const T u2 = P::sub(P::mulr(t3, AIM_RC(0.58778525229247312917)), P::mulr(t4, AIM_RC(0.95105651629515357212)));
-  const T e1 = P::template mul_mi<INV>(u1), e2 = P::template mul_mi<INV>(u2);
-  v[0] = P::add(a0, P::add(t1, t2));
-  v[1] = P::add(b1, e1);
-  v[4] = P::sub(b1, e1);
-  v[2] = P::add(b2, e2);
-  v[3] = P::sub(b2, e2);
 }
 
 // One Stockham stage over `count` pencils of length L in shared memory.
@@ -257,11 +159,31 @@ __device__ typename P::S* stockham(typename P::S* b0, typename P::S* b1, const F
 }
 
 // ------------------------------------------------------------------ strided pass
-struct StridedArgs {
-  int n_in, n_out;  // samples read (rest zero) / samples written
-  int X, A;         // contiguous extent, other-axis extent
-  long long sG_in, sA_in, sP_in;
-  long long sG_out, sA_out, sP_out;
+using StridedArgs = StridedArgs4;
+
+// Four-step kernels per policy (fft4_p32.cu, fft4_p64.cu, fft4_pff.cu):
+// 1 launched, 0 no kernel for this length, < 0 minus an error code.
+int fft4_strided_p32(aim_ctx*, const char*, bool, const float2*, float2*, double2*, const StridedArgs4&, int, int,
+                     const float2*);
+int fft4_strided_p64(aim_ctx*, const char*, bool, const double2*, double2*, double2*, const StridedArgs4&, int, int,
+                     const double2*);
+int fft4_strided_pff(aim_ctx*, const char*, bool, const float4*, float4*, double2*, const StridedArgs4&, int, int,
+                     const float4*);
+int fft4_x_p32(aim_ctx*, const char*, float2*, const XArgs4&, int, const float2*, const float2*);
+int fft4_x_p64(aim_ctx*, const char*, double2*, const XArgs4&, int, const double2*, const double2*);
+int fft4_x_pff(aim_ctx*, const char*, float4*, const XArgs4&, int, const float4*, const float4*);
+template <class P> struct Fft4;
+template <> struct Fft4<P32> {
+  template <class... A> static int strided(A... a) { return fft4_strided_p32(a...); }
+  template <class... A> static int x(A... a) { return fft4_x_p32(a...); }
+};
+template <> struct Fft4<P64> {
+  template <class... A> static int strided(A... a) { return fft4_strided_p64(a...); }
+  template <class... A> static int x(A... a) { return fft4_x_p64(a...); }
+};
+template <> struct Fft4<PFF> {
+  template <class... A> static int strided(A... a) { return fft4_strided_pff(a...); }
+  template <class... A> static int x(A... a) { return fft4_x_pff(a...); }
 };
 
 // Output element conversion of a pass (identity, or float-float -> FP64).
@@ -400,6 +322,37 @@ static int launch_x(aim_ctx* c, const char* name, typename P::S* buf, XArgs a, c
 
 // phi64: when non-null (float-float policy only), the last inverse pass writes
 // Phi there in FP64 instead of back into g0.
+// Strided pass: the four-step kernel when the length has one, else Stockham.
+template <class P, bool INV, class O = typename P::S>
+static int strided_pass(aim_ctx* c, const char* name, const typename P::S* in, O* out, const StridedArgs& a, int G,
+                        const FftPlan* plan_dev, int L, const typename P::S* tw) {
+  // The float-float strided four-step kernels need ~120 registers per thread;
+  // the Stockham kernels (54) keep twice the warps resident and run faster.
+  if (c->fourstep && !std::is_same<P, PFF>::value) {
+    int rc;
+    if constexpr (std::is_same<O, double2>::value && !std::is_same<typename P::S, double2>::value)
+      rc = Fft4<P>::strided(c, name, INV, in, (typename P::S*)nullptr, out, a, G, L, tw);
+    else
+      rc = Fft4<P>::strided(c, name, INV, in, out, (double2*)nullptr, a, G, L, tw);
+    if (rc == 1) return AIM_OK;
+    if (rc < 0) return -rc;
+  }
+  return launch_strided<P, INV, O>(c, name, in, out, a, G, plan_dev, L, tw);
+}
+
+template <class P>
+static int x_pass(aim_ctx* c, const char* name, typename P::S* buf, XArgs a, const FftPlan* plan_dev, int L,
+                  const typename P::S* ghat, const typename P::S* tw) {
+  if (c->fourstep) {
+    XArgs4 x4{};
+    x4.nx = a.nx; x4.Ly = a.rows_y; x4.Lz = a.rows_z; x4.G = a.G; x4.sG = a.sG; x4.hx = a.hx; x4.hy = a.hy;
+    const int rc = Fft4<P>::x(c, name, buf, x4, L, ghat, tw);
+    if (rc == 1) return AIM_OK;
+    if (rc < 0) return -rc;
+  }
+  return launch_x<P, 0>(c, name, buf, a, plan_dev, L, ghat, tw);
+}
+
 template <class P>
 static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P::S* g2, const typename P::S* ghat,
                     typename P::S* const* tw, int G, double2* phi64 = nullptr) {
@@ -411,28 +364,28 @@ static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P
     a.n_in = nz; a.n_out = Lz; a.X = nx; a.A = ny;
     a.sG_in = (long long)nz * ny * nx; a.sA_in = nx; a.sP_in = (long long)ny * nx;
     a.sG_out = (long long)Lz * ny * nx; a.sA_out = nx; a.sP_out = (long long)ny * nx;
-    AIM_TRY((launch_strided<P, false>(c, "fft_z_fwd", g0, g1, a, G, pd + 2, Lz, tw[2])));
+    AIM_TRY((strided_pass<P, false>(c, "fft_z_fwd", g0, g1, a, G, pd + 2, Lz, tw[2])));
   }
   {  // y forward: g1 [G][Lz][ny][nx] -> g2 [G][Lz][Ly][nx]
     StridedArgs a{};
     a.n_in = ny; a.n_out = Ly; a.X = nx; a.A = Lz;
     a.sG_in = (long long)Lz * ny * nx; a.sA_in = (long long)ny * nx; a.sP_in = nx;
     a.sG_out = (long long)Lz * Ly * nx; a.sA_out = (long long)Ly * nx; a.sP_out = nx;
-    AIM_TRY((launch_strided<P, false>(c, "fft_y_fwd", g1, g2, a, G, pd + 1, Ly, tw[1])));
+    AIM_TRY((strided_pass<P, false>(c, "fft_y_fwd", g1, g2, a, G, pd + 1, Ly, tw[1])));
   }
   {  // x: forward, times Ghat, inverse, in place on g2
     XArgs a{};
     a.nx = nx; a.rows_y = Ly; a.rows_z = Lz; a.G = G;
     a.sG = (long long)Lz * Ly * nx;
     a.hx = Lx / 2 + 1; a.hy = Ly / 2 + 1; a.hz = Lz / 2 + 1;
-    AIM_TRY((launch_x<P, 0>(c, "fft_x_conv", g2, a, pd + 0, Lx, ghat, tw[0])));
+    AIM_TRY((x_pass<P>(c, "fft_x_conv", g2, a, pd + 0, Lx, ghat, tw[0])));
   }
   {  // y inverse: g2 -> g1 [G][Lz][ny][nx]
     StridedArgs a{};
     a.n_in = Ly; a.n_out = ny; a.X = nx; a.A = Lz;
     a.sG_in = (long long)Lz * Ly * nx; a.sA_in = (long long)Ly * nx; a.sP_in = nx;
     a.sG_out = (long long)Lz * ny * nx; a.sA_out = (long long)ny * nx; a.sP_out = nx;
-    AIM_TRY((launch_strided<P, true>(c, "fft_y_inv", g2, g1, a, G, pd + 1, Ly, tw[1])));
+    AIM_TRY((strided_pass<P, true>(c, "fft_y_inv", g2, g1, a, G, pd + 1, Ly, tw[1])));
   }
   {  // z inverse: g1 -> g0 [G][nz][ny][nx]
     StridedArgs a{};
@@ -440,9 +393,9 @@ static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P
     a.sG_in = (long long)Lz * ny * nx; a.sA_in = nx; a.sP_in = (long long)ny * nx;
     a.sG_out = (long long)nz * ny * nx; a.sA_out = nx; a.sP_out = (long long)ny * nx;
     if constexpr (std::is_same<P, PFF>::value) {
-      if (phi64) return launch_strided<P, true, double2>(c, "fft_z_inv", g1, phi64, a, G, pd + 2, Lz, tw[2]);
+      if (phi64) return strided_pass<P, true, double2>(c, "fft_z_inv", g1, phi64, a, G, pd + 2, Lz, tw[2]);
     }
-    AIM_TRY((launch_strided<P, true>(c, "fft_z_inv", g1, g0, a, G, pd + 2, Lz, tw[2])));
+    AIM_TRY((strided_pass<P, true>(c, "fft_z_inv", g1, g0, a, G, pd + 2, Lz, tw[2])));
   }
   return AIM_OK;
 }

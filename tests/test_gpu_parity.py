@@ -138,6 +138,39 @@ def test_other_stencil_orders(M):
         assert rel(y, op.matvec(x)) <= 1e-12
 
 
+@pytest.mark.parametrize("nrhs", [8, 9, 17, 70])
+def test_many_rhs_products(nrhs):
+    """Batches of 8 to 70 right-hand sides (lanes, tiles and grid chunks cover every RHS)."""
+    v, t = plate_mesh(1.0, 9)
+    ctx, op = make(v, t, max_rhs=nrhs)
+    x = random_complex((nrhs, ctx.N), 40 + nrhs)
+    ref = op.matvec(x)
+    for prec in WIDE:
+        y = g.aim_matvec(ctx, torch.from_numpy(x).cuda(), precision=prec).cpu().numpy()
+        assert rel(y, ref) <= 1e-12
+    y32 = g.aim_matvec(ctx, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
+    assert rel(y32, op.matvec(x.astype(np.complex64).astype(np.complex128))) <= 1e-5
+    # each right-hand side on its own equals its column of the batch
+    for b in (0, nrhs - 1):
+        yb = g.aim_matvec(ctx, torch.from_numpy(x[b : b + 1]).cuda(), precision=g.AIM_C128).cpu().numpy()
+        assert rel(yb[0], ref[b]) <= 1e-12
+
+
+def test_stockham_fallback_length():
+    """A padded length outside the four-step menu (18) runs the Stockham kernels."""
+    v, t = plate_mesh(0.7, 6)
+    ctx, op = make(v, t, max_rhs=2)
+    n, L, _ = g.aim_grid_info(ctx)
+    assert L[0] == 18 and L[1] == 18 and L[2] == 5
+    x = random_complex((2, ctx.N), 18)
+    ref = op.matvec(x)
+    for prec in WIDE:
+        y = g.aim_matvec(ctx, torch.from_numpy(x).cuda(), precision=prec).cpu().numpy()
+        assert rel(y, ref) <= 1e-12
+    y32 = g.aim_matvec(ctx, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
+    assert rel(y32, ref) <= 1e-5
+
+
 def test_all_pairs_near_equals_dense():
     """Near radius beyond the body: the product is the dense Galerkin matrix."""
     from oracle.efie import dense_Z
