@@ -58,11 +58,13 @@ def mesh_for(kind, size):
 
 
 # ---------------------------------------------------------------- kernel models
-def kernel_models(N, n, L, nnz, nent, S, nrhs, e):
+def kernel_models(N, n, L, nnz, nent, S, nrhs, e, touched=None):
     """Algorithmic bytes and flops per launch of each product kernel.
 
     e = bytes per complex value, w = bytes per real weight.  FFT flops use
-    the 5 L log2 L convention per length-L transform.
+    the 5 L log2 L convention per length-L transform.  touched = grid nodes
+    that lie in some stencil (the interpolation reads only those; the
+    projection writes every node, zeros included); default all nodes.
     """
     nx, ny, nz = n
     Lx, Ly, Lz = L
@@ -78,16 +80,22 @@ def kernel_models(N, n, L, nnz, nent, S, nrhs, e):
     m["fft_x_conv"] = (2 * G * Lz * Ly * nx * e + oct_ * e, G * Ly * Lz * (10.0 * Lx * lg(Lx) + 6.0 * Lx))
     m["fft_y_inv"] = m["fft_y_fwd"]
     m["fft_z_inv"] = m["fft_z_fwd"]
+    m["transpose_phi"] = (2.0 * G * Nc * e, 0.0)
+    m["transpose_x"] = (2.0 * nrhs * N * e, 0.0)
+    m["x_to_ff"] = (2.0 * nrhs * N * 16, 0.0)
+    nt = Nc if touched is None else touched
     m["interp_near"] = (
-        G * Nc * e + N * 4 * S * w + N * 4 + nnz * (e + 4) + (N + 1) * 4 + 2 * nrhs * N * e,
+        G * nt * e + N * 4 * S * w + N * 4 + nnz * (e + 4) + (N + 1) * 4 + 2 * nrhs * N * e,
         nrhs * (16.0 * N * S + 8.0 * nnz),
     )
     return m
 
 
+FFT_SOURCES = ("fft.cu", "common.h", "ff.h", "fft_policy.h", "fft4.cuh", "fft4_launch.cuh", "fft4_p32.cu",
+               "fft4_p64.cu", "fft4_pff.cu")
 KERNEL_SOURCES = {
-    "proj_gather": ("matvec.cu", "common.h"),
-    "interp_near": ("matvec.cu", "common.h"),
+    "proj_gather": ("matvec.cu", "common.h", "ff.h"),
+    "interp_near": ("matvec.cu", "common.h", "ff.h"),
 }
 
 
@@ -135,8 +143,8 @@ def ff_fft_flops(kernel, n, L, nrhs):
 
 
 def source_digest(kernel):
-    """Hash of the source files a kernel is built from (fft.cu for the FFT passes)."""
-    files = KERNEL_SOURCES.get(kernel, ("fft.cu", "common.h"))
+    """Hash of the source files a kernel is built from (FFT_SOURCES for the FFT passes)."""
+    files = KERNEL_SOURCES.get(kernel, FFT_SOURCES)
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1010_1456_gb300", "csrc")
     for f in files:
@@ -295,6 +303,23 @@ def solve_section(g, ctx, kind, size, nrhs, P0):
         out[name] = {"time_s": t, "solves_per_s": 1.0 / t, "rhs_per_s": nrhs / t, "iterations": info["iterations"],
                      "restarts": info["restarts"], "max_rel_res": float(info["rel_res"].max()),
                      "converged": bool(info["converged"].all())}
+    # where the mixed solve's time goes: device time per kernel (a second,
+    # profiled run) against its wall time
+    g.aim_set_precision(ctx, g.AIM_C64)
+    g.aim_profile(ctx, 2)
+    g.aim_profile(ctx, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.aim_solve(ctx, V, 1e-6, raise_on_noconv=False)
+    wall = time.perf_counter() - t0
+    g.aim_profile(ctx, 0)
+    prof = g.aim_profile_read(ctx)
+    g.aim_profile(ctx, 2)
+    dev = sum(ms for _, ms in prof.values())
+    top = sorted(prof.items(), key=lambda kv: -kv[1][1])[:12]
+    out["mixed_profile"] = {"wall_s_profiled": wall, "device_s": dev / 1e3,
+                            "launches": int(sum(c for c, _ in prof.values())),
+                            "top": {k: {"launches": c, "ms": round(ms, 3)} for k, (c, ms) in top}}
     g.aim_set_precision(ctx, P0)
     out["err_thth_mixed_vs_plain"] = float(np.max(g.err_thth(sig["mixed_c64_fp64_refined"], sig["plain_fp64"], w)))
     out["err_thth_float_float_vs_plain"] = float(np.max(g.err_thth(sig["fp64_float_float_fft"], sig["plain_fp64"], w)))
@@ -388,6 +413,42 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- our arm
+FFT_KERNEL_NAMES = {1: "stockham", 2: "fourstep", 3: "fourstep_small"}
+
+
+def cufft_comparison(torch, dev, stream, L, nrhs, wide, kernels, flush, reps=5, max_gb=8.0):
+    """Timed comparison only: the same convolution on the full zero-padded grids
+    through cuFFT (torch.fft: forward 3-D FFT, product with a spectrum, inverse),
+    against the five pruned passes of this library."""
+    G = 4 * nrhs
+    dt = torch.complex128 if wide else torch.complex64
+    esize = 16 if wide else 8
+    gb = G * int(np.prod(L)) * esize / 1e9
+    ours = sum(kernels[k]["avg_ms"] for k in ("fft_z_fwd", "fft_y_fwd", "fft_x_conv", "fft_y_inv", "fft_z_inv")
+               if k in kernels)
+    if gb > max_gb:
+        return {"skipped": f"padded batch of {gb:.1f} GB (> {max_gb} GB)", "ours_fft_ms": ours}
+    Lx, Ly, Lz = L
+    a = torch.randn(G, Lz, Ly, Lx, dtype=dt, device=dev)
+    spec = torch.randn(Lz, Ly, Lx, dtype=dt, device=dev)
+    for _ in range(3):
+        torch.fft.ifftn(torch.fft.fftn(a, dim=(1, 2, 3)) * spec, dim=(1, 2, 3))
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        b, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b.record(stream)
+        torch.fft.ifftn(torch.fft.fftn(a, dim=(1, 2, 3)) * spec, dim=(1, 2, 3))
+        e_.record(stream)
+        torch.cuda.synchronize()
+        tot += b.elapsed_time(e_)
+    del a, spec
+    torch.cuda.empty_cache()
+    return {"what": "cuFFT (torch.fft) forward + spectral product + inverse on the unpruned padded grids",
+            "cufft_ms": tot / reps, "ours_fft_ms": ours, "speedup_ours": (tot / reps) / ours if ours else None}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -412,6 +473,16 @@ def run_ours(args, rank, world, local_rank):
     xh = random_complex((nrhs, N), 1000 + rank).astype(np.complex128 if wide else np.complex64)
     x = torch.from_numpy(xh).to(dev)
     y = torch.empty_like(x)
+    tune = None
+    if args.autotune:
+        t0 = time.perf_counter()
+        chosen, tune_ms = g.aim_autotune(ctx, P, nrhs=nrhs, reps=3)
+        tune = {"seconds": round(time.perf_counter() - t0, 2),
+                "kernels": {p_: FFT_KERNEL_NAMES[k] for p_, k in zip(g.FFT_PASSES, chosen)},
+                "pass_ms": {p_: {FFT_KERNEL_NAMES[k]: round(float(tune_ms[i, k]), 4) for k in (1, 2, 3)
+                                 if tune_ms[i, k] > 0} for i, p_ in enumerate(g.FFT_PASSES)}}
+    else:
+        chosen = g.aim_fft_config(ctx, P)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         g.aim_matvec(ctx, x, y, precision=P)
@@ -445,6 +516,8 @@ def run_ours(args, rank, world, local_rank):
         VP = PRECISION[vname]
         xv = torch.from_numpy(xh.astype(np.complex64 if vname == "c64" else np.complex128)).to(dev)
         yv = torch.empty_like(xv)
+        if args.autotune:
+            g.aim_autotune(ctx, VP, nrhs=nrhs, reps=3)
         for _ in range(3):
             g.aim_matvec(ctx, xv, yv, precision=VP)
         torch.cuda.synchronize()
@@ -472,8 +545,10 @@ def run_ours(args, rank, world, local_rank):
            "h2d_bytes_per_step": int(xh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
 
     # roofline of the dominant kernel
-    nent = int(g.aim_export(ctx, g.AIM_EXPORT_PROJ_PTR)[-1])
-    models = kernel_models(N, n, L, nnz, nent, 27, nrhs, e)
+    pptr = g.aim_export(ctx, g.AIM_EXPORT_PROJ_PTR)
+    nent = int(pptr[-1])
+    touched = int(np.count_nonzero(np.diff(pptr)))
+    models = kernel_models(N, n, L, nnz, nent, 27, nrhs, e, touched)
     kernels = {k: {"launches": c, "avg_ms": ms / max(c, 1), "share": ms / max(sum(v[1] for v in prof.values()), 1e-30)}
                for k, (c, ms) in prof.items()}
     dom = max(kernels, key=lambda k: kernels[k]["share"])
@@ -537,7 +612,10 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "grid": n, "padded": L, "nnz_near": nnz, "nrhs": nrhs,
                    "M": 2, "h_lambda": H, "near_radius_h": 3, "l2": "flushed between steps (256 MB write)",
-                   "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2)},
+                   "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
+                   "fft_kernels": {p_: FFT_KERNEL_NAMES[k] for p_, k in zip(g.FFT_PASSES, chosen)}},
+        "autotune": tune,
+        "cufft_comparison": cufft_comparison(torch, dev, stream, L, nrhs, wide, kernels, flush) if args.cufft else None,
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -565,6 +643,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve", type=int, default=1, help="1: also time plain and mixed solves")
     ap.add_argument("--variants", type=int, default=1, help="1: also time the other product precisions")
+    ap.add_argument("--autotune", type=int, default=1, help="1: autotune the FFT kernels before timing")
+    ap.add_argument("--cufft", type=int, default=1, help="1: also time the unpruned cuFFT convolution")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--serve", action="store_true", help="run the serving stream instead of the product benchmark")
     ap.add_argument("--serve-sizes", choices=sorted(SERVE_SIZES), default="small")

@@ -220,6 +220,40 @@ int aim_profile_read(aim_ctx* ctx, int max_kernels, char* names, int64_t* launch
 int aim_probe_fma_peak(int which, double* tflops);
 
 /*
+ * FFT kernel selection.  The paper (Section 4.1) runs the convolution's
+ * FFTs through a library and does not fix the transform; the choice here
+ * changes the product only by rounding.  For each precision, each of the
+ * five passes of the convolution (z forward, y forward, the fused x pass --
+ * forward transform, spectral product, inverse -- y inverse, z inverse, in
+ * that order) runs one of:
+ *   AIM_FFT_AUTO            the built-in rule (default): four-step, except
+ *                           the float-float strided passes, which use Stockham;
+ *   AIM_FFT_STOCKHAM        mixed-radix Stockham kernel (any 2,3,5-smooth length);
+ *   AIM_FFT_FOURSTEP        four-step register kernel (compiled lengths; any
+ *                           other length falls back to the Stockham kernel);
+ *   AIM_FFT_FOURSTEP_SMALL  four-step with blocks of at most 128 threads
+ *                           (the x pass; elsewhere as AIM_FFT_FOURSTEP).
+ * aim_fft_config sets (set != NULL, [5]) and/or reads (get != NULL, [5]) the
+ * choices of one precision; get receives them with AUTO resolved by the rule.
+ */
+enum { AIM_FFT_AUTO = 0, AIM_FFT_STOCKHAM = 1, AIM_FFT_FOURSTEP = 2, AIM_FFT_FOURSTEP_SMALL = 3 };
+#define AIM_FFT_PASSES 5
+int aim_fft_config(aim_ctx* ctx, int precision, const int32_t* set, int32_t* get);
+
+/*
+ * Autotune the FFT kernels of one precision for products of nrhs vectors
+ * (1 <= nrhs <= opts.max_rhs, reps >= 1): pass by pass, each candidate
+ * kernel runs one warm-up product and `reps` products timed with CUDA events
+ * on the context stream, and the fastest stays selected.  Allocates (and
+ * frees) one input and one output batch, and the precision's grids like the
+ * first aim_matvec.  kernel_out [5] (may be NULL) receives the choices;
+ * ms_out [5][4] (may be NULL) the mean time in ms of each pass under each
+ * AIM_FFT_* value (-1 where not tried).  The profiler's totals and on/off
+ * state are left as they were.  Synchronises.
+ */
+int aim_autotune(aim_ctx* ctx, int precision, int nrhs, int reps, int32_t* kernel_out, double* ms_out);
+
+/*
  * Complex64 AIM product (same result as aim_matvec with AIM_C64) that
  * allocates no device memory.  The paper has no counterpart: this serves
  * callers that cannot let the library call cudaMalloc, because their device

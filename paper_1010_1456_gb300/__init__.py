@@ -281,6 +281,32 @@ def aim_probe_fma_peak(which=64):
     return float(t.value)
 
 
+AIM_FFT_AUTO, AIM_FFT_STOCKHAM, AIM_FFT_FOURSTEP, AIM_FFT_FOURSTEP_SMALL = 0, 1, 2, 3
+FFT_PASSES = ("fft_z_fwd", "fft_y_fwd", "fft_x_conv", "fft_y_inv", "fft_z_inv")
+
+
+def aim_fft_config(ctx, precision=AIM_C128, kernels=None):
+    """Set (kernels: five AIM_FFT_* values, or None) and return the FFT kernel of each pass."""
+    lib = load()
+    get = (C.c_int32 * 5)()
+    st = None
+    if kernels is not None:
+        if len(kernels) != 5:
+            raise ValueError("kernels: one AIM_FFT_* value per pass (5)")
+        st = (C.c_int32 * 5)(*[int(k) for k in kernels])
+    check(lib.aim_fft_config(ctx.handle, int(precision), st, get), "aim_fft_config")
+    return [int(k) for k in get]
+
+
+def aim_autotune(ctx, precision=AIM_C128, nrhs=1, reps=3):
+    """Time each FFT kernel per pass, keep the fastest.  Returns (kernels, ms[5][4])."""
+    lib = load()
+    k = (C.c_int32 * 5)()
+    ms = (C.c_double * 20)()
+    check(lib.aim_autotune(ctx.handle, int(precision), int(nrhs), int(reps), k, ms), "aim_autotune")
+    return [int(v) for v in k], np.array(list(ms)).reshape(5, 4)
+
+
 def rcs_direction_grid(n_theta, n_phi=None):
     """Directions and weights for eq. (1): Gauss-Legendre nodes in cos(theta),
     uniform phi.  Returns (theta, phi, weight) flattened theta-major."""

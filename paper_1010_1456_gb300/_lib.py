@@ -65,6 +65,8 @@ SIGNATURES = {
     "aim_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.c_char_p, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int)]),
     "aim_probe_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "aim_fft_config": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "aim_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "aim_strerror": (C.c_char_p, [C.c_int]),
     "aim_last_error": (C.c_char_p, []),
 }

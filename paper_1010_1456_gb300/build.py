@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaim.so")
-SOURCES = ["api.cu", "setup.cu", "fft.cu", "matvec.cu", "krylov.cu", "rcs.cu", "probe.cu", "profile.cu", "noalloc.cu", "fft4_p32.cu",
+SOURCES = ["api.cu", "setup.cu", "fft.cu", "matvec.cu", "krylov.cu", "rcs.cu", "probe.cu", "profile.cu", "noalloc.cu", "autotune.cu", "fft4_p32.cu",
            "fft4_p64.cu", "fft4_pff.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = [
@@ -46,7 +46,7 @@ def _newer(src_list, target):
 
 def build(verbose=False, force=False):
     os.makedirs(OUT_DIR, exist_ok=True)
-    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "aim.h"))
     objs = []
     jobs = []

@@ -26,6 +26,7 @@ template <typename R> static void free_prec(PrecData<R>& p) {
   cudaFree(p.lam); cudaFree(p.pnode_w); cudaFree(p.ghat); cudaFree(p.near_val);
   for (int d = 0; d < 3; ++d) cudaFree(p.tw[d]);
   cudaFree(p.grid0); cudaFree(p.grid1); cudaFree(p.grid2); cudaFree(p.xbuf); cudaFree(p.ybuf);
+  cudaFree(p.phiT); cudaFree(p.xT);
   p = PrecData<R>{};
 }
 
@@ -36,7 +37,8 @@ static void free_ctx(aim_ctx* c) {
   free_prec(c->p32);
   cudaFree(c->pff.ghat);
   for (int d = 0; d < 3; ++d) cudaFree(c->pff.tw[d]);
-  cudaFree(c->pff.grid0); cudaFree(c->pff.grid1); cudaFree(c->pff.grid2); cudaFree(c->pff.phi64);
+  cudaFree(c->pff.grid0); cudaFree(c->pff.grid1); cudaFree(c->pff.grid2);
+  cudaFree(c->pff.pnode_w); cudaFree(c->pff.lam); cudaFree(c->pff.near_val); cudaFree(c->pff.xff);
   cudaFree(c->plan_dev);
   free_krylov(c);
   profile_free(c);

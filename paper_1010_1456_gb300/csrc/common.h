@@ -87,17 +87,25 @@ template <typename R> struct PrecData {
   cplx<R>* grid2 = nullptr;       // [B][4][Lz][Ly][nx]
   cplx<R>* xbuf = nullptr;        // [B][N] staging for host/solver conversions
   cplx<R>* ybuf = nullptr;        // [B][N]
+  cplx<R>* phiT = nullptr;        // [4][nz][ny][nx][B] Phi, RHS-minor (many-RHS interpolation)
+  cplx<R>* xT = nullptr;          // [N][B] x, RHS-minor
 };
 
-// Grids, spectrum and twiddles of the float-float path (AIM_C128); its
-// weights, near entries and vectors are the complex128 ones.
+// Float-float copies of the AIM_C128 path: spectrum, twiddles and grids of
+// the FFT passes, and (rounded once from the FP64 setup arrays) the weights
+// and near entries of the projection and interpolation.  A float-float real
+// is (hi, lo) with value hi + lo; a complex one is float4 (re.hi, re.lo,
+// im.hi, im.lo).
 struct FFData {
   float4* ghat = nullptr;
   float4* tw[3] = {nullptr, nullptr, nullptr};
   float4* grid0 = nullptr;
   float4* grid1 = nullptr;
   float4* grid2 = nullptr;
-  double2* phi64 = nullptr;  // [B][4][nz][ny][nx] Phi in FP64, read by the interpolation
+  float4* pnode_w = nullptr;   // [nent][2]: (x, y, z, charge) high parts, then low parts
+  float2* lam = nullptr;       // [N][4][S]
+  float4* near_val = nullptr;  // [nnz]
+  float4* xff = nullptr;       // [B][N] the product's input
 };
 
 // Per-kernel timing with CUDA events on the context stream (aim_profile).
@@ -148,7 +156,11 @@ struct aim_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
   int64_t launches = 0;
-  bool fourstep = true;  // four-step FFT kernels for the lengths that have them
+  // FFT kernel per arithmetic policy (complex64, native FP64, float-float) and
+  // pass (z fwd, y fwd, x, y inv, z inv): AIM_FFT_AUTO, AIM_FFT_STOCKHAM,
+  // AIM_FFT_FOURSTEP or AIM_FFT_FOURSTEP_SMALL (set by aim_fft_config and
+  // aim_autotune).
+  int32_t fft_kernel[3][AIM_FFT_PASSES] = {};
   aim::FftPlan plan[3];
   aim::FftPlan* plan_dev = nullptr;  // device copy of plan[3]
 
@@ -221,6 +233,10 @@ int fft_convolve_c128(aim_ctx* c, int G);
 int fft_convolve_ff(aim_ctx* c, int G);
 // complex64 product and convolution on caller-provided grids (noalloc.cu)
 int fft_convolve_c64_bufs(aim_ctx* c, int G, float2* g0, float2* g1, float2* g2);
+// FFT kernel tables: policy index of a precision (0 complex64, 1 native FP64,
+// 2 float-float) and the kernel a pass runs (AIM_FFT_AUTO resolved).
+int fft_policy_of(int precision);
+int fft_kernel_for(const aim_ctx* c, int pol, int pass);
 int matvec_c64_bufs(aim_ctx* c, const float2* x, float2* y, int nrhs, float2* g0, float2* g1, float2* g2);
 int build_ghat(aim_ctx* c);
 // krylov.cu

@@ -81,6 +81,19 @@ __device__ __forceinline__ ff ff_dot2(ff a, ff b, ff c, ff d) {
   return ff_fast_two_sum(s.hi, e);
 }
 
+// acc + a * b with one closing renormalisation: the product's rounding
+// error is recovered with FMA and carried in the low part, so the result is
+// good to about 2^-47 (|acc| + |a b|).
+__device__ __forceinline__ ff ff_mad(ff a, ff b, ff acc) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const ff s = ff_two_sum(acc.hi, p);
+  const float t = __fadd_rn(__fadd_rn(s.lo, acc.lo), e);
+  return ff_fast_two_sum(s.hi, t);
+}
+
 __device__ __forceinline__ ff ff_from_double(double v) {
   const float hi = __double2float_rn(v);
   const float lo = __double2float_rn(v - (double)hi);

@@ -163,15 +163,15 @@ using StridedArgs = StridedArgs4;
 
 // Four-step kernels per policy (fft4_p32.cu, fft4_p64.cu, fft4_pff.cu):
 // 1 launched, 0 no kernel for this length, < 0 minus an error code.
-int fft4_strided_p32(aim_ctx*, const char*, bool, const float2*, float2*, double2*, const StridedArgs4&, int, int,
+int fft4_strided_p32(aim_ctx*, const char*, bool, const float2*, float2*, const StridedArgs4&, int, int,
                      const float2*);
-int fft4_strided_p64(aim_ctx*, const char*, bool, const double2*, double2*, double2*, const StridedArgs4&, int, int,
+int fft4_strided_p64(aim_ctx*, const char*, bool, const double2*, double2*, const StridedArgs4&, int, int,
                      const double2*);
-int fft4_strided_pff(aim_ctx*, const char*, bool, const float4*, float4*, double2*, const StridedArgs4&, int, int,
+int fft4_strided_pff(aim_ctx*, const char*, bool, const float4*, float4*, const StridedArgs4&, int, int,
                      const float4*);
-int fft4_x_p32(aim_ctx*, const char*, float2*, const XArgs4&, int, const float2*, const float2*);
-int fft4_x_p64(aim_ctx*, const char*, double2*, const XArgs4&, int, const double2*, const double2*);
-int fft4_x_pff(aim_ctx*, const char*, float4*, const XArgs4&, int, const float4*, const float4*);
+int fft4_x_p32(aim_ctx*, const char*, float2*, const XArgs4&, int, const float2*, const float2*, int);
+int fft4_x_p64(aim_ctx*, const char*, double2*, const XArgs4&, int, const double2*, const double2*, int);
+int fft4_x_pff(aim_ctx*, const char*, float4*, const XArgs4&, int, const float4*, const float4*, int);
 template <class P> struct Fft4;
 template <> struct Fft4<P32> {
   template <class... A> static int strided(A... a) { return fft4_strided_p32(a...); }
@@ -186,14 +186,9 @@ template <> struct Fft4<PFF> {
   template <class... A> static int x(A... a) { return fft4_x_pff(a...); }
 };
 
-// Output element conversion of a pass (identity, or float-float -> FP64).
+// Output element conversion of a pass (identity for every policy in use).
 template <class S, class O> struct OutConv {
   __device__ static O f(const S& s) { return s; }
-};
-template <> struct OutConv<float4, double2> {
-  __device__ static double2 f(const float4& s) {
-    return make_double2((double)s.x + (double)s.y, (double)s.z + (double)s.w);
-  }
 };
 
 template <class P, bool INV, class O>
@@ -320,20 +315,26 @@ static int launch_x(aim_ctx* c, const char* name, typename P::S* buf, XArgs a, c
   return launch_check(c, name);
 }
 
-// phi64: when non-null (float-float policy only), the last inverse pass writes
-// Phi there in FP64 instead of back into g0.
-// Strided pass: the four-step kernel when the length has one, else Stockham.
+int fft_policy_of(int precision) { return precision == AIM_C64 ? 0 : precision == AIM_C128_F64 ? 1 : 2; }
+
+int fft_kernel_for(const aim_ctx* c, int pol, int pass) {
+  const int k = c->fft_kernel[pol][pass];
+  if (k != AIM_FFT_AUTO) return k;
+  // The float-float strided four-step kernels need 110-160 registers per
+  // thread; the Stockham kernels (54) keep more warps resident.
+  return (pol == 2 && pass != 2) ? AIM_FFT_STOCKHAM : AIM_FFT_FOURSTEP;
+}
+
+template <class P> constexpr int policy_index() {
+  return std::is_same<P, P32>::value ? 0 : std::is_same<P, P64>::value ? 1 : 2;
+}
+
+// Strided pass with the selected kernel (four-step where the length has one).
 template <class P, bool INV, class O = typename P::S>
-static int strided_pass(aim_ctx* c, const char* name, const typename P::S* in, O* out, const StridedArgs& a, int G,
-                        const FftPlan* plan_dev, int L, const typename P::S* tw) {
-  // The float-float strided four-step kernels need ~120 registers per thread;
-  // the Stockham kernels (54) keep twice the warps resident and run faster.
-  if (c->fourstep && !std::is_same<P, PFF>::value) {
-    int rc;
-    if constexpr (std::is_same<O, double2>::value && !std::is_same<typename P::S, double2>::value)
-      rc = Fft4<P>::strided(c, name, INV, in, (typename P::S*)nullptr, out, a, G, L, tw);
-    else
-      rc = Fft4<P>::strided(c, name, INV, in, out, (double2*)nullptr, a, G, L, tw);
+static int strided_pass(aim_ctx* c, int pass, const char* name, const typename P::S* in, O* out,
+                        const StridedArgs& a, int G, const FftPlan* plan_dev, int L, const typename P::S* tw) {
+  if (fft_kernel_for(c, policy_index<P>(), pass) != AIM_FFT_STOCKHAM) {
+    const int rc = Fft4<P>::strided(c, name, INV, in, out, a, G, L, tw);
     if (rc == 1) return AIM_OK;
     if (rc < 0) return -rc;
   }
@@ -343,10 +344,11 @@ static int strided_pass(aim_ctx* c, const char* name, const typename P::S* in, O
 template <class P>
 static int x_pass(aim_ctx* c, const char* name, typename P::S* buf, XArgs a, const FftPlan* plan_dev, int L,
                   const typename P::S* ghat, const typename P::S* tw) {
-  if (c->fourstep) {
+  const int k = fft_kernel_for(c, policy_index<P>(), 2);
+  if (k != AIM_FFT_STOCKHAM) {
     XArgs4 x4{};
     x4.nx = a.nx; x4.Ly = a.rows_y; x4.Lz = a.rows_z; x4.G = a.G; x4.sG = a.sG; x4.hx = a.hx; x4.hy = a.hy;
-    const int rc = Fft4<P>::x(c, name, buf, x4, L, ghat, tw);
+    const int rc = Fft4<P>::x(c, name, buf, x4, L, ghat, tw, k == AIM_FFT_FOURSTEP_SMALL ? 128 : 256);
     if (rc == 1) return AIM_OK;
     if (rc < 0) return -rc;
   }
@@ -355,7 +357,7 @@ static int x_pass(aim_ctx* c, const char* name, typename P::S* buf, XArgs a, con
 
 template <class P>
 static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P::S* g2, const typename P::S* ghat,
-                    typename P::S* const* tw, int G, double2* phi64 = nullptr) {
+                    typename P::S* const* tw, int G) {
   const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
   const int Lx = c->L[0], Ly = c->L[1], Lz = c->L[2];
   const FftPlan* pd = c->plan_dev;
@@ -364,14 +366,14 @@ static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P
     a.n_in = nz; a.n_out = Lz; a.X = nx; a.A = ny;
     a.sG_in = (long long)nz * ny * nx; a.sA_in = nx; a.sP_in = (long long)ny * nx;
     a.sG_out = (long long)Lz * ny * nx; a.sA_out = nx; a.sP_out = (long long)ny * nx;
-    AIM_TRY((strided_pass<P, false>(c, "fft_z_fwd", g0, g1, a, G, pd + 2, Lz, tw[2])));
+    AIM_TRY((strided_pass<P, false>(c, 0, "fft_z_fwd", g0, g1, a, G, pd + 2, Lz, tw[2])));
   }
   {  // y forward: g1 [G][Lz][ny][nx] -> g2 [G][Lz][Ly][nx]
     StridedArgs a{};
     a.n_in = ny; a.n_out = Ly; a.X = nx; a.A = Lz;
     a.sG_in = (long long)Lz * ny * nx; a.sA_in = (long long)ny * nx; a.sP_in = nx;
     a.sG_out = (long long)Lz * Ly * nx; a.sA_out = (long long)Ly * nx; a.sP_out = nx;
-    AIM_TRY((strided_pass<P, false>(c, "fft_y_fwd", g1, g2, a, G, pd + 1, Ly, tw[1])));
+    AIM_TRY((strided_pass<P, false>(c, 1, "fft_y_fwd", g1, g2, a, G, pd + 1, Ly, tw[1])));
   }
   {  // x: forward, times Ghat, inverse, in place on g2
     XArgs a{};
@@ -385,17 +387,14 @@ static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P
     a.n_in = Ly; a.n_out = ny; a.X = nx; a.A = Lz;
     a.sG_in = (long long)Lz * Ly * nx; a.sA_in = (long long)Ly * nx; a.sP_in = nx;
     a.sG_out = (long long)Lz * ny * nx; a.sA_out = (long long)ny * nx; a.sP_out = nx;
-    AIM_TRY((strided_pass<P, true>(c, "fft_y_inv", g2, g1, a, G, pd + 1, Ly, tw[1])));
+    AIM_TRY((strided_pass<P, true>(c, 3, "fft_y_inv", g2, g1, a, G, pd + 1, Ly, tw[1])));
   }
   {  // z inverse: g1 -> g0 [G][nz][ny][nx]
     StridedArgs a{};
     a.n_in = Lz; a.n_out = nz; a.X = nx; a.A = ny;
     a.sG_in = (long long)Lz * ny * nx; a.sA_in = nx; a.sP_in = (long long)ny * nx;
     a.sG_out = (long long)nz * ny * nx; a.sA_out = nx; a.sP_out = (long long)ny * nx;
-    if constexpr (std::is_same<P, PFF>::value) {
-      if (phi64) return strided_pass<P, true, double2>(c, "fft_z_inv", g1, phi64, a, G, pd + 2, Lz, tw[2]);
-    }
-    AIM_TRY((strided_pass<P, true>(c, "fft_z_inv", g1, g0, a, G, pd + 2, Lz, tw[2])));
+    AIM_TRY((strided_pass<P, true>(c, 4, "fft_z_inv", g1, g0, a, G, pd + 2, Lz, tw[2])));
   }
   return AIM_OK;
 }
@@ -410,7 +409,7 @@ int fft_convolve_c128(aim_ctx* c, int G) {
 }
 int fft_convolve_ff(aim_ctx* c, int G) {
   FFData& p = c->pff;
-  return convolve<PFF>(c, p.grid0, p.grid1, p.grid2, p.ghat, p.tw, G, p.phi64);
+  return convolve<PFF>(c, p.grid0, p.grid1, p.grid2, p.ghat, p.tw, G);
 }
 
 // ------------------------------------------------------------------ Ghat

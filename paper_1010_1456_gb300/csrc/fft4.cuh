@@ -7,15 +7,15 @@
 //                            X[k1 + L1 k2] = result[k2].
 // (X[k1 + L1 k2] = sum_n2 w_L2^(n2 k2) w_L^(n2 k1) sum_n1 x[L2 n1 + n2] w_L1^(n1 k1).)
 // Compared with one shared-memory round trip per radix stage, a pencil makes
-// two round trips and all index arithmetic inside the register DFTs is
-// resolved at compile time.  These kernels serve the padded lengths in
+// one round trip (two for the fused forward-product-inverse x pass) and all
+// index arithmetic inside the register DFTs is resolved at compile time.  These kernels serve the padded lengths in
 // kFourStepLengths; other lengths use the Stockham kernels of fft.cu.
 //
 // fft4_strided: the z and y passes (pencil along a strided axis, TX
 // consecutive x columns per block, as in fft.cu).
 // fft4_x: the fused x pass: forward transform of the nx zero-padded samples
-// of RY rows (ky) x TG grids per block, product with the Ghat rows (folded
-// into step B of the forward transform), inverse transform, nx samples kept.
+// of RY rows (ky) x TG grids per block, product with the Ghat rows and the
+// inverse transform, nx samples kept.
 #pragma once
 
 #include "fft_policy.h"
@@ -39,86 +39,101 @@ struct XArgs4 {
 template <class S, class O> struct OutConv4 {
   __device__ static O f(const S& s) { return s; }
 };
-template <> struct OutConv4<float4, double2> {
-  __device__ static double2 f(const float4& s) {
-    return make_double2((double)s.x + (double)s.y, (double)s.z + (double)s.w);
-  }
-};
+
+// Columns per block of the strided kernels for length L: the policy's
+// preferred width, halved while one pencil set would need more than 48 KB of
+// shared memory (so long pencils still leave several blocks per SM).
+template <class P, int L> constexpr int strided_tx() {
+  int tx = P::kTX;
+  while (tx > 4 && (long long)L * tx * (long long)sizeof(typename P::S) > 48 * 1024) tx /= 2;
+  return tx;
+}
+
+// Shared-memory row length: odd, so lanes that walk a strided row hit
+// distinct banks.
+constexpr int odd_row(int n) { return n + (n % 2 == 0 ? 1 : 0); }
 
 // A block transforms AY consecutive other-axis indices (ia) x TX columns, so
-// short pencils still give every thread work.
+// short pencils still give every thread work.  Step A loads its L1 samples
+// straight from global memory into registers (samples >= n_in are zero and
+// never read); the only shared-memory round trip is the transpose between
+// the two steps.  Step B writes the first n_out outputs.
 template <class P, bool INV, int L1, int L2, class O>
 __global__ void __launch_bounds__(256) fft4_strided(const typename P::S* __restrict__ in, O* __restrict__ out,
                                                     StridedArgs4 a, const typename P::S* __restrict__ twL, int AY) {
   using S = typename P::S;
   using T = typename P::T;
-  constexpr int L = L1 * L2, TX = P::kTX;
+  constexpr int L = L1 * L2, TX = strided_tx<P, L>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* b0 = reinterpret_cast<S*>(smem_raw);  // [AY][L][TX]
-  S* b1 = b0 + AY * L * TX;
+  S* b = reinterpret_cast<S*>(smem_raw);  // [AY][L1][L2][TX]
   const int x0 = blockIdx.x * TX;
   const int ia0 = blockIdx.y * AY;
   const int nay = min(AY, a.A - ia0);
   const long long g = blockIdx.z;
-  const S* src = in + g * a.sG_in + (long long)ia0 * a.sA_in + x0;
-  if (nay == 1) {
-    for (int e = threadIdx.x; e < L * TX; e += blockDim.x) {
-      const int p = e / TX, c = e % TX;
-      S v = P::st(P::zero());
-      if (p < a.n_in && x0 + c < a.X) v = src[p * a.sP_in + c];
-      b0[e] = v;
-    }
-  } else {  // several short pencils per block: one flat loop keeps every thread loading
-    for (int e = threadIdx.x; e < nay * L * TX; e += blockDim.x) {
-      const int t = e / (L * TX), rem = e - t * (L * TX);
-      const int p = rem / TX, c = rem % TX;
-      S v = P::st(P::zero());
-      if (p < a.n_in && x0 + c < a.X) v = src[t * a.sA_in + p * a.sP_in + c];
-      b0[e] = v;
-    }
-  }
-  __syncthreads();
   for (int u = threadIdx.x; u < nay * TX * L2; u += blockDim.x) {
     const int t = u / (TX * L2), rem = u - t * (TX * L2);
     const int c = rem % TX, n2 = rem / TX;
-    const S* x = b0 + t * L * TX;
+    const bool col = x0 + c < a.X;
+    const S* src = in + g * a.sG_in + (long long)(ia0 + t) * a.sA_in + x0 + c;
     T v[L1];
-    static_for<0, L1>([&](auto n1) { v[n1] = P::ld(x[(L2 * decltype(n1)::value + n2) * TX + c]); });
+    static_for<0, L1>([&](auto n1) {
+      const int p = L2 * decltype(n1)::value + n2;
+      v[n1] = (col && p < a.n_in) ? P::ld(src[(long long)p * a.sP_in]) : P::zero();
+    });
     RegDFT<P, L1, INV>::run(v);
     if (n2 > 0)
       static_for<1, L1>([&](auto k1) { v[k1] = P::mul(v[k1], P::conj_if(P::ld(twL[n2 * decltype(k1)::value]), INV)); });
-    S* y = b1 + t * L * TX;
+    S* y = b + t * L * TX;
     static_for<0, L1>([&](auto k1) { y[(decltype(k1)::value * L2 + n2) * TX + c] = P::st(v[k1]); });
   }
   __syncthreads();
   for (int u = threadIdx.x; u < nay * TX * L1; u += blockDim.x) {
     const int t = u / (TX * L1), rem = u - t * (TX * L1);
     const int c = rem % TX, k1 = rem / TX;
-    const S* y = b1 + t * L * TX;
+    const S* y = b + t * L * TX;
     T w[L2];
     static_for<0, L2>([&](auto n2) { w[n2] = P::ld(y[(k1 * L2 + decltype(n2)::value) * TX + c]); });
     RegDFT<P, L2, INV>::run(w);
-    O* dst = out + g * a.sG_out + (long long)(ia0 + t) * a.sA_out + x0;
+    O* dst = out + g * a.sG_out + (long long)(ia0 + t) * a.sA_out + x0 + c;
     if (x0 + c < a.X)
       static_for<0, L2>([&](auto k2) {
         const int p = k1 + L1 * decltype(k2)::value;
-        if (p < a.n_out) dst[p * a.sP_out + c] = OutConv4<S, O>::f(P::st(w[k2]));
+        if (p < a.n_out) dst[(long long)p * a.sP_out] = OutConv4<S, O>::f(P::st(w[k2]));
       });
   }
 }
 
+// The fused x pass.  With k = k1 + L1 k2 and n = n2 + L2 n1,
+//   forward  X[k1 + L1 k2] = sum_n2 w_L2^(n2 k2) w_L^(n2 k1) sum_n1 x[L2 n1 + n2] w_L1^(n1 k1),
+//   inverse  y[n2 + L2 n1] = sum_k1 w_L1^(-k1 n1) w_L^(-k1 n2) sum_k2 X[k1 + L1 k2] w_L2^(-k2 n2).
+// The thread that finishes the forward transform for one k1 holds X[k1 + L1 k2]
+// for every k2, which is exactly the input of the inverse's first step, so it
+// multiplies by Ghat and starts the inverse in registers:
+//   step A (thread n2, from global):   DFT_L1, twiddle, into row k1 column n2 of the tile;
+//   step B (thread k1):                row k1: DFT_L2, x Ghat, inverse DFT_L2, twiddle,
+//                                      written back over the same row;
+//   step C (thread n2, to global):     column n2: inverse DFT_L1, samples < nx written.
+// One [L1][odd L2] tile per pencil, two shared-memory round trips.  The block
+// handles RY rows (ky) x TG grids at a time with at most one work item per
+// thread in each step (the launcher sizes RY * TG * max(L1, L2) <= blockDim)
+// and keeps the RY rows of Ghat in shared memory.
+// Resident 256-thread blocks per SM the register allocation must allow:
+// three for complex64, two for the 16-byte policies.
+template <class P> constexpr int x_min_blocks() { return sizeof(typename P::S) <= 8 ? 3 : 2; }
+
 template <class P, int L1, int L2>
-__global__ void __launch_bounds__(256) fft4_x(typename P::S* __restrict__ buf, XArgs4 a,
+__global__ void __launch_bounds__(256, x_min_blocks<P>()) fft4_x(typename P::S* __restrict__ buf, XArgs4 a,
                                               const typename P::S* __restrict__ ghat,
                                               const typename P::S* __restrict__ twL) {
   using S = typename P::S;
   using T = typename P::T;
   constexpr int L = L1 * L2;
+  constexpr int RA = odd_row(L2);
+  constexpr int PA = L1 * RA;  // per-pencil tile
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int RY = a.RY, TG = a.TG;
   S* gr = reinterpret_cast<S*>(smem_raw);  // [RY][L]
-  S* b0 = gr + RY * L;                      // [RY * TG][L]
-  S* b1 = b0 + RY * TG * L;
+  S* tile = gr + RY * L;                    // [RY * TG][L1][RA]
   const int ky0 = blockIdx.x * RY, kz = blockIdx.y;
   const int nry = min(RY, a.Ly - ky0);
   const int iz = min(kz, a.Lz - kz);
@@ -129,71 +144,55 @@ __global__ void __launch_bounds__(256) fft4_x(typename P::S* __restrict__ buf, X
     gr[e] = ghat[((long long)iz * a.hy + iy) * a.hx + min(p, L - p)];
   }
   const long long row0 = ((long long)kz * a.Ly + ky0) * a.nx;
+  const int u = threadIdx.x;
   for (int g0 = 0; g0 < a.G; g0 += TG) {
     const int ng = min(TG, a.G - g0);
     const int np = nry * ng;  // pencil pc = r * ng + gl
-    __syncthreads();
-    for (int e = threadIdx.x; e < np * L; e += blockDim.x) {
-      const int pc = e / L, p = e % L;
-      const int r = pc / ng, gl = pc - r * ng;
-      S v = P::st(P::zero());
-      if (p < a.nx) v = buf[(long long)(g0 + gl) * a.sG + row0 + (long long)r * a.nx + p];
-      b0[e] = v;
-    }
-    __syncthreads();
-    // forward, step A
-    for (int u = threadIdx.x; u < np * L2; u += blockDim.x) {
+    if (g0 > 0) __syncthreads();  // the previous group's step C has read its tiles
+    // step A: forward DFT_L1 of the zero-padded row, straight from global memory
+    if (u < np * L2) {
       const int n2 = u % L2, pc = u / L2;
-      const S* x = b0 + pc * L;
+      const int r = pc / ng, gl = pc - r * ng;
+      const S* src = buf + (long long)(g0 + gl) * a.sG + row0 + (long long)r * a.nx;
       T v[L1];
-      static_for<0, L1>([&](auto n1) { v[n1] = P::ld(x[L2 * decltype(n1)::value + n2]); });
+      static_for<0, L1>([&](auto n1) {
+        const int p = L2 * decltype(n1)::value + n2;
+        v[n1] = p < a.nx ? P::ld(src[p]) : P::zero();
+      });
       RegDFT<P, L1, false>::run(v);
       if (n2 > 0) static_for<1, L1>([&](auto k1) { v[k1] = P::mul(v[k1], P::ld(twL[n2 * decltype(k1)::value])); });
-      S* y = b1 + pc * L;
-      static_for<0, L1>([&](auto k1) { y[decltype(k1)::value * L2 + n2] = P::st(v[k1]); });
+      S* y = tile + pc * PA + n2;
+      static_for<0, L1>([&](auto k1) { y[decltype(k1)::value * RA] = P::st(v[k1]); });
     }
-    __syncthreads();
-    // forward, step B, times Ghat -> b0 in natural order
-    for (int u = threadIdx.x; u < np * L1; u += blockDim.x) {
+    __syncthreads();  // also orders Ghat's staging before the first step B
+    // step B: forward DFT_L2, product with Ghat, inverse DFT_L2, over one row
+    if (u < np * L1) {
       const int k1 = u % L1, pc = u / L1;
       const int r = pc / ng;
-      const S* y = b1 + pc * L;
+      S* y = tile + pc * PA + k1 * RA;
       T w[L2];
-      static_for<0, L2>([&](auto n2) { w[n2] = P::ld(y[k1 * L2 + decltype(n2)::value]); });
+      static_for<0, L2>([&](auto n2) { w[n2] = P::ld(y[decltype(n2)::value]); });
       RegDFT<P, L2, false>::run(w);
-      S* x = b0 + pc * L;
-      const S* gg = gr + r * L;
-      static_for<0, L2>([&](auto k2) {
-        const int p = k1 + L1 * decltype(k2)::value;
-        x[p] = P::st(P::mul(w[k2], P::ld(gg[p])));
-      });
-    }
-    __syncthreads();
-    // inverse, step A
-    for (int u = threadIdx.x; u < np * L2; u += blockDim.x) {
-      const int n2 = u % L2, pc = u / L2;
-      const S* x = b0 + pc * L;
-      T v[L1];
-      static_for<0, L1>([&](auto n1) { v[n1] = P::ld(x[L2 * decltype(n1)::value + n2]); });
-      RegDFT<P, L1, true>::run(v);
-      if (n2 > 0)
-        static_for<1, L1>([&](auto k1) { v[k1] = P::mul(v[k1], P::conj_if(P::ld(twL[n2 * decltype(k1)::value]), true)); });
-      S* y = b1 + pc * L;
-      static_for<0, L1>([&](auto k1) { y[decltype(k1)::value * L2 + n2] = P::st(v[k1]); });
-    }
-    __syncthreads();
-    // inverse, step B -> global (first nx samples)
-    for (int u = threadIdx.x; u < np * L1; u += blockDim.x) {
-      const int k1 = u % L1, pc = u / L1;
-      const int r = pc / ng, gl = pc - r * ng;
-      const S* y = b1 + pc * L;
-      T w[L2];
-      static_for<0, L2>([&](auto n2) { w[n2] = P::ld(y[k1 * L2 + decltype(n2)::value]); });
+      const S* gg = gr + r * L + k1;
+      static_for<0, L2>([&](auto k2) { w[k2] = P::mul(w[k2], P::ld(gg[L1 * decltype(k2)::value])); });
       RegDFT<P, L2, true>::run(w);
+      if (k1 > 0)
+        static_for<1, L2>([&](auto n2) { w[n2] = P::mul(w[n2], P::conj_if(P::ld(twL[k1 * decltype(n2)::value]), true)); });
+      static_for<0, L2>([&](auto n2) { y[decltype(n2)::value] = P::st(w[n2]); });
+    }
+    __syncthreads();
+    // step C: inverse DFT_L1 over one column, the first nx samples back to global memory
+    if (u < np * L2) {
+      const int n2 = u % L2, pc = u / L2;
+      const int r = pc / ng, gl = pc - r * ng;
+      const S* z = tile + pc * PA + n2;
+      T v[L1];
+      static_for<0, L1>([&](auto k1) { v[k1] = P::ld(z[decltype(k1)::value * RA]); });
+      RegDFT<P, L1, true>::run(v);
       S* dst = buf + (long long)(g0 + gl) * a.sG + row0 + (long long)r * a.nx;
-      static_for<0, L2>([&](auto k2) {
-        const int p = k1 + L1 * decltype(k2)::value;
-        if (p < a.nx) dst[p] = P::st(w[k2]);
+      static_for<0, L1>([&](auto n1) {
+        const int p = n2 + L2 * decltype(n1)::value;
+        if (p < a.nx) dst[p] = P::st(v[n1]);
       });
     }
   }

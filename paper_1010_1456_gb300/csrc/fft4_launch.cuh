@@ -14,61 +14,59 @@ using S = Pol::S;
 
 template <bool INV, int L1, int L2, class O>
 int launch_strided4(aim_ctx* c, const char* name, const S* in, O* out, const StridedArgs4& a, int G, const S* tw) {
-  constexpr int L = L1 * L2, TX = Pol::kTX;
-  // other-axis indices per block: about 256 work units per step, <= 100 KB of shared memory
+  constexpr int L = L1 * L2, TX = strided_tx<Pol, L>();
+  constexpr long long pencil_set = (long long)L * TX * sizeof(S);
+  // other-axis indices per block: about 256 work units in the heavier step,
+  // one buffer of at most 48 KB
   int AY = std::max(1, 256 / (TX * std::min(L1, L2)));
-  AY = std::min<int>(AY, (int)std::max<long long>(1, (100 * 1024) / (2ll * L * TX * (long long)sizeof(S))));
+  AY = std::min<int>(AY, (int)std::max<long long>(1, (48 * 1024) / pencil_set));
   AY = std::min(AY, a.A);
-  const size_t sm = 2ull * AY * L * TX * sizeof(S);
+  const int items = AY * TX * std::max(L1, L2);
+  const int threads = std::min(256, (items + 31) / 32 * 32);
+  const size_t sm = (size_t)AY * pencil_set;
   static const cudaError_t attr =
       cudaFuncSetAttribute(fft4_strided<Pol, INV, L1, L2, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   AIM_CUDA_TRY(attr);
   dim3 grid((a.X + TX - 1) / TX, (a.A + AY - 1) / AY, G);
-  AIM_LAUNCH(c, name, (fft4_strided<Pol, INV, L1, L2, O><<<grid, 256, sm, c->stream>>>(in, out, a, tw, AY)));
+  AIM_LAUNCH(c, name, (fft4_strided<Pol, INV, L1, L2, O><<<grid, threads, sm, c->stream>>>(in, out, a, tw, AY)));
   return launch_check(c, name);
 }
 
 template <int L1, int L2>
-int launch_x4(aim_ctx* c, const char* name, S* buf, XArgs4 a, const S* ghat, const S* tw) {
+int launch_x4(aim_ctx* c, const char* name, S* buf, XArgs4 a, const S* ghat, const S* tw, int threads) {
   constexpr int L = L1 * L2;
-  // pencils per block: about 256 work units per step, shared memory <= 100 KB
-  const long long budget = (100 * 1024) / sizeof(S);
-  const int want = std::max(1, 256 / std::min(L1, L2));
-  const int npmax = (int)std::max<long long>(1, std::min<long long>(want, (budget - L) / (2 * L)));
-  int TG = std::min(a.G, npmax);
-  int RY = std::max(1, npmax / TG);
-  RY = std::min(RY, a.Ly);
-  while (RY > 1 && (long long)(RY * L + 2 * RY * TG * L) > budget) --RY;
+  constexpr long long per_pencil = (long long)L1 * odd_row(L2);
+  constexpr int LM = std::max(L1, L2);
+  // pencils per block: one work item per thread in each step, shared memory
+  // within what one block may hold
+  const long long cap = (200 * 1024) / sizeof(S);
+  int np = std::max(1, threads / LM);
+  while (np > 1 && L + np * per_pencil > cap) --np;
+  const int TG = std::min(a.G, np);
+  const int RY = std::max(1, std::min(np / TG, a.Ly));
   a.RY = RY;
   a.TG = TG;
-  const size_t sm = (size_t)(RY * L + 2 * RY * TG * L) * sizeof(S);
-  if (sm > 227 * 1024) return kNotHandled;  // leave it to the Stockham kernel
+  const size_t sm = (size_t)(RY * L + RY * TG * per_pencil) * sizeof(S);
+  if (sm > 227 * 1024 || RY * TG * LM > 256) return kNotHandled;  // leave it to the Stockham kernel
+  const int nthreads = (RY * TG * LM + 31) / 32 * 32;
   static const cudaError_t attr =
       cudaFuncSetAttribute(fft4_x<Pol, L1, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   AIM_CUDA_TRY(attr);
   dim3 grid((a.Ly + RY - 1) / RY, a.Lz);
-  AIM_LAUNCH(c, name, (fft4_x<Pol, L1, L2><<<grid, 256, sm, c->stream>>>(buf, a, ghat, tw)));
+  AIM_LAUNCH(c, name, (fft4_x<Pol, L1, L2><<<grid, nthreads, sm, c->stream>>>(buf, a, ghat, tw)));
   return launch_check(c, name);
 }
 }  // namespace
 
 // 1: launched; 0: no four-step kernel for this length; < 0: -error code.
-int AIM_FFT4_NAME(strided)(aim_ctx* c, const char* name, bool inv, const S* in, S* out, double2* out64,
-                           const StridedArgs4& a, int G, int L, const S* tw) {
+int AIM_FFT4_NAME(strided)(aim_ctx* c, const char* name, bool inv, const S* in, S* out, const StridedArgs4& a, int G,
+                           int L, const S* tw) {
   int rc = AIM_OK;
   switch (L) {
-#define AIM_CASE(LL, A1, A2)                                                                         \
-  case LL:                                                                                           \
-    if (out64) {                                                                                     \
-      if constexpr (std::is_same<S, float4>::value)                                                  \
-        rc = launch_strided4<true, A1, A2, double2>(c, name, in, out64, a, G, tw);                   \
-      else                                                                                           \
-        return 0;                                                                                    \
-    } else if (inv) {                                                                                \
-      rc = launch_strided4<true, A1, A2, S>(c, name, in, out, a, G, tw);                             \
-    } else {                                                                                         \
-      rc = launch_strided4<false, A1, A2, S>(c, name, in, out, a, G, tw);                            \
-    }                                                                                                \
+#define AIM_CASE(LL, A1, A2)                                         \
+  case LL:                                                           \
+    rc = inv ? launch_strided4<true, A1, A2, S>(c, name, in, out, a, G, tw)  \
+             : launch_strided4<false, A1, A2, S>(c, name, in, out, a, G, tw); \
     return rc == AIM_OK ? 1 : -rc;
     AIM_FOURSTEP_LENGTHS(AIM_CASE)
 #undef AIM_CASE
@@ -76,11 +74,12 @@ int AIM_FFT4_NAME(strided)(aim_ctx* c, const char* name, bool inv, const S* in, 
   }
 }
 
-int AIM_FFT4_NAME(x)(aim_ctx* c, const char* name, S* buf, const XArgs4& a, int L, const S* ghat, const S* tw) {
+int AIM_FFT4_NAME(x)(aim_ctx* c, const char* name, S* buf, const XArgs4& a, int L, const S* ghat, const S* tw,
+                     int threads) {
   int rc = kNotHandled;
   switch (L) {
 #define AIM_CASE(LL, A1, A2) \
-  case LL: rc = launch_x4<A1, A2>(c, name, buf, a, ghat, tw); break;
+  case LL: rc = launch_x4<A1, A2>(c, name, buf, a, ghat, tw, threads); break;
     AIM_FOURSTEP_LENGTHS(AIM_CASE)
 #undef AIM_CASE
     default: break;

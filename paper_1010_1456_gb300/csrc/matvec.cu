@@ -13,9 +13,9 @@
 // 8-lane group: the lanes split the stencil nodes and the near entries and
 // reduce with warp shuffles.
 //
-// Modes: M32 (complex64, FP32 accumulation), M64 (complex128 throughout) and
-// MFF (complex128 vectors, FP64 weights and accumulation, grids stored as
-// float-float for the FFT passes).
+// Modes: M32 (complex64, FP32 accumulation) and M64 (complex128 throughout);
+// the float-float product (complex128 vectors, float-float grids, weights and
+// accumulation) has its own kernels below.
 #include <algorithm>
 
 #include "common.h"
@@ -45,18 +45,6 @@ struct M64 {
   __device__ static S put(double2 v) { return v; }
   __device__ static double2 get(const S& s) { return s; }
 };
-struct MFF {
-  using R = double;
-  using S = float4;
-  __device__ static S put(double2 v) {
-    const ff re = ff_from_double(v.x), im = ff_from_double(v.y);
-    return make_float4(re.hi, re.lo, im.hi, im.lo);
-  }
-  __device__ static double2 get(const S& s) {
-    return make_double2((double)s.x + (double)s.y, (double)s.z + (double)s.w);
-  }
-};
-
 // Four projection weights of one entry (x, y, z, charge).
 template <typename R> struct W4 {
   R x, y, z, w;
@@ -172,6 +160,339 @@ __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restr
   }
 }
 
+// out[c][r] = in[r][c] for an R x Cn row-major matrix (32 x 32 tiles through
+// shared memory, so both the reads and the writes are coalesced).
+template <class E>
+__global__ void __launch_bounds__(256) k_transpose(const E* __restrict__ in, E* __restrict__ out, int R, long long Cn) {
+  __shared__ E t[32][33];
+  const long long c0 = blockIdx.x * 32LL;
+  const int r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i;
+    const long long cc = c0 + threadIdx.x;
+    if (r < R && cc < Cn) t[i][threadIdx.x] = in[(long long)r * Cn + cc];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const long long cc = c0 + i;
+    const int r = r0 + threadIdx.x;
+    if (r < R && cc < Cn) out[cc * R + r] = t[threadIdx.x][i];
+  }
+}
+
+template <class E>
+static int transpose(aim_ctx* c, const char* name, const E* in, E* out, int R, long long Cn) {
+  dim3 grid((unsigned)((Cn + 31) / 32), (unsigned)((R + 31) / 32));
+  AIM_LAUNCH(c, name, (k_transpose<E><<<grid, dim3(32, 8), 0, c->stream>>>(in, out, R, Cn)));
+  return launch_check(c, name);
+}
+
+// RL consecutive complex values as one load (16 bytes for two complex64).
+template <class C, int RL> struct Run {
+  C v[RL];
+};
+template <class C, int RL> __device__ __forceinline__ Run<C, RL> load_run(const C* p) {
+  Run<C, RL> r;
+  if constexpr (RL == 2 && sizeof(C) == 8) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    r.v[0] = cmake<C>(q.x, q.y);
+    r.v[1] = cmake<C>(q.z, q.w);
+  } else {
+#pragma unroll
+    for (int i = 0; i < RL; ++i) r.v[i] = p[i];
+  }
+  return r;
+}
+
+// Interpolation + near correction for many right-hand sides: one warp per
+// basis function, lanes over right-hand sides (RL consecutive ones per lane),
+// with Phi and x in RHS-minor layout so every grid value and every near-zone
+// x value a warp reads is one contiguous run of right-hand sides; the weights
+// and near entries are warp-uniform.  The block's 8 rows of y are staged in
+// shared memory and written back in the [B][N] layout.
+template <class MI, int M, int RL>
+__global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R>* __restrict__ PhiT,
+                                                       const cplx<typename MI::R>* __restrict__ xT,
+                                                       cplx<typename MI::R>* __restrict__ y,
+                                                       const typename MI::R* __restrict__ lam,
+                                                       const int32_t* __restrict__ base,
+                                                       const int32_t* __restrict__ nptr,
+                                                       const int32_t* __restrict__ ncol,
+                                                       const cplx<typename MI::R>* __restrict__ nval, int N,
+                                                       long long Nc, int nx, int ny, int B, typename MI::R fvec,
+                                                       typename MI::R frho) {
+  using R = typename MI::R;
+  using C = cplx<R>;
+  constexpr int P = M + 1;
+  constexpr int S = P * P * P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* ys = reinterpret_cast<C*>(smem_raw);  // [8][B]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * 8, m = m0 + warp;
+  if (m < N) {
+    const int b0 = base[m];
+    const R* lm = lam + (long long)m * 4 * S;
+    const int r0 = nptr[m], r1 = nptr[m + 1];
+    const long long cs = Nc * B;  // component stride of PhiT
+    for (int bc = 0; bc < B; bc += 32 * RL) {
+      const int b = bc + RL * lane;  // B is a multiple of RL
+      if (b < B) {
+        C av[RL], ar[RL], an[RL];
+#pragma unroll
+        for (int q = 0; q < RL; ++q) av[q] = ar[q] = an[q] = cmake<C>(0, 0);
+#pragma unroll 3
+        for (int s = 0; s < S; ++s) {
+          const int i = s % P, j = (s / P) % P, kk = s / (P * P);
+          const C* ph = PhiT + (b0 + ((long long)kk * ny + j) * nx + i) * B + b;
+          const Run<C, RL> px = load_run<C, RL>(ph), py = load_run<C, RL>(ph + cs), pz = load_run<C, RL>(ph + 2 * cs),
+                           pr = load_run<C, RL>(ph + 3 * cs);
+          const R wx = lm[s], wy = lm[S + s], wz = lm[2 * S + s], wr = lm[3 * S + s];
+#pragma unroll
+          for (int q = 0; q < RL; ++q) {
+            av[q].x += wx * px.v[q].x + wy * py.v[q].x + wz * pz.v[q].x;
+            av[q].y += wx * px.v[q].y + wy * py.v[q].y + wz * pz.v[q].y;
+            ar[q].x += wr * pr.v[q].x;
+            ar[q].y += wr * pr.v[q].y;
+          }
+        }
+#pragma unroll 4
+        for (int e = r0; e < r1; ++e) {
+          const C v = nval[e];
+          const Run<C, RL> xv = load_run<C, RL>(xT + (long long)ncol[e] * B + b);
+#pragma unroll
+          for (int q = 0; q < RL; ++q) {
+            an[q].x += v.x * xv.v[q].x - v.y * xv.v[q].y;
+            an[q].y += v.x * xv.v[q].y + v.y * xv.v[q].x;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+          C t;
+          t.x = fvec * av[q].x - frho * ar[q].x;
+          t.y = fvec * av[q].y - frho * ar[q].y;
+          C out;
+          out.x = an[q].x - t.y;
+          out.y = an[q].y + t.x;
+          ys[warp * B + b + q] = out;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int rows = min(8, N - m0);
+  for (int t = threadIdx.x; t < 8 * B; t += blockDim.x) {
+    const int i = t & 7, b = t >> 3;
+    if (i < rows) y[(long long)b * N + m0 + i] = ys[i * B + b];
+  }
+}
+
+// Right-hand sides from which the interpolation runs with lanes over them.
+constexpr int kRhsLanesMin = 16;
+
+// ---- float-float projection and interpolation (AIM_C128) ----
+// The FP64-accurate product keeps its grids in float-float form for the FFT
+// passes; these kernels do the projection, interpolation and near SpMV in the
+// same arithmetic on the FP32 pipes (GB300 retires about 64 FP32 FMAs for
+// every FP64 FMA), with weights and near entries rounded once to float-float
+// at the first product.  Only the input and the output vectors are FP64.
+
+__device__ __forceinline__ ff ffv(float hi, float lo) { return ff{hi, lo}; }
+
+__global__ void k_real_to_ff(const double* __restrict__ in, float2* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const ff v = ff_from_double(in[i]);
+    out[i] = make_float2(v.hi, v.lo);
+  }
+}
+__global__ void k_cplx_to_ff(const double2* __restrict__ in, float4* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const ff re = ff_from_double(in[i].x), im = ff_from_double(in[i].y);
+    out[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+}
+// [nent][4] FP64 weights -> [nent][2] float4: high parts, then low parts.
+__global__ void k_w4_to_ff(const double* __restrict__ in, float4* __restrict__ out, long long nent) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nent;
+       e += (long long)gridDim.x * blockDim.x) {
+    const ff a = ff_from_double(in[4 * e]), b = ff_from_double(in[4 * e + 1]), c = ff_from_double(in[4 * e + 2]),
+             d = ff_from_double(in[4 * e + 3]);
+    out[2 * e] = make_float4(a.hi, b.hi, c.hi, d.hi);
+    out[2 * e + 1] = make_float4(a.lo, b.lo, c.lo, d.lo);
+  }
+}
+
+// Projection: 4 lanes per grid node, as proj_gather.
+__global__ void __launch_bounds__(256) proj_gather_ff(const float4* __restrict__ x, float4* __restrict__ Q,
+                                                      const int32_t* __restrict__ ptr, const int32_t* __restrict__ mm,
+                                                      const float4* __restrict__ w, int N, long long Nc, int nrhs) {
+  const int lane = threadIdx.x & 3;
+  const long long stride = ((long long)gridDim.x * blockDim.x) >> 2;
+  for (long long u0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 2;; u0 += stride) {
+    const bool live = u0 < Nc;
+    if (!__any_sync(0xffffffffu, live)) break;
+    const long long u = live ? u0 : Nc - 1;
+    const int e0 = ptr[u], e1 = ptr[u + 1];
+    for (int b = 0; b < nrhs; ++b) {
+      ff a[4][2];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a[c][0] = a[c][1] = ffv(0.f, 0.f);
+      const float4* xb = x + (long long)b * N;
+      for (int e = e0 + lane; e < e1; e += 4) {
+        const float4 wh = w[2 * e], wl = w[2 * e + 1];
+        const float4 xv = xb[mm[e]];
+        const ff xr = ffv(xv.x, xv.y), xi = ffv(xv.z, xv.w);
+        const ff wc[4] = {ffv(wh.x, wl.x), ffv(wh.y, wl.y), ffv(wh.z, wl.z), ffv(wh.w, wl.w)};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          a[c][0] = ff_mad(wc[c], xr, a[c][0]);
+          a[c][1] = ff_mad(wc[c], xi, a[c][1]);
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < 4; o <<= 1)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const ff t = ffv(__shfl_xor_sync(0xffffffffu, a[c][q].hi, o, 4), __shfl_xor_sync(0xffffffffu, a[c][q].lo, o, 4));
+            a[c][q] = ff_add(a[c][q], t);
+          }
+      if (live) {
+        // lane c writes component c
+        ff re = a[0][0], im = a[0][1];
+#pragma unroll
+        for (int c = 1; c < 4; ++c)
+          if (lane == c) {
+            re = a[c][0];
+            im = a[c][1];
+          }
+        Q[(long long)b * 4 * Nc + (long long)lane * Nc + u] = make_float4(re.hi, re.lo, im.hi, im.lo);
+      }
+    }
+  }
+}
+
+// Interpolation + near correction: 8 lanes per basis function, as interp_near.
+template <int M>
+__global__ void __launch_bounds__(256) interp_near_ff(const float4* __restrict__ Phi, const float4* __restrict__ x,
+                                                      double2* __restrict__ y, const float2* __restrict__ lam,
+                                                      const int32_t* __restrict__ base, const int32_t* __restrict__ nptr,
+                                                      const int32_t* __restrict__ ncol,
+                                                      const float4* __restrict__ nval, int N, long long Nc, int nx,
+                                                      int ny, int nrhs, float2 fvec, float2 frho) {
+  constexpr int P = M + 1;
+  constexpr int S = P * P * P;
+  const int lane = threadIdx.x & 7;
+  const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const bool live = m < N;
+  const int mm = live ? m : N - 1;
+  const int b0 = base[mm];
+  const float2* lm = lam + (long long)mm * 4 * S;
+  const int r0 = nptr[mm], r1 = nptr[mm + 1];
+  const ff kv = ffv(fvec.x, fvec.y), kr = ffv(frho.x, frho.y);
+  for (int b = 0; b < nrhs; ++b) {
+    const float4* Pb = Phi + (long long)b * 4 * Nc;
+    ff avr = ffv(0.f, 0.f), avi = avr, arr = avr, ari = avr, anr = avr, ani = avr;
+    for (int s = lane; s < S; s += 8) {
+      const int i = s % P, j = (s / P) % P, kk = s / (P * P);
+      const long long node = b0 + ((long long)kk * ny + j) * nx + i;
+      const float4 px = Pb[node], py = Pb[Nc + node], pz = Pb[2 * Nc + node], pr = Pb[3 * Nc + node];
+      const float2 wx = lm[s], wy = lm[S + s], wz = lm[2 * S + s], wr = lm[3 * S + s];
+      avr = ff_mad(ffv(wx.x, wx.y), ffv(px.x, px.y), avr);
+      avi = ff_mad(ffv(wx.x, wx.y), ffv(px.z, px.w), avi);
+      avr = ff_mad(ffv(wy.x, wy.y), ffv(py.x, py.y), avr);
+      avi = ff_mad(ffv(wy.x, wy.y), ffv(py.z, py.w), avi);
+      avr = ff_mad(ffv(wz.x, wz.y), ffv(pz.x, pz.y), avr);
+      avi = ff_mad(ffv(wz.x, wz.y), ffv(pz.z, pz.w), avi);
+      arr = ff_mad(ffv(wr.x, wr.y), ffv(pr.x, pr.y), arr);
+      ari = ff_mad(ffv(wr.x, wr.y), ffv(pr.z, pr.w), ari);
+    }
+    const float4* xb = x + (long long)b * N;
+    for (int e = r0 + lane; e < r1; e += 8) {
+      const float4 v = nval[e], xv = xb[ncol[e]];
+      const ff vr = ffv(v.x, v.y), vi = ffv(v.z, v.w), xr = ffv(xv.x, xv.y), xi = ffv(xv.z, xv.w);
+      anr = ff_mad(vr, xr, anr);
+      anr = ff_mad(ff_neg(vi), xi, anr);
+      ani = ff_mad(vr, xi, ani);
+      ani = ff_mad(vi, xr, ani);
+    }
+    // grid part j (fvec av - frho ar): out = an + j t
+    const ff tr = ff_sub(ff_mul(kv, avr), ff_mul(kr, arr));
+    const ff ti = ff_sub(ff_mul(kv, avi), ff_mul(kr, ari));
+    ff outr = ff_sub(anr, ti), outi = ff_add(ani, tr);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      outr = ff_add(outr, ffv(__shfl_xor_sync(0xffffffffu, outr.hi, o, 8), __shfl_xor_sync(0xffffffffu, outr.lo, o, 8)));
+      outi = ff_add(outi, ffv(__shfl_xor_sync(0xffffffffu, outi.hi, o, 8), __shfl_xor_sync(0xffffffffu, outi.lo, o, 8)));
+    }
+    if (live && lane == 0) y[(long long)b * N + m] = make_double2(ff_to_double(outr), ff_to_double(outi));
+  }
+}
+
+static int ensure_ff_arrays(aim_ctx* c) {
+  FFData& p = c->pff;
+  if (p.pnode_w) return AIM_OK;
+  const long long nent = c->nent, nl = (long long)c->N * 4 * c->S;
+  AIM_CUDA_TRY(cudaMalloc(&p.pnode_w, sizeof(float4) * 2 * nent));
+  AIM_CUDA_TRY(cudaMalloc(&p.lam, sizeof(float2) * nl));
+  AIM_CUDA_TRY(cudaMalloc(&p.near_val, sizeof(float4) * std::max<long long>(1, c->nnz)));
+  AIM_CUDA_TRY(cudaMalloc(&p.xff, sizeof(float4) * c->max_rhs * c->N));
+  const int blocks = 152 * 8;
+  AIM_LAUNCH(c, "weights_to_ff", (k_w4_to_ff<<<blocks, 256, 0, c->stream>>>(c->p64.pnode_w, p.pnode_w, nent)));
+  AIM_TRY(launch_check(c, "weights_to_ff"));
+  AIM_LAUNCH(c, "weights_to_ff", (k_real_to_ff<<<blocks, 256, 0, c->stream>>>(c->p64.lam, p.lam, nl)));
+  AIM_TRY(launch_check(c, "weights_to_ff"));
+  if (c->nnz > 0) {
+    AIM_LAUNCH(c, "weights_to_ff", (k_cplx_to_ff<<<blocks, 256, 0, c->stream>>>(c->p64.near_val, p.near_val, c->nnz)));
+    AIM_TRY(launch_check(c, "weights_to_ff"));
+  }
+  return AIM_OK;
+}
+
+static int run_product_ff(aim_ctx* c, const double2* x, double2* y, int nrhs) {
+  AIM_TRY(ensure_ff_arrays(c));
+  FFData& p = c->pff;
+  const long long Nc = (long long)c->n[0] * c->n[1] * c->n[2];
+  const long long nx_ = (long long)nrhs * c->N;
+  {
+    const int blocks = (int)std::min<long long>((nx_ + 255) / 256, 152LL * 8);
+    AIM_LAUNCH(c, "x_to_ff", (k_cplx_to_ff<<<blocks, 256, 0, c->stream>>>(x, p.xff, nx_)));
+    AIM_TRY(launch_check(c, "x_to_ff"));
+  }
+  {
+    const int blocks = (int)std::min<long long>((4 * Nc + 255) / 256, 152LL * 16);
+    AIM_LAUNCH(c, "proj_gather",
+               (proj_gather_ff<<<blocks, 256, 0, c->stream>>>(p.xff, p.grid0, c->pnode_ptr, c->pnode_m, p.pnode_w, c->N,
+                                                             Nc, nrhs)));
+    AIM_TRY(launch_check(c, "proj_gather"));
+  }
+  AIM_TRY(fft_convolve_ff(c, 4 * nrhs));
+  {
+    const long long threads = (long long)c->N * 8;
+    const int blocks = (int)((threads + 255) / 256);
+    const double fv = c->k * kEta0, fr = kEta0 / c->k;
+    const float fvh = (float)fv, frh = (float)fr;
+    const float2 fvec = make_float2(fvh, (float)(fv - (double)fvh)), frho = make_float2(frh, (float)(fr - (double)frh));
+#define AIM_INTERP_FF(MM)                                                                                          \
+  AIM_LAUNCH(c, "interp_near",                                                                                     \
+             (interp_near_ff<MM><<<blocks, 256, 0, c->stream>>>(p.grid0, p.xff, y, p.lam, c->base, c->near_ptr,    \
+                                                                c->near_col, p.near_val, c->N, Nc, c->n[0], c->n[1], \
+                                                                nrhs, fvec, frho)))
+    switch (c->M) {
+      case 1: AIM_INTERP_FF(1); break;
+      case 2: AIM_INTERP_FF(2); break;
+      default: AIM_INTERP_FF(3); break;
+    }
+#undef AIM_INTERP_FF
+    AIM_TRY(launch_check(c, "interp_near"));
+  }
+  return AIM_OK;
+}
+
+template <typename R> PrecData<R>& prec_data(aim_ctx* c);
+template <> PrecData<float>& prec_data<float>(aim_ctx* c) { return c->p32; }
+template <> PrecData<double>& prec_data<double>(aim_ctx* c) { return c->p64; }
+
 // MD: storage of the projected grid; MI: storage of Phi read by the interpolation.
 template <class MD, class MI>
 static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename MD::R>* y, int nrhs,
@@ -186,6 +507,35 @@ static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename 
     AIM_TRY(launch_check(c, "proj_gather"));
   }
   AIM_TRY(convolve(c, 4 * nrhs));
+  if (nrhs >= kRhsLanesMin) {
+    PrecData<R>& pd = prec_data<R>(c);
+    if (!pd.phiT) {
+      AIM_CUDA_TRY(cudaMalloc(&pd.phiT, sizeof(cplx<R>) * c->max_rhs * 4 * Nc));
+      AIM_CUDA_TRY(cudaMalloc(&pd.xT, sizeof(cplx<R>) * c->max_rhs * c->N));
+    }
+    AIM_TRY(transpose(c, "transpose_phi", reinterpret_cast<const cplx<R>*>(phi), pd.phiT, nrhs, 4 * Nc));
+    AIM_TRY(transpose(c, "transpose_x", x, pd.xT, nrhs, (long long)c->N));
+    const int blocks = (c->N + 7) / 8;
+    const size_t sm = sizeof(cplx<R>) * 8 * nrhs;
+    const R fvec = (R)(c->k * kEta0), frho = (R)(kEta0 / c->k);
+    // two right-hand sides per lane once a warp has 64 to cover
+    const bool two = nrhs >= 64 && nrhs % 2 == 0;
+#define AIM_INTERP_RHS(MM, RL)                                                                                   \
+  AIM_LAUNCH(c, "interp_near",                                                                                   \
+             (interp_near_rhs<MI, MM, RL><<<blocks, 256, sm, c->stream>>>(pd.phiT, pd.xT, y, lam, c->base,        \
+                                                                          c->near_ptr, c->near_col, nval, c->N, Nc, \
+                                                                          c->n[0], c->n[1], nrhs, fvec, frho)))
+    switch (c->M * 2 + (two ? 1 : 0)) {
+      case 2: AIM_INTERP_RHS(1, 1); break;
+      case 3: AIM_INTERP_RHS(1, 2); break;
+      case 4: AIM_INTERP_RHS(2, 1); break;
+      case 5: AIM_INTERP_RHS(2, 2); break;
+      case 6: AIM_INTERP_RHS(3, 1); break;
+      default: AIM_INTERP_RHS(3, 2); break;
+    }
+#undef AIM_INTERP_RHS
+    return launch_check(c, "interp_near");
+  }
   {
     const long long threads = (long long)c->N * 8;
     const int blocks = (int)((threads + 255) / 256);
@@ -230,7 +580,6 @@ int ensure_grids(aim_ctx* c, int precision) {
       AIM_CUDA_TRY(cudaMalloc(&p.grid0, sizeof(float4) * e0));
       AIM_CUDA_TRY(cudaMalloc(&p.grid1, sizeof(float4) * e1));
       AIM_CUDA_TRY(cudaMalloc(&p.grid2, sizeof(float4) * e2));
-      AIM_CUDA_TRY(cudaMalloc(&p.phi64, sizeof(double2) * e0));
     }
   }
   return AIM_OK;
@@ -244,8 +593,7 @@ int matvec(aim_ctx* c, const void* x, void* y, int nrhs, int precision) {
   if (precision == AIM_C128_F64)
     return run_product<M64, M64>(c, (const double2*)x, (double2*)y, nrhs, c->p64.grid0, c->p64.grid0,
                                  c->p64.pnode_w, c->p64.lam, c->p64.near_val, fft_convolve_c128);
-  return run_product<MFF, M64>(c, (const double2*)x, (double2*)y, nrhs, c->pff.grid0, c->pff.phi64, c->p64.pnode_w,
-                               c->p64.lam, c->p64.near_val, fft_convolve_ff);
+  return run_product_ff(c, (const double2*)x, (double2*)y, nrhs);
 }
 
 __global__ void k_c128_to_c64(const double2* __restrict__ in, float2* __restrict__ out, long long n) {

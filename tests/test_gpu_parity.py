@@ -156,6 +156,59 @@ def test_many_rhs_products(nrhs):
         assert rel(yb[0], ref[b]) <= 1e-12
 
 
+FFT_CHOICES = [g.AIM_FFT_STOCKHAM, g.AIM_FFT_FOURSTEP, g.AIM_FFT_FOURSTEP_SMALL]
+
+
+@pytest.mark.parametrize("kernel", FFT_CHOICES)
+def test_every_fft_kernel_choice(plate_a, sphere_small, kernel):
+    """Each FFT kernel, forced on all five passes, gives the oracle's product in every precision."""
+    for (ctx, op), nrhs, seed in ((plate_a, 3, 31), (sphere_small, 2, 32)):
+        x = random_complex((nrhs, ctx.N), seed)
+        ref = op.matvec(x)
+        for prec in WIDE + [g.AIM_C64]:
+            assert g.aim_fft_config(ctx, prec, [kernel] * 5) == [kernel] * 5
+            xt = torch.from_numpy(x if prec != g.AIM_C64 else x.astype(np.complex64)).cuda()
+            y = g.aim_matvec(ctx, xt, precision=prec).cpu().numpy()
+            if prec == g.AIM_C64:
+                assert rel(y, op.matvec(x.astype(np.complex64).astype(np.complex128))) <= 1e-5
+            else:
+                assert rel(y, ref) <= 1e-12
+            g.aim_fft_config(ctx, prec, [g.AIM_FFT_AUTO] * 5)
+
+
+def test_autotune_keeps_parity_and_profiler_state(sphere_small):
+    ctx, op = sphere_small
+    x = random_complex((2, ctx.N), 33)
+    xt = torch.from_numpy(x).cuda()
+    g.aim_profile(ctx, 2)
+    g.aim_profile(ctx, 1)
+    g.aim_matvec(ctx, xt, precision=g.AIM_C128)
+    before = g.aim_profile_read(ctx)
+    kernels, ms = g.aim_autotune(ctx, g.AIM_C128, nrhs=2, reps=2)
+    after = g.aim_profile_read(ctx)
+    g.aim_profile(ctx, 0)
+    g.aim_profile(ctx, 2)
+    assert {k: v[0] for k, v in after.items()} == {k: v[0] for k, v in before.items()}
+    assert all(k in FFT_CHOICES for k in kernels)
+    assert g.aim_fft_config(ctx, g.AIM_C128) == kernels
+    for p, k in enumerate(kernels):
+        assert ms[p, k] > 0 and ms[p, k] == ms[p, ms[p] > 0].min()
+    assert (ms[:, 0] == -1).all() and (ms[[0, 1, 3, 4], 3] == -1).all()
+    y = g.aim_matvec(ctx, xt, precision=g.AIM_C128).cpu().numpy()
+    assert rel(y, op.matvec(x)) <= 1e-12
+    g.aim_fft_config(ctx, g.AIM_C128, [g.AIM_FFT_AUTO] * 5)
+
+
+def test_fft_config_rejects_bad_choices(plate_a):
+    ctx, _ = plate_a
+    with pytest.raises(g.AIMError):
+        g.aim_fft_config(ctx, g.AIM_C64, [4, 0, 0, 0, 0])
+    with pytest.raises(g.AIMError):
+        g.aim_autotune(ctx, g.AIM_C64, nrhs=ctx.max_rhs + 1)
+    assert g.aim_fft_config(ctx, g.AIM_C128) == [1, 1, 2, 1, 1]  # the built-in rule
+    assert g.aim_fft_config(ctx, g.AIM_C64) == [2, 2, 2, 2, 2]
+
+
 def test_stockham_fallback_length():
     """A padded length outside the four-step menu (18) runs the Stockham kernels."""
     v, t = plate_mesh(0.7, 6)
@@ -238,12 +291,13 @@ def test_full_size_sphere_sampled_rows():
 
 @pytest.mark.slow
 def test_full_size_plate_32_lambda_multi_rhs_sampled_rows():
-    """32 lambda plate (N = 248,256, grid 321x321x3 padded 648x648x5), 4 RHS, sampled rows."""
+    """32 lambda plate (N = 248,256, grid 321x321x3 padded 648x648x5), 16 RHS (the
+    lanes-over-RHS interpolation), sampled rows."""
     v, t = plate_mesh(32.0, 288)
     rows = np.sort(np.random.default_rng(1).choice(248256, 200, replace=False))
-    ctx, op = make(v, t, max_rhs=4, near_rows=rows)
+    ctx, op = make(v, t, max_rhs=16, near_rows=rows)
     assert ctx.N == 248256
-    x = random_complex((4, ctx.N), 22)
+    x = random_complex((16, ctx.N), 22)
     ref = op.matvec(x)[:, rows]
     y = g.aim_matvec(ctx, torch.from_numpy(x).cuda(), precision=g.AIM_C128).cpu().numpy()[:, rows]
     assert rel(y, ref) <= 1e-12
