@@ -226,8 +226,7 @@ int aim_probe_fma_peak(int which, double* tflops);
  * five passes of the convolution (z forward, y forward, the fused x pass --
  * forward transform, spectral product, inverse -- y inverse, z inverse, in
  * that order) runs one of:
- *   AIM_FFT_AUTO            the built-in rule (default): four-step, except
- *                           the float-float strided passes, which use Stockham;
+ *   AIM_FFT_AUTO            the built-in rule (default): four-step;
  *   AIM_FFT_STOCKHAM        mixed-radix Stockham kernel (any 2,3,5-smooth length);
  *   AIM_FFT_FOURSTEP        four-step register kernel (compiled lengths; any
  *                           other length falls back to the Stockham kernel);

@@ -117,7 +117,9 @@ def aim_destroy(ctx):
 
 
 def aim_set_stream(ctx, stream):
-    check(load().aim_set_stream(ctx.handle, C.c_void_p(int(stream))), "aim_set_stream")
+    """stream: a torch.cuda.Stream or a raw cudaStream_t handle (int)."""
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    check(load().aim_set_stream(ctx.handle, C.c_void_p(h)), "aim_set_stream")
 
 
 def aim_set_precision(ctx, precision):

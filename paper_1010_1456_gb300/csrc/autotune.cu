@@ -114,6 +114,7 @@ extern "C" int aim_fft_config(aim_ctx* ctx, int precision, const int32_t* set, i
         return AIM_EINVAL;
       }
     for (int i = 0; i < AIM_FFT_PASSES; ++i) ctx->fft_kernel[pol][i] = set[i];
+    drop_step_graph(ctx);
   }
   if (get)
     for (int i = 0; i < AIM_FFT_PASSES; ++i) get[i] = fft_kernel_for(ctx, pol, i);
@@ -140,6 +141,7 @@ extern "C" int aim_autotune(aim_ctx* ctx, int precision, int nrhs, int reps, int
   const int pol = fft_policy_of(precision);
   for (int i = 0; i < AIM_FFT_PASSES; ++i) saved[i] = ctx->fft_kernel[pol][i];
   const int rc = autotune(ctx, precision, nrhs, reps, kernel_out, ms_out);
+  drop_step_graph(ctx);
   if (rc != AIM_OK)
     for (int i = 0; i < AIM_FFT_PASSES; ++i) ctx->fft_kernel[pol][i] = saved[i];
   profile_collect(ctx);

@@ -128,17 +128,26 @@ struct KrylovWork {
   double2* r = nullptr;      // [B][N]
   double2* H = nullptr;      // [B][m+1][m]
   double2* hcol = nullptr;   // [B][m+1] current column (dot results)
-  double2* partial = nullptr;// [B][nblk][m+1] partial dots
+  double2* partial = nullptr;// [B][nblk][m+1+kDotGroup] partial dots
   double2* cs = nullptr;     // [B][m]
   double2* sn = nullptr;     // [B][m]
   double2* g = nullptr;      // [B][m+1]
   double2* y = nullptr;      // [B][m]
-  double* nrm = nullptr;     // [B]
+  double* nrm = nullptr;     // [B] norms; then est [B], w0 [B] (|w|^2 before orthogonalising), partials
   double* bnorm = nullptr;   // [B]
   double* h_est = nullptr;   // pinned host [B] residual estimates
   int* active = nullptr;     // [B]
+  int* reorth = nullptr;     // [B] second Gram-Schmidt pass needed for the current column
+  int* jdev = nullptr;       // current Arnoldi column (read by the step's kernels)
   int m = 0;
-  int nblk = 0;
+  int nblk = 0;              // blocks per right-hand side of the norm kernel
+  int nblk_dot = 0;          // blocks per right-hand side and vector group of the dot kernel
+  // CUDA graph of one Arnoldi step (per precision and batch size), captured
+  // on a private stream (the legacy default stream cannot be captured)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  int step_prec = 0, step_nrhs = 0;
+  int64_t step_launches = 0;
 };
 
 }  // namespace aim
@@ -242,6 +251,11 @@ int build_ghat(aim_ctx* c);
 // krylov.cu
 int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_solve_info* info);
 int alloc_krylov(aim_ctx* c);
+// Allocates everything a product of this precision allocates lazily, so a
+// product can be captured into a CUDA graph.
+int prepare_product(aim_ctx* c, int precision);
+// Forgets the solver's captured Arnoldi step (after the kernel choice changed).
+void drop_step_graph(aim_ctx* c);
 void free_krylov(aim_ctx* c);
 // rcs.cu
 int rhs_planewave(aim_ctx* c, int nrhs, const double* khat, const double* pol, double2* V);

@@ -319,10 +319,7 @@ int fft_policy_of(int precision) { return precision == AIM_C64 ? 0 : precision =
 
 int fft_kernel_for(const aim_ctx* c, int pol, int pass) {
   const int k = c->fft_kernel[pol][pass];
-  if (k != AIM_FFT_AUTO) return k;
-  // The float-float strided four-step kernels need 110-160 registers per
-  // thread; the Stockham kernels (54) keep more warps resident.
-  return (pol == 2 && pass != 2) ? AIM_FFT_STOCKHAM : AIM_FFT_FOURSTEP;
+  return k != AIM_FFT_AUTO ? k : AIM_FFT_FOURSTEP;
 }
 
 template <class P> constexpr int policy_index() {

@@ -5,7 +5,9 @@
 // its own Arnoldi basis, Hessenberg matrix and Givens rotations.  Dot
 // products, norms and rotations are FP64 (two-level block reductions, so the
 // results do not depend on launch timing).  Orthogonalisation is classical
-// Gram-Schmidt with one re-orthogonalisation (CGS2).  The Arnoldi product is
+// Gram-Schmidt with a second pass where the Daniel-Gragg-Kaufman-Stewart test
+// asks for it.  One Arnoldi step is captured once as a CUDA graph and replayed
+// (its kernels take the column index from device memory).  The Arnoldi product is
 // complex64 or complex128 (aim_opts.precision); every restart recomputes the
 // true residual V - Z~ X with the complex128 product, so the complex64 mode
 // is FP64 iterative refinement wrapped around a complex64 inner solve.
@@ -49,59 +51,96 @@ __device__ __forceinline__ void block_reduce_store(double2* v, double2* out, int
   __syncthreads();
 }
 
-// partial[b][blk][i] = sum over this block's chunk of conj(V[b][i]) . w[b], i in [0, nvec)
-__global__ void k_dots(const double2* __restrict__ V, const double2* __restrict__ w, double2* __restrict__ partial,
-                       int N, int nvec, int ldv_vec, int nblk, int ldp) {
-  const int b = blockIdx.y, blk = blockIdx.x;
+// Every kernel of the Arnoldi step reads the column index j from device
+// memory (jdev), so one captured CUDA graph serves every step of a cycle.
+
+// Pass `pass` of classical Gram-Schmidt for column j, partial dot products:
+// partial[b][blk][i] = sum over block blk's chunk of conj(V[b][i]) . w[b],
+// i <= j; on the first pass the slot i = j + 1 receives |w|^2 (the norm before
+// orthogonalising, for the re-orthogonalisation test).  Grid: (vector groups
+// of kDotGroup, nblk, B); blocks past the column's vectors, and the second
+// pass of right-hand sides that need no re-orthogonalisation, return at once.
+__global__ void __launch_bounds__(256) k_dots(const double2* __restrict__ V, const double2* __restrict__ w,
+                                              double2* __restrict__ partial, const int* __restrict__ jdev,
+                                              const int* __restrict__ reorth, int N, int ldv_vec, int nblk, int ldp,
+                                              int pass) {
+  const int b = blockIdx.z, blk = blockIdx.y, i0 = blockIdx.x * kDotGroup;
+  const int nvec = *jdev + 1;
+  const int nslot = pass == 0 ? nvec + 1 : nvec;
+  if (i0 >= nslot || (pass == 1 && !reorth[b])) return;
   const double2* Vb = V + (long long)b * ldv_vec * N;
   const double2* wb = w + (long long)b * N;
   const int chunk = (N + nblk - 1) / nblk;
   const int n0 = blk * chunk, n1 = min(N, n0 + chunk);
-  double2* pout = partial + ((long long)b * nblk + blk) * ldp;
-  for (int i0 = 0; i0 < nvec; i0 += kDotGroup) {
-    double2 acc[kDotGroup];
+  double2 acc[kDotGroup];
 #pragma unroll
-    for (int i = 0; i < kDotGroup; ++i) acc[i] = make_double2(0, 0);
-    const int ni = min(kDotGroup, nvec - i0);
-    for (int n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
-      const double2 wv = wb[n];
+  for (int i = 0; i < kDotGroup; ++i) acc[i] = make_double2(0, 0);
+  const int ni = min(kDotGroup, nslot - i0);
+  for (int n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+    const double2 wv = wb[n];
 #pragma unroll
-      for (int i = 0; i < kDotGroup; ++i)
-        if (i < ni) acc[i] = cfma_conj(Vb[(long long)(i0 + i) * N + n], wv, acc[i]);
-    }
-    block_reduce_store<kDotGroup>(acc, pout + i0, 1);
+    for (int i = 0; i < kDotGroup; ++i)
+      if (i < ni) acc[i] = cfma_conj(i0 + i < nvec ? Vb[(long long)(i0 + i) * N + n] : wv, wv, acc[i]);
+  }
+  block_reduce_store<kDotGroup>(acc, partial + ((long long)b * nblk + blk) * ldp + i0, 1);
+}
+
+// hcol[b][i] = sum over blocks of the partial dots (one warp per (b, i));
+// H[b][i][j] = hcol (first pass) or += hcol (second pass).  First pass,
+// slot i = j + 1: w0[b] = |w|^2.
+__global__ void __launch_bounds__(256) k_dots_reduce(const double2* __restrict__ partial, double2* __restrict__ hcol,
+                                                     double2* __restrict__ H, double* __restrict__ w0,
+                                                     const int* __restrict__ jdev, const int* __restrict__ reorth,
+                                                     int nblk, int ldp, int m, int B, int pass) {
+  const int j = *jdev, nvec = j + 1;
+  const int nslot = pass == 0 ? nvec + 1 : nvec;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int b = wid / (m + 2), i = wid % (m + 2);
+  if (b >= B || i >= nslot || (pass == 1 && !reorth[b])) return;
+  double2 s = make_double2(0, 0);
+  for (int blk = lane; blk < nblk; blk += 32) {
+    const double2 p = partial[((long long)b * nblk + blk) * ldp + i];
+    s.x += p.x;
+    s.y += p.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+  }
+  if (lane != 0) return;
+  if (i == nvec) {  // first pass only
+    w0[b] = s.x;
+    return;
+  }
+  hcol[(long long)b * (m + 1) + i] = s;
+  double2* h = H + ((long long)b * (m + 1) + i) * m + j;
+  if (pass == 1) {
+    h->x += s.x;
+    h->y += s.y;
+  } else {
+    *h = s;
   }
 }
 
-// hcol[b][i] = sum_blk partial; H[b][i][j] (+)= hcol (accumulate when add != 0)
-__global__ void k_dots_reduce(const double2* __restrict__ partial, double2* __restrict__ hcol, double2* __restrict__ H,
-                              int nvec, int nblk, int ldp, int m, int j, int add) {
-  const int b = blockIdx.x;
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-    double2 s = make_double2(0, 0);
-    for (int blk = 0; blk < nblk; ++blk) {
-      const double2 p = partial[((long long)b * nblk + blk) * ldp + i];
-      s.x += p.x;
-      s.y += p.y;
-    }
-    hcol[(long long)b * (m + 1) + i] = s;
-    double2* h = H + ((long long)b * (m + 1) + i) * m + j;
-    if (add) {
-      h->x += s.x;
-      h->y += s.y;
-    } else {
-      *h = s;
-    }
-  }
-}
-
-// w[b] -= sum_i hcol[b][i] V[b][i]
-__global__ void k_update(const double2* __restrict__ V, double2* __restrict__ w, const double2* __restrict__ hcol,
-                         int N, int nvec, int ldv_vec, int m) {
+// w[b] -= sum_{i <= j} hcol[b][i] V[b][i].  After the first pass every block
+// of right-hand side b evaluates the re-orthogonalisation test of Daniel,
+// Gragg, Kaufman and Stewart on the same data, |w1|^2 = |w0|^2 - |h|^2 <
+// |w0|^2 / 2, and block 0 stores it; the second pass runs only where it holds.
+__global__ void __launch_bounds__(256) k_update(const double2* __restrict__ V, double2* __restrict__ w,
+                                                const double2* __restrict__ hcol, const double* __restrict__ w0,
+                                                int* __restrict__ reorth, const int* __restrict__ jdev, int N,
+                                                int ldv_vec, int m, int pass) {
   __shared__ double2 hs[256];
   const int b = blockIdx.y;
+  if (pass == 1 && !reorth[b]) return;
+  const int nvec = *jdev + 1;
   for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = hcol[(long long)b * (m + 1) + i];
   __syncthreads();
+  if (pass == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    double h2 = 0.0;
+    for (int i = 0; i < nvec; ++i) h2 += hs[i].x * hs[i].x + hs[i].y * hs[i].y;
+    reorth[b] = (w0[b] - h2) < 0.5 * w0[b] ? 1 : 0;
+  }
   const double2* Vb = V + (long long)b * ldv_vec * N;
   double2* wb = w + (long long)b * N;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
@@ -158,13 +197,32 @@ __global__ void k_scale(const double2* __restrict__ src, double2* __restrict__ d
   }
 }
 
-// z = dinv .* v, in precision R
-template <typename R>
-__global__ void k_precond(const double2* __restrict__ v, const double2* __restrict__ dinv, cplx<R>* __restrict__ z,
-                          int N, long long ldv) {
+// V[b][j + 1] = w[b] / nrm[b] (the step's last kernel)
+__global__ void k_scale_next(const double2* __restrict__ w, double2* __restrict__ V, const double* __restrict__ nrm,
+                             const int* __restrict__ jdev, int N, long long ldv) {
   const int b = blockIdx.y;
+  const int j = *jdev;
+  const double s = nrm[b] > 0.0 ? 1.0 / nrm[b] : 0.0;
+  double2* dst = V + (long long)b * ldv + (long long)(j + 1) * N;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
-    const double2 a = v[(long long)b * ldv + n], d = dinv[n];
+    double2 v = w[(long long)b * N + n];
+    v.x *= s;
+    v.y *= s;
+    dst[n] = v;
+  }
+}
+
+__global__ void k_next_j(int* jdev) { *jdev += 1; }
+__global__ void k_set_j(int* jdev, int j) { *jdev = j; }
+
+// z = dinv .* V_j, in precision R
+template <typename R>
+__global__ void k_precond(const double2* __restrict__ V, const double2* __restrict__ dinv, cplx<R>* __restrict__ z,
+                          const int* __restrict__ jdev, int N, long long ldv) {
+  const int b = blockIdx.y;
+  const double2* v = V + (long long)b * ldv + (long long)(*jdev) * N;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+    const double2 a = v[n], d = dinv[n];
     z[(long long)b * N + n] = cmake<cplx<R>>(a.x * d.x - a.y * d.y, a.x * d.y + a.y * d.x);
   }
 }
@@ -181,45 +239,68 @@ __global__ void k_residual(const double2* __restrict__ Vrhs, const double2* __re
   }
 }
 
-// Givens step for column j, one thread per rhs.  Rotation
-// [[conj(c), conj(s)], [-s, c]], c = a/d, s = b/d maps (a, b) to (d, 0).
-__global__ void k_givens(double2* __restrict__ H, double2* __restrict__ cs, double2* __restrict__ sn,
-                         double2* __restrict__ g, const double* __restrict__ hnext, const double* __restrict__ bnorm,
-                         double* __restrict__ est, int m, int j, int nrhs) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+// End of the step for column j, one warp per right-hand side: the norm of w
+// from the partial sums, H[j+1][j] = |w|, then the Givens rotations: the j
+// earlier ones applied to column j (staged in shared memory), a new one
+// [[conj(c), conj(s)], [-s, c]], c = a/d, s = b/d, mapping (a, b) to (d, 0),
+// applied to g; est = |g[j+1]| / |b|.
+__global__ void __launch_bounds__(128) k_finish(double2* __restrict__ H, double2* __restrict__ cs,
+                                                double2* __restrict__ sn, double2* __restrict__ g,
+                                                const double* __restrict__ npart, double* __restrict__ nrm,
+                                                const double* __restrict__ bnorm, double* __restrict__ est,
+                                                const int* __restrict__ jdev, int nblk, int m, int nrhs) {
+  extern __shared__ double2 sh[];  // per warp: column [m+1], c [m], s [m]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * (blockDim.x >> 5) + warp;
   if (b >= nrhs) return;
+  const int j = *jdev;
+  double2* col = sh + (long long)warp * (3 * m + 1);
+  double2* cc = col + m + 1;
+  double2* ss = cc + m;
+  double t = 0.0;
+  for (int blk = lane; blk < nblk; blk += 32) t += npart[(long long)b * nblk + blk];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  const double hnext = sqrt(t);
   double2* Hb = H + (long long)b * (m + 1) * m;
-  double2* cb = cs + (long long)b * m;
-  double2* sb = sn + (long long)b * m;
-  double2* gb = g + (long long)b * (m + 1);
-  Hb[(long long)(j + 1) * m + j] = make_double2(hnext[b], 0.0);
-  for (int i = 0; i < j; ++i) {
-    const double2 c = cb[i], s = sb[i];
-    const double2 hi = Hb[(long long)i * m + j], hn = Hb[(long long)(i + 1) * m + j];
-    double2 t, u;
-    t.x = (c.x * hi.x + c.y * hi.y) + (s.x * hn.x + s.y * hn.y);
-    t.y = (c.x * hi.y - c.y * hi.x) + (s.x * hn.y - s.y * hn.x);
-    u.x = -(s.x * hi.x - s.y * hi.y) + (c.x * hn.x - c.y * hn.y);
-    u.y = -(s.x * hi.y + s.y * hi.x) + (c.x * hn.y + c.y * hn.x);
-    Hb[(long long)i * m + j] = t;
-    Hb[(long long)(i + 1) * m + j] = u;
+  for (int i = lane; i <= j; i += 32) col[i] = Hb[(long long)i * m + j];
+  for (int i = lane; i < j; i += 32) {
+    cc[i] = cs[(long long)b * m + i];
+    ss[i] = sn[(long long)b * m + i];
   }
-  const double2 a = Hb[(long long)j * m + j], bb = Hb[(long long)(j + 1) * m + j];
-  const double d = sqrt(a.x * a.x + a.y * a.y + bb.x * bb.x + bb.y * bb.y);
-  double2 c = make_double2(1.0, 0.0), s = make_double2(0.0, 0.0);
-  if (d > 0.0) {
-    c = make_double2(a.x / d, a.y / d);
-    s = make_double2(bb.x / d, bb.y / d);
+  __syncwarp();
+  if (lane == 0) {
+    nrm[b] = hnext;
+    col[j + 1] = make_double2(hnext, 0.0);
+    for (int i = 0; i < j; ++i) {
+      const double2 c = cc[i], s = ss[i], hi = col[i], hn = col[i + 1];
+      double2 u, v;
+      u.x = (c.x * hi.x + c.y * hi.y) + (s.x * hn.x + s.y * hn.y);
+      u.y = (c.x * hi.y - c.y * hi.x) + (s.x * hn.y - s.y * hn.x);
+      v.x = -(s.x * hi.x - s.y * hi.y) + (c.x * hn.x - c.y * hn.y);
+      v.y = -(s.x * hi.y + s.y * hi.x) + (c.x * hn.y + c.y * hn.x);
+      col[i] = u;
+      col[i + 1] = v;
+    }
+    const double2 a = col[j], bb = col[j + 1];
+    const double d = sqrt(a.x * a.x + a.y * a.y + bb.x * bb.x + bb.y * bb.y);
+    double2 c = make_double2(1.0, 0.0), s = make_double2(0.0, 0.0);
+    if (d > 0.0) {
+      c = make_double2(a.x / d, a.y / d);
+      s = make_double2(bb.x / d, bb.y / d);
+    }
+    cs[(long long)b * m + j] = c;
+    sn[(long long)b * m + j] = s;
+    col[j] = make_double2(d, 0.0);
+    col[j + 1] = make_double2(0.0, 0.0);
+    double2* gb = g + (long long)b * (m + 1);
+    const double2 gj = gb[j];
+    const double2 r = make_double2(-(s.x * gj.x - s.y * gj.y), -(s.x * gj.y + s.y * gj.x));
+    gb[j + 1] = r;
+    gb[j] = make_double2(c.x * gj.x + c.y * gj.y, c.x * gj.y - c.y * gj.x);
+    est[b] = bnorm[b] > 0.0 ? sqrt(r.x * r.x + r.y * r.y) / bnorm[b] : 0.0;
   }
-  cb[j] = c;
-  sb[j] = s;
-  Hb[(long long)j * m + j] = make_double2(d, 0.0);
-  Hb[(long long)(j + 1) * m + j] = make_double2(0.0, 0.0);
-  const double2 gj = gb[j];
-  gb[j + 1] = make_double2(-(s.x * gj.x - s.y * gj.y), -(s.x * gj.y + s.y * gj.x));
-  gb[j] = make_double2(c.x * gj.x + c.y * gj.y, c.x * gj.y - c.y * gj.x);
-  const double2 r = gb[j + 1];
-  est[b] = bnorm[b] > 0.0 ? sqrt(r.x * r.x + r.y * r.y) / bnorm[b] : 0.0;
+  __syncwarp();
+  for (int i = lane; i <= j + 1; i += 32) Hb[(long long)i * m + j] = col[i];
 }
 
 // g = (beta, 0, ...), one thread per rhs
@@ -279,31 +360,44 @@ int alloc_krylov(aim_ctx* c) {
   if (k.V) return AIM_OK;
   const int B = c->max_rhs, m = c->opts.restart, N = c->N;
   k.m = m;
-  // about four blocks per SM over all right-hand sides, at least 256 elements per block
+  // norm kernel: about four blocks per SM over all right-hand sides, at least 256 elements per block
   k.nblk = std::max(1, std::min((4 * 152 + B - 1) / B, (N + 255) / 256));
+  // dot kernel: at least 1024 elements per block, about two blocks per SM per vector group
+  k.nblk_dot = std::max(1, std::min((2 * 152 + B - 1) / B, (N + 1023) / 1024));
+  const int nb = std::max(k.nblk, k.nblk_dot);
   const size_t vec = (size_t)N * sizeof(double2);
   AIM_CUDA_TRY(cudaMalloc(&k.V, vec * B * (m + 1)));
   AIM_CUDA_TRY(cudaMalloc(&k.w, vec * B));
   AIM_CUDA_TRY(cudaMalloc(&k.r, vec * B));
   AIM_CUDA_TRY(cudaMalloc(&k.H, sizeof(double2) * B * (m + 1) * m));
   AIM_CUDA_TRY(cudaMalloc(&k.hcol, sizeof(double2) * B * (m + 1)));
-  AIM_CUDA_TRY(cudaMalloc(&k.partial, sizeof(double2) * B * k.nblk * (m + 1 + kDotGroup)));
+  AIM_CUDA_TRY(cudaMalloc(&k.partial, sizeof(double2) * B * nb * (m + 1 + kDotGroup)));
   AIM_CUDA_TRY(cudaMalloc(&k.cs, sizeof(double2) * B * m));
   AIM_CUDA_TRY(cudaMalloc(&k.sn, sizeof(double2) * B * m));
   AIM_CUDA_TRY(cudaMalloc(&k.g, sizeof(double2) * B * (m + 1)));
   AIM_CUDA_TRY(cudaMalloc(&k.y, sizeof(double2) * B * m));
-  AIM_CUDA_TRY(cudaMalloc(&k.nrm, sizeof(double) * B * (2 + k.nblk)));
+  AIM_CUDA_TRY(cudaMalloc(&k.nrm, sizeof(double) * B * (3 + nb)));
   AIM_CUDA_TRY(cudaMalloc(&k.bnorm, sizeof(double) * B));
   AIM_CUDA_TRY(cudaMalloc(&k.active, sizeof(int) * B));
+  AIM_CUDA_TRY(cudaMalloc(&k.reorth, sizeof(int) * B));
+  AIM_CUDA_TRY(cudaMalloc(&k.jdev, sizeof(int)));
   AIM_CUDA_TRY(cudaMallocHost(&k.h_est, sizeof(double) * B));
+  AIM_CUDA_TRY(cudaStreamCreateWithFlags(&k.cap_stream, cudaStreamNonBlocking));
   return AIM_OK;
+}
+
+void drop_step_graph(aim_ctx* c) {
+  if (c->kw.step_exec) cudaGraphExecDestroy(c->kw.step_exec);
+  c->kw.step_exec = nullptr;
 }
 
 void free_krylov(aim_ctx* c) {
   KrylovWork& k = c->kw;
+  if (k.step_exec) cudaGraphExecDestroy(k.step_exec);
+  if (k.cap_stream) cudaStreamDestroy(k.cap_stream);
   cudaFree(k.V); cudaFree(k.w); cudaFree(k.r); cudaFree(k.H); cudaFree(k.hcol); cudaFree(k.partial);
   cudaFree(k.cs); cudaFree(k.sn); cudaFree(k.g); cudaFree(k.y); cudaFree(k.nrm); cudaFree(k.bnorm);
-  cudaFree(k.active);
+  cudaFree(k.active); cudaFree(k.reorth); cudaFree(k.jdev);
   if (k.h_est) cudaFreeHost(k.h_est);
   k = KrylovWork{};
 }
@@ -315,50 +409,106 @@ struct Solver {
   int B, N, m;
   cudaStream_t st;
   double* est;       // device [B]
+  double* w0;        // device [B]
   double* npart;     // device [B][nblk]
   Solver(aim_ctx* cc, int nrhs) : c(cc), k(cc->kw), B(nrhs), N(cc->N), m(cc->kw.m), st(cc->stream) {
     est = k.nrm + B;
-    npart = k.nrm + 2 * B;
+    w0 = k.nrm + 2 * B;
+    npart = k.nrm + 3 * B;
   }
   dim3 vgrid() const { return dim3((unsigned)std::min(1024, std::max(1, (N + 255) / 256)), B); }
   int chk(const char* w) { return launch_check(c, w); }
+  long long ldV() const { return (long long)(m + 1) * N; }
 
-  int norms(const double2* x, long long ldx, double* out) {
+  int norm_partials(const double2* x, long long ldx) {
     AIM_LAUNCH(c, "k_norm2", k_norm2<<<dim3(k.nblk, B), 256, 0, st>>>(x, npart, N, ldx, k.nblk));
-    AIM_TRY(chk("k_norm2"));
+    return chk("k_norm2");
+  }
+  int norms(const double2* x, long long ldx, double* out) {
+    AIM_TRY(norm_partials(x, ldx));
     AIM_LAUNCH(c, "k_sqrt_sum", k_sqrt_sum<<<(B + 127) / 128, 128, 0, st>>>(npart, out, k.nblk, B));
     return chk("k_sqrt_sum");
   }
-  double2* Vcol(int i) { return k.V + (size_t)i * N; }  // basis i of rhs 0; rhs stride (m+1) N
-  long long ldV() const { return (long long)(m + 1) * N; }
 
-  // w = Z~ (dinv .* v_j) in the requested precision
-  int apply(int j, int precision) {
+  // One Arnoldi step for the column j held in device memory (k.jdev):
+  // w = Z~ (dinv .* v_j) in `precision`, CGS with selective second pass,
+  // H column, Givens rotation, v_{j+1} = w / |w|, j += 1.
+  int step(int precision) {
     if (precision == AIM_C64) {
-      AIM_LAUNCH(c, "k_precond", k_precond<float><<<vgrid(), 256, 0, st>>>(Vcol(j), c->dinv64, c->p32.xbuf, N, ldV()));
+      AIM_LAUNCH(c, "k_precond", k_precond<float><<<vgrid(), 256, 0, st>>>(k.V, c->dinv64, c->p32.xbuf, k.jdev, N, ldV()));
       AIM_TRY(chk("k_precond"));
       AIM_TRY(matvec(c, c->p32.xbuf, c->p32.ybuf, B, AIM_C64));
-      return convert_c64_to_c128(c, c->p32.ybuf, k.w, (int64_t)B * N);
+      AIM_TRY(convert_c64_to_c128(c, c->p32.ybuf, k.w, (int64_t)B * N));
+    } else {
+      AIM_LAUNCH(c, "k_precond", k_precond<double><<<vgrid(), 256, 0, st>>>(k.V, c->dinv64, c->p64.xbuf, k.jdev, N, ldV()));
+      AIM_TRY(chk("k_precond"));
+      AIM_TRY(matvec(c, c->p64.xbuf, k.w, B, precision));
     }
-    AIM_LAUNCH(c, "k_precond", k_precond<double><<<vgrid(), 256, 0, st>>>(Vcol(j), c->dinv64, c->p64.xbuf, N, ldV()));
-    AIM_TRY(chk("k_precond"));
-    return matvec(c, c->p64.xbuf, k.w, B, precision);
-  }
-
-  int orthogonalise(int j) {
-    const int nvec = j + 1;
     const int ldp = m + 1 + kDotGroup;
+    const dim3 dgrid((m + 2 + kDotGroup - 1) / kDotGroup, k.nblk_dot, B);
+    const int rblocks = (B * (m + 2) * 32 + 255) / 256;
     for (int pass = 0; pass < 2; ++pass) {
-      AIM_LAUNCH(c, "k_dots", k_dots<<<dim3(k.nblk, B), 256, 0, st>>>(k.V, k.w, k.partial, N, nvec, m + 1, k.nblk, ldp));
+      AIM_LAUNCH(c, "k_dots", k_dots<<<dgrid, 256, 0, st>>>(k.V, k.w, k.partial, k.jdev, k.reorth, N, m + 1,
+                                                            k.nblk_dot, ldp, pass));
       AIM_TRY(chk("k_dots"));
-      AIM_LAUNCH(c, "k_dots_reduce", k_dots_reduce<<<B, 64, 0, st>>>(k.partial, k.hcol, k.H, nvec, k.nblk, ldp, m, j, pass));
+      AIM_LAUNCH(c, "k_dots_reduce", k_dots_reduce<<<rblocks, 256, 0, st>>>(k.partial, k.hcol, k.H, w0, k.jdev,
+                                                                            k.reorth, k.nblk_dot, ldp, m, B, pass));
       AIM_TRY(chk("k_dots_reduce"));
-      AIM_LAUNCH(c, "k_update", k_update<<<vgrid(), 256, 0, st>>>(k.V, k.w, k.hcol, N, nvec, m + 1, m));
+      AIM_LAUNCH(c, "k_update", k_update<<<vgrid(), 256, 0, st>>>(k.V, k.w, k.hcol, w0, k.reorth, k.jdev, N, m + 1,
+                                                                  m, pass));
       AIM_TRY(chk("k_update"));
     }
-    AIM_TRY(norms(k.w, N, k.nrm));
-    AIM_LAUNCH(c, "k_scale", k_scale<<<vgrid(), 256, 0, st>>>(k.w, Vcol(j + 1), k.nrm, N, N, ldV()));
-    return chk("k_scale");
+    AIM_TRY(norm_partials(k.w, N));
+    const size_t fsm = sizeof(double2) * 4 * (3 * m + 1);
+    AIM_LAUNCH(c, "k_finish", k_finish<<<(B + 3) / 4, 128, fsm, st>>>(k.H, k.cs, k.sn, k.g, npart, k.nrm, k.bnorm, est,
+                                                                      k.jdev, k.nblk, m, B));
+    AIM_TRY(chk("k_finish"));
+    AIM_LAUNCH(c, "k_scale", k_scale_next<<<vgrid(), 256, 0, st>>>(k.w, k.V, k.nrm, k.jdev, N, ldV()));
+    AIM_TRY(chk("k_scale"));
+    AIM_LAUNCH(c, "k_next_j", k_next_j<<<1, 1, 0, st>>>(k.jdev));
+    return chk("k_next_j");
+  }
+
+  // The step as a CUDA graph (captured on first use for this precision and
+  // batch size), or launched directly while the profiler is on.
+  int run_step(int precision, bool allow_graph) {
+    if (!allow_graph || c->prof.on) return step(precision);
+    if (!k.step_exec || k.step_prec != precision || k.step_nrhs != B) {
+      if (k.step_exec) {
+        cudaGraphExecDestroy(k.step_exec);
+        k.step_exec = nullptr;
+      }
+      const int64_t l0 = c->launches;
+      const cudaStream_t st0 = st;
+      AIM_CUDA_TRY(cudaStreamBeginCapture(k.cap_stream, cudaStreamCaptureModeThreadLocal));
+      c->stream = st = k.cap_stream;  // every launch of the step goes to the capturing stream
+      const int rc = step(precision);
+      c->stream = st = st0;
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(k.cap_stream, &graph);
+      k.step_launches = c->launches - l0;
+      c->launches = l0;
+      if (rc != AIM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      if (e != cudaSuccess) {
+        set_error(std::string("aim_solve: stream capture of the Arnoldi step: ") + cudaGetErrorString(e));
+        return AIM_ECUDA;
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&k.step_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) {
+        k.step_exec = nullptr;
+        set_error(std::string("aim_solve: graph instantiation: ") + cudaGetErrorString(ei));
+        return AIM_ECUDA;
+      }
+      k.step_prec = precision;
+      k.step_nrhs = B;
+    }
+    c->launches += k.step_launches;
+    AIM_CUDA_TRY(cudaGraphLaunch(k.step_exec, st));
+    return AIM_OK;
   }
 };
 }  // namespace
@@ -371,6 +521,8 @@ int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_so
   const int prec = c->opts.precision;
   const int exact = prec == AIM_C128_F64 ? AIM_C128_F64 : AIM_C128;  // FP64-accurate product for true residuals
   const int check = std::max(1, c->opts.check_every);
+  AIM_TRY(prepare_product(c, prec));
+  AIM_TRY(prepare_product(c, exact));
   std::vector<int> act(nrhs, 1);
   std::vector<double> bn(nrhs), rel(nrhs, 1.0);
   AIM_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double2) * (size_t)nrhs * N, c->stream));
@@ -383,7 +535,7 @@ int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_so
       rel[b] = 0.0;
     }
   int iters = 0, restarts = 0;
-  bool first = true;
+  bool first = true, stepped = false;
   for (;;) {
     // true residual (FP64 product) and convergence check
     AIM_CUDA_TRY(cudaMemcpyAsync(k.active, act.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, c->stream));
@@ -410,17 +562,18 @@ int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_so
     first = false;
     ++restarts;
     AIM_CUDA_TRY(cudaMemcpyAsync(k.active, act.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, c->stream));
-    // v0 = r / beta, g = (beta, 0, ...)
+    // v0 = r / beta, g = (beta, 0, ...), j = 0
     AIM_LAUNCH(c, "k_scale", k_scale<<<s.vgrid(), 256, 0, c->stream>>>(k.r, k.V, k.nrm, N, N, s.ldV()));
     AIM_TRY(s.chk("k_scale"));
     AIM_LAUNCH(c, "k_ginit", k_ginit<<<(nrhs + 127) / 128, 128, 0, c->stream>>>(k.g, k.nrm, m, nrhs));
     AIM_TRY(s.chk("k_ginit"));
+    AIM_LAUNCH(c, "k_set_j", k_set_j<<<1, 1, 0, c->stream>>>(k.jdev, 0));
+    AIM_TRY(s.chk("k_set_j"));
     int kk = 0;
     for (int j = 0; j < m && iters < c->opts.maxit; ++j) {
-      AIM_TRY(s.apply(j, prec));
-      AIM_TRY(s.orthogonalise(j));
-      AIM_LAUNCH(c, "k_givens", k_givens<<<(nrhs + 127) / 128, 128, 0, c->stream>>>(k.H, k.cs, k.sn, k.g, k.nrm, k.bnorm, s.est, m, j, nrhs));
-      AIM_TRY(s.chk("k_givens"));
+      // the very first step runs uncaptured (first launches set kernel attributes)
+      AIM_TRY(s.run_step(prec, stepped));
+      stepped = true;
       ++iters;
       kk = j + 1;
       if ((j + 1) % check == 0 || j == m - 1) {

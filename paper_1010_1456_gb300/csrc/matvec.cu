@@ -585,6 +585,23 @@ int ensure_grids(aim_ctx* c, int precision) {
   return AIM_OK;
 }
 
+int prepare_product(aim_ctx* c, int precision) {
+  AIM_TRY(ensure_grids(c, precision));
+  if (precision == AIM_C128) return ensure_ff_arrays(c);
+  if (c->max_rhs >= kRhsLanesMin) {
+    const long long Nc = (long long)c->n[0] * c->n[1] * c->n[2];
+    if (precision == AIM_C64 && !c->p32.phiT) {
+      AIM_CUDA_TRY(cudaMalloc(&c->p32.phiT, sizeof(float2) * c->max_rhs * 4 * Nc));
+      AIM_CUDA_TRY(cudaMalloc(&c->p32.xT, sizeof(float2) * c->max_rhs * c->N));
+    }
+    if (precision == AIM_C128_F64 && !c->p64.phiT) {
+      AIM_CUDA_TRY(cudaMalloc(&c->p64.phiT, sizeof(double2) * c->max_rhs * 4 * Nc));
+      AIM_CUDA_TRY(cudaMalloc(&c->p64.xT, sizeof(double2) * c->max_rhs * c->N));
+    }
+  }
+  return AIM_OK;
+}
+
 int matvec(aim_ctx* c, const void* x, void* y, int nrhs, int precision) {
   AIM_TRY(ensure_grids(c, precision));
   if (precision == AIM_C64)

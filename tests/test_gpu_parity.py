@@ -205,7 +205,7 @@ def test_fft_config_rejects_bad_choices(plate_a):
         g.aim_fft_config(ctx, g.AIM_C64, [4, 0, 0, 0, 0])
     with pytest.raises(g.AIMError):
         g.aim_autotune(ctx, g.AIM_C64, nrhs=ctx.max_rhs + 1)
-    assert g.aim_fft_config(ctx, g.AIM_C128) == [1, 1, 2, 1, 1]  # the built-in rule
+    assert g.aim_fft_config(ctx, g.AIM_C128) == [2, 2, 2, 2, 2]  # the built-in rule
     assert g.aim_fft_config(ctx, g.AIM_C64) == [2, 2, 2, 2, 2]
 
 

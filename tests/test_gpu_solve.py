@@ -108,3 +108,32 @@ def test_iteration_limit_reports_noconv():
     X, info = g.aim_solve(ctx, V, 1e-12, raise_on_noconv=False)
     assert info["status"] == g.AIM_ENOCONV and not info["converged"].any()
     assert 0 < info["rel_res"][0] < 1.0  # X holds the last iterate, better than zero
+
+
+def test_graph_replayed_steps_equal_direct_launches(sphere):
+    """Arnoldi steps replayed from the captured CUDA graph give the same
+    iterate, bit for bit, as the same steps launched one by one (the profiler
+    forces direct launches); also on a caller's non-default stream."""
+    R, v, t, op = sphere
+    kh, po = random_incidence(1, seed=5)  # 2 right-hand sides
+    ctx = g.aim_setup(v, t, K0, H, max_rhs=2, precision=g.AIM_C64)
+    V = g.aim_rhs_planewave(ctx, kh, po)
+    g.aim_solve(ctx, V, TOL)  # one-time allocations and conversions of the first solve
+    l0 = g.aim_launch_count(ctx)
+    Xg, ig = g.aim_solve(ctx, V, TOL)
+    launches_graph = g.aim_launch_count(ctx) - l0
+    g.aim_profile(ctx, 1)
+    l0 = g.aim_launch_count(ctx)
+    Xd, idd = g.aim_solve(ctx, V, TOL)
+    launches_direct = g.aim_launch_count(ctx) - l0
+    g.aim_profile(ctx, 0)
+    assert ig["iterations"] == idd["iterations"] and launches_graph == launches_direct
+    assert torch.equal(Xg, Xd)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        g.aim_set_stream(ctx, s)
+        Xs, _ = g.aim_solve(ctx, V, TOL)
+    s.synchronize()
+    g.aim_set_stream(ctx, torch.cuda.current_stream())
+    assert torch.equal(Xs, Xg)
+    assert true_res(op, V.cpu().numpy(), Xg.cpu().numpy()).max() <= 1.01 * TOL
