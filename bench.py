@@ -383,6 +383,66 @@ def run_serve(args):
     return 0
 
 
+# ---------------------------------------------------------------- complexity sweep
+SWEEP = {"plate": (1, 2, 4, 8, 16, 32), "sphere": (1, 2, 4, 8, 16)}
+
+
+def run_sweep(args):
+    """Matvec time against N over the plates 1-32 lambda and spheres 1-16 lambda
+    (the shape of the paper's complexity figure, Section 3, on one GPU): one
+    right-hand side, complex64 and FP64-accurate products, FFT kernels
+    autotuned, L2 flushed between products."""
+    import torch
+
+    import paper_1010_1456_gb300 as g
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    rows = []
+    from aim_inputs import random_complex
+
+    kinds = [(k, sz) for k in ("plate", "sphere") for sz in SWEEP[k] if not args.sweep_max or sz <= args.sweep_max]
+    for kind, size in kinds:
+        verts, tris = mesh_for(kind, size)
+        t0 = time.perf_counter()
+        ctx = g.aim_setup(verts, tris, K0, H, M=2, near_radius=3 * H, max_rhs=1, stream=stream.cuda_stream)
+        setup_s = time.perf_counter() - t0
+        n, L, nnz = g.aim_grid_info(ctx)
+        row = {"kind": kind, "size_lambda": size, "N": ctx.N, "grid": n, "padded": L, "nnz_near": nnz,
+               "setup_s": round(setup_s, 3)}
+        xh = random_complex((1, ctx.N), 7)
+        for name, P, dt in (("c64", g.AIM_C64, torch.complex64), ("fp64_accurate", g.AIM_C128, torch.complex128)):
+            x = torch.from_numpy(xh).to(dev, dt)
+            y = torch.empty_like(x)
+            g.aim_autotune(ctx, P, nrhs=1, reps=2)
+            for _ in range(3):
+                g.aim_matvec(ctx, x, y, precision=P)
+            torch.cuda.synchronize()
+            reps = 20
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                g.aim_matvec(ctx, x, y, precision=P)
+                b.record(stream)
+                torch.cuda.synchronize()
+                tot += a.elapsed_time(b)
+            row[name + "_ms"] = round(tot / reps, 4)
+        rows.append(row)
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+    line = {"metric": "AIM matvec time vs N (complexity sweep)", "unit": "ms", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "PEC plates 1-32 lambda (mesh lambda/9) and icospheres 1-16 lambda, h = lambda/10, "
+                                   "M = 2, near radius 3h, one RHS", "l2": "flushed between products"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
@@ -414,6 +474,12 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- our arm
 FFT_KERNEL_NAMES = {1: "stockham", 2: "fourstep", 3: "fourstep_small"}
+
+
+def fft_kernel_names(g, chosen, L):
+    """Pass -> kernel name; a planar grid (L_z = 1) runs no z passes."""
+    return {p_: ("none (planar grid)" if L[2] == 1 and p_ in ("fft_z_fwd", "fft_z_inv") else FFT_KERNEL_NAMES[k])
+            for p_, k in zip(g.FFT_PASSES, chosen)}
 
 
 def cufft_comparison(torch, dev, stream, L, nrhs, wide, kernels, flush, reps=5, max_gb=8.0):
@@ -478,7 +544,7 @@ def run_ours(args, rank, world, local_rank):
         t0 = time.perf_counter()
         chosen, tune_ms = g.aim_autotune(ctx, P, nrhs=nrhs, reps=3)
         tune = {"seconds": round(time.perf_counter() - t0, 2),
-                "kernels": {p_: FFT_KERNEL_NAMES[k] for p_, k in zip(g.FFT_PASSES, chosen)},
+                "kernels": fft_kernel_names(g, chosen, L),
                 "pass_ms": {p_: {FFT_KERNEL_NAMES[k]: round(float(tune_ms[i, k]), 4) for k in (1, 2, 3)
                                  if tune_ms[i, k] > 0} for i, p_ in enumerate(g.FFT_PASSES)}}
     else:
@@ -532,6 +598,29 @@ def run_ours(args, rank, world, local_rank):
         vms = sum(a.elapsed_time(b) for a, b in evs) / vsteps
         variants[vname] = {"what": vprec, "matvec_per_s": nrhs * 1e3 / vms, "ms_per_step": vms, "steps": vsteps}
         del xv, yv
+    if args.variants and L[2] == 1:
+        # the same product on the full three-dimensional grid (no plane collapse)
+        ctx3 = g.aim_setup(verts, tris, K0, H, M=2, near_radius=3 * H, max_rhs=nrhs, precision=P,
+                           stream=stream.cuda_stream, planar=False)
+        if args.autotune:
+            g.aim_autotune(ctx3, P, nrhs=nrhs, reps=3)
+        for _ in range(3):
+            g.aim_matvec(ctx3, x, y, precision=P)
+        torch.cuda.synchronize()
+        vsteps = max(10, args.steps // 4)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(vsteps)]
+        for i in range(vsteps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            g.aim_matvec(ctx3, x, y, precision=P)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        vms = sum(a.elapsed_time(b) for a, b in evs) / vsteps
+        n3, L3, _ = g.aim_grid_info(ctx3)
+        variants["grid_3d"] = {"what": f"same product on the full grid {n3} padded {L3} (no plane collapse)",
+                               "matvec_per_s": nrhs * 1e3 / vms, "ms_per_step": vms, "steps": vsteps}
+        ctx3.close()
+        del ctx3
     solve = solve_section(g, ctx, kind, size, nrhs, P) if args.solve else None
 
     # end to end through the host-buffer entry point (copies inside the timed region)
@@ -613,7 +702,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": args.workload, "N": N, "grid": n, "padded": L, "nnz_near": nnz, "nrhs": nrhs,
                    "M": 2, "h_lambda": H, "near_radius_h": 3, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
-                   "fft_kernels": {p_: FFT_KERNEL_NAMES[k] for p_, k in zip(g.FFT_PASSES, chosen)}},
+                   "fft_kernels": fft_kernel_names(g, chosen, L)},
         "autotune": tune,
         "cufft_comparison": cufft_comparison(torch, dev, stream, L, nrhs, wide, kernels, flush) if args.cufft else None,
         "roofline": roof,
@@ -647,11 +736,15 @@ def main():
     ap.add_argument("--cufft", type=int, default=1, help="1: also time the unpruned cuFFT convolution")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--serve", action="store_true", help="run the serving stream instead of the product benchmark")
+    ap.add_argument("--sweep", action="store_true", help="matvec time against N over plates and spheres")
+    ap.add_argument("--sweep-max", type=float, default=0.0, help="largest size (lambda) in the sweep; 0: all")
     ap.add_argument("--serve-sizes", choices=sorted(SERVE_SIZES), default="small")
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-max-rhs", type=int, default=16)
     args = ap.parse_args()
+    if args.sweep:
+        return run_sweep(args)
     if args.serve:
         return run_serve(args)
     if args.warmup < 3:

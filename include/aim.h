@@ -81,6 +81,11 @@ typedef struct {
   int max_rhs;     /* largest nrhs the context is sized for (default 1, <= 256) */
   int verbose;     /* 0: silent (default) */
   void* stream;    /* cudaStream_t; NULL = the legacy default stream */
+  int planar;      /* 1 (default): when every basis function's weights vanish off one z plane of
+                      the grid (a planar scatterer at constant z on a node plane), keep only that
+                      plane: the grid becomes nx x ny x 1 and the convolution two-dimensional
+                      (same product up to rounding; aim_grid_info reports the reduced grid).
+                      0: always three-dimensional. */
 } aim_opts;
 
 /* Per-solve report. rel_res and iters are caller arrays of length nrhs. */
@@ -175,7 +180,7 @@ int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int
 /*
  * Copy internal setup arrays to host memory for inspection and testing.
  * what: AIM_EXPORT_ANCHORS int32 [N][3] (absolute node index),
- *       AIM_EXPORT_WEIGHTS f64 [N][4][(M+1)^3],
+ *       AIM_EXPORT_WEIGHTS f64 [N][4][(M+1)^3] (full stencil, also for a planar grid),
  *       AIM_EXPORT_NEAR_PTR int32 [N+1], AIM_EXPORT_NEAR_COL int32 [nnz],
  *       AIM_EXPORT_NEAR_VAL c128 [nnz], AIM_EXPORT_DIAG c128 [N],
  *       AIM_EXPORT_GHAT c128 octant [Lz/2+1][Ly/2+1][Lx/2+1] (scaled by 1/(Lx Ly Lz)),
@@ -245,7 +250,8 @@ int aim_fft_config(aim_ctx* ctx, int precision, const int32_t* set, int32_t* get
  * kernel runs one warm-up product and `reps` products timed with CUDA events
  * on the context stream, and the fastest stays selected.  Allocates (and
  * frees) one input and one output batch, and the precision's grids like the
- * first aim_matvec.  kernel_out [5] (may be NULL) receives the choices;
+ * first aim_matvec.  kernel_out [5] (may be NULL) receives the choices (a
+ * planar grid has no z passes: those two keep their setting, untimed);
  * ms_out [5][4] (may be NULL) the mean time in ms of each pass under each
  * AIM_FFT_* value (-1 where not tried).  The profiler's totals and on/off
  * state are left as they were.  Synchronises.

@@ -29,6 +29,7 @@ class aim_opts(C.Structure):
         ("max_rhs", C.c_int),
         ("verbose", C.c_int),
         ("stream", C.c_void_p),
+        ("planar", C.c_int),
     ]
 
 

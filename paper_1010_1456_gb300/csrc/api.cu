@@ -97,6 +97,7 @@ void aim_default_opts(aim_opts* o) {
   o->max_rhs = 1;
   o->verbose = 0;
   o->stream = nullptr;
+  o->planar = 1;
 }
 
 int aim_setup(const aim_mesh* mesh, double k, double h, int M, double near_radius, const aim_opts* opts,
@@ -296,9 +297,22 @@ int aim_export(aim_ctx* c, int what, void* dst, size_t bytes) {
   AIM_TRY(check_ctx(c));
   const void* src = nullptr;
   size_t need = 0;
+  std::vector<double> full;
   switch (what) {
     case AIM_EXPORT_ANCHORS: src = c->h_anchor.data(); need = c->h_anchor.size() * 4; break;
-    case AIM_EXPORT_WEIGHTS: src = c->h_lam.data(); need = c->h_lam.size() * 8; break;
+    case AIM_EXPORT_WEIGHTS:
+      if (c->planar) {  // the full stencil: the kept plane's weights, zeros elsewhere
+        const int P = c->M + 1, S3 = P * P * P, S2 = P * P;
+        full.assign((size_t)c->N * 4 * S3, 0.0);
+        for (size_t mc = 0; mc < (size_t)c->N * 4; ++mc)
+          for (int t = 0; t < S2; ++t) full[mc * S3 + (size_t)c->kk0 * S2 + t] = c->h_lam[mc * S2 + t];
+        src = full.data();
+        need = full.size() * 8;
+      } else {
+        src = c->h_lam.data();
+        need = c->h_lam.size() * 8;
+      }
+      break;
     case AIM_EXPORT_NEAR_PTR: src = c->h_near_ptr.data(); need = c->h_near_ptr.size() * 4; break;
     case AIM_EXPORT_NEAR_COL: src = c->h_near_col.data(); need = c->h_near_col.size() * 4; break;
     case AIM_EXPORT_NEAR_VAL: src = c->h_near_val.data(); need = c->h_near_val.size() * 8; break;

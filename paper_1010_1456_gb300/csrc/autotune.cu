@@ -73,6 +73,7 @@ static int autotune(aim_ctx* c, int precision, int nrhs, int reps, int32_t* kern
   if (ms_out)
     for (int i = 0; i < AIM_FFT_PASSES * 4; ++i) ms_out[i] = -1.0;
   for (int pass = 0; pass < AIM_FFT_PASSES && rc == AIM_OK; ++pass) {
+    if ((pass == 0 || pass == 4) && c->L[2] == 1) continue;  // a planar grid has no z passes
     const int last = pass == 2 ? AIM_FFT_FOURSTEP_SMALL : AIM_FFT_FOURSTEP;
     int best = AIM_FFT_AUTO;
     double best_ms = 0.0;
@@ -90,7 +91,7 @@ static int autotune(aim_ctx* c, int precision, int nrhs, int reps, int32_t* kern
     c->fft_kernel[pol][pass] = best;
   }
   if (rc == AIM_OK && kernel_out)
-    for (int pass = 0; pass < AIM_FFT_PASSES; ++pass) kernel_out[pass] = c->fft_kernel[pol][pass];
+    for (int pass = 0; pass < AIM_FFT_PASSES; ++pass) kernel_out[pass] = fft_kernel_for(c, pol, pass);
   cudaStreamSynchronize(c->stream);
   cudaFree(x);
   cudaFree(y);

@@ -126,16 +126,13 @@ struct KrylovWork {
   double2* V = nullptr;      // [B][m+1][N] Arnoldi basis
   double2* w = nullptr;      // [B][N]
   double2* r = nullptr;      // [B][N]
-  double2* H = nullptr;      // [B][m+1][m]
+  double2* H = nullptr;      // [m][B][m+1] Hessenberg columns (column j of every RHS is contiguous)
   double2* hcol = nullptr;   // [B][m+1] current column (dot results)
   double2* partial = nullptr;// [B][nblk][m+1+kDotGroup] partial dots
-  double2* cs = nullptr;     // [B][m]
-  double2* sn = nullptr;     // [B][m]
-  double2* g = nullptr;      // [B][m+1]
-  double2* y = nullptr;      // [B][m]
-  double* nrm = nullptr;     // [B] norms; then est [B], w0 [B] (|w|^2 before orthogonalising), partials
+  double2* y = nullptr;      // [B][m] least-squares solution of the cycle
+  double* nrm = nullptr;     // [B] norms; then w0 [B] (|w|^2 before orthogonalising), norm partials
   double* bnorm = nullptr;   // [B]
-  double* h_est = nullptr;   // pinned host [B] residual estimates
+  double2* h_H = nullptr;    // pinned host copy of H columns
   int* active = nullptr;     // [B]
   int* reorth = nullptr;     // [B] second Gram-Schmidt pass needed for the current column
   int* jdev = nullptr;       // current Arnoldi column (read by the step's kernels)
@@ -154,7 +151,9 @@ struct KrylovWork {
 
 struct aim_ctx {
   // problem
-  int N = 0, M = 2, S = 27;
+  int N = 0, M = 2, S = 27;  // S: stencil nodes per basis function ((M+1)^3, or (M+1)^2 on a planar grid)
+  int planar = 0;            // grid reduced to the one z plane that holds every nonzero weight
+  int kk0 = 0;               // that plane's offset in the stencil
   double k = 0, h = 0, radius = 0;
   int lo[3] = {0, 0, 0};
   int n[3] = {0, 0, 0};  // grid nodes x, y, z

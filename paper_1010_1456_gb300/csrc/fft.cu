@@ -358,19 +358,22 @@ static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P
   const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
   const int Lx = c->L[0], Ly = c->L[1], Lz = c->L[2];
   const FftPlan* pd = c->plan_dev;
-  {  // z forward: g0 [G][nz][ny][nx] -> g1 [G][Lz][ny][nx]
+  // A planar grid (Lz = nz = 1) has no z passes: the y passes read and write g0.
+  const bool zpass = Lz > 1;
+  typename P::S* gz = zpass ? g1 : g0;
+  if (zpass) {  // z forward: g0 [G][nz][ny][nx] -> g1 [G][Lz][ny][nx]
     StridedArgs a{};
     a.n_in = nz; a.n_out = Lz; a.X = nx; a.A = ny;
     a.sG_in = (long long)nz * ny * nx; a.sA_in = nx; a.sP_in = (long long)ny * nx;
     a.sG_out = (long long)Lz * ny * nx; a.sA_out = nx; a.sP_out = (long long)ny * nx;
     AIM_TRY((strided_pass<P, false>(c, 0, "fft_z_fwd", g0, g1, a, G, pd + 2, Lz, tw[2])));
   }
-  {  // y forward: g1 [G][Lz][ny][nx] -> g2 [G][Lz][Ly][nx]
+  {  // y forward: gz [G][Lz][ny][nx] -> g2 [G][Lz][Ly][nx]
     StridedArgs a{};
     a.n_in = ny; a.n_out = Ly; a.X = nx; a.A = Lz;
     a.sG_in = (long long)Lz * ny * nx; a.sA_in = (long long)ny * nx; a.sP_in = nx;
     a.sG_out = (long long)Lz * Ly * nx; a.sA_out = (long long)Ly * nx; a.sP_out = nx;
-    AIM_TRY((strided_pass<P, false>(c, 1, "fft_y_fwd", g1, g2, a, G, pd + 1, Ly, tw[1])));
+    AIM_TRY((strided_pass<P, false>(c, 1, "fft_y_fwd", gz, g2, a, G, pd + 1, Ly, tw[1])));
   }
   {  // x: forward, times Ghat, inverse, in place on g2
     XArgs a{};
@@ -379,14 +382,14 @@ static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P
     a.hx = Lx / 2 + 1; a.hy = Ly / 2 + 1; a.hz = Lz / 2 + 1;
     AIM_TRY((x_pass<P>(c, "fft_x_conv", g2, a, pd + 0, Lx, ghat, tw[0])));
   }
-  {  // y inverse: g2 -> g1 [G][Lz][ny][nx]
+  {  // y inverse: g2 -> gz [G][Lz][ny][nx]
     StridedArgs a{};
     a.n_in = Ly; a.n_out = ny; a.X = nx; a.A = Lz;
     a.sG_in = (long long)Lz * Ly * nx; a.sA_in = (long long)Ly * nx; a.sP_in = nx;
     a.sG_out = (long long)Lz * ny * nx; a.sA_out = (long long)ny * nx; a.sP_out = nx;
-    AIM_TRY((strided_pass<P, true>(c, 3, "fft_y_inv", g2, g1, a, G, pd + 1, Ly, tw[1])));
+    AIM_TRY((strided_pass<P, true>(c, 3, "fft_y_inv", g2, gz, a, G, pd + 1, Ly, tw[1])));
   }
-  {  // z inverse: g1 -> g0 [G][nz][ny][nx]
+  if (zpass) {  // z inverse: g1 -> g0 [G][nz][ny][nx]
     StridedArgs a{};
     a.n_in = Lz; a.n_out = nz; a.X = nx; a.A = ny;
     a.sG_in = (long long)Lz * ny * nx; a.sA_in = nx; a.sP_in = (long long)ny * nx;
@@ -460,12 +463,16 @@ int build_ghat(aim_ctx* c) {
   AIM_LAUNCH(c, "sample_green",
              sample_green<<<1024, 256, 0, c->stream>>>(a, Lx, Ly, Lz, c->n[0], c->n[1], c->n[2], c->k, c->h));
   AIM_TRY(launch_check(c, "sample_green"));
-  // z: full transform a -> b ; y: b -> a ; x: rows of a in place (FP64)
+  // z: full transform a -> b (none for a planar grid, Lz = 1); y: b -> a;
+  // x: rows of a in place (FP64)
   StridedArgs s{};
   s.n_in = Lz; s.n_out = Lz; s.X = Lx; s.A = Ly;
   s.sG_in = total; s.sA_in = Lx; s.sP_in = (long long)Ly * Lx;
   s.sG_out = total; s.sA_out = Lx; s.sP_out = (long long)Ly * Lx;
-  AIM_TRY((launch_strided<P64, false>(c, "ghat_z", a, b, s, 1, c->plan_dev + 2, Lz, c->p64.tw[2])));
+  if (Lz > 1)
+    AIM_TRY((launch_strided<P64, false>(c, "ghat_z", a, b, s, 1, c->plan_dev + 2, Lz, c->p64.tw[2])));
+  else
+    std::swap(a, b);
   s.n_in = Ly; s.n_out = Ly; s.X = Lx; s.A = Lz;
   s.sA_in = (long long)Ly * Lx; s.sP_in = Lx;
   s.sA_out = (long long)Ly * Lx; s.sP_out = Lx;

@@ -1,18 +1,21 @@
-// Batched right-preconditioned restarted GMRES(m) on the device.
+// Batched right-preconditioned restarted GMRES(m).
 //
 // Paper Section 2.2: diagonal preconditioner, iteration stopped on the
 // relative residual.  All right-hand sides advance in lockstep; each keeps
-// its own Arnoldi basis, Hessenberg matrix and Givens rotations.  Dot
-// products, norms and rotations are FP64 (two-level block reductions, so the
-// results do not depend on launch timing).  Orthogonalisation is classical
-// Gram-Schmidt with a second pass where the Daniel-Gragg-Kaufman-Stewart test
-// asks for it.  One Arnoldi step is captured once as a CUDA graph and replayed
-// (its kernels take the column index from device memory).  The Arnoldi product is
-// complex64 or complex128 (aim_opts.precision); every restart recomputes the
-// true residual V - Z~ X with the complex128 product, so the complex64 mode
-// is FP64 iterative refinement wrapped around a complex64 inner solve.
+// its own Arnoldi basis and Hessenberg matrix.  On the device: the product,
+// dot products and norms in FP64 (two-level block reductions, so the results
+// do not depend on launch timing), classical Gram-Schmidt with a second pass
+// where the Daniel-Gragg-Kaufman-Stewart test asks for it.  One Arnoldi step
+// is captured once as a CUDA graph and replayed (its kernels take the column
+// index from device memory).  On the host, every few steps: the new
+// Hessenberg columns, their Givens rotations in FP64, the residual estimate,
+// and at the end of a cycle the small triangular solve.  The Arnoldi product
+// is complex64 or complex128 (aim_opts.precision); every restart recomputes
+// the true residual V - Z~ X with the FP64-accurate product, so the complex64
+// mode is FP64 iterative refinement wrapped around a complex64 inner solve.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 
 #include "common.h"
 
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(256) k_dots(const double2* __restrict__ V, con
 }
 
 // hcol[b][i] = sum over blocks of the partial dots (one warp per (b, i));
-// H[b][i][j] = hcol (first pass) or += hcol (second pass).  First pass,
+// H[j][b][i] = hcol (first pass) or += hcol (second pass).  First pass,
 // slot i = j + 1: w0[b] = |w|^2.
 __global__ void __launch_bounds__(256) k_dots_reduce(const double2* __restrict__ partial, double2* __restrict__ hcol,
                                                      double2* __restrict__ H, double* __restrict__ w0,
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(256) k_dots_reduce(const double2* __restrict__
     return;
   }
   hcol[(long long)b * (m + 1) + i] = s;
-  double2* h = H + ((long long)b * (m + 1) + i) * m + j;
+  double2* h = H + ((long long)j * B + b) * (m + 1) + i;
   if (pass == 1) {
     h->x += s.x;
     h->y += s.y;
@@ -197,12 +200,30 @@ __global__ void k_scale(const double2* __restrict__ src, double2* __restrict__ d
   }
 }
 
-// V[b][j + 1] = w[b] / nrm[b] (the step's last kernel)
-__global__ void k_scale_next(const double2* __restrict__ w, double2* __restrict__ V, const double* __restrict__ nrm,
-                             const int* __restrict__ jdev, int N, long long ldv) {
+// End of the step: |w| from the norm kernel's partial sums (every block
+// reduces them in the same order), V[b][j + 1] = w[b] / |w|; block 0 stores
+// |w| as the subdiagonal H[j][b][j + 1].
+__global__ void __launch_bounds__(256) k_normalize(const double2* __restrict__ w, double2* __restrict__ V,
+                                                   const double* __restrict__ npart, double2* __restrict__ H,
+                                                   const int* __restrict__ jdev, int N, long long ldv, int nblk,
+                                                   int m, int B) {
+  __shared__ double red[8];
+  __shared__ double nrm_s;
   const int b = blockIdx.y;
   const int j = *jdev;
-  const double s = nrm[b] > 0.0 ? 1.0 / nrm[b] : 0.0;
+  double t = 0.0;
+  for (int blk = threadIdx.x; blk < nblk; blk += blockDim.x) t += npart[(long long)b * nblk + blk];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) u += red[i];
+    nrm_s = sqrt(u);
+    if (blockIdx.x == 0) H[((long long)j * B + b) * (m + 1) + j + 1] = make_double2(nrm_s, 0.0);
+  }
+  __syncthreads();
+  const double s = nrm_s > 0.0 ? 1.0 / nrm_s : 0.0;
   double2* dst = V + (long long)b * ldv + (long long)(j + 1) * N;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
     double2 v = w[(long long)b * N + n];
@@ -236,98 +257,6 @@ __global__ void k_residual(const double2* __restrict__ Vrhs, const double2* __re
     const long long i = (long long)b * N + n;
     double2 v = Vrhs[i], t = y[i];
     r[i] = on ? make_double2(v.x - t.x, v.y - t.y) : make_double2(0, 0);
-  }
-}
-
-// End of the step for column j, one warp per right-hand side: the norm of w
-// from the partial sums, H[j+1][j] = |w|, then the Givens rotations: the j
-// earlier ones applied to column j (staged in shared memory), a new one
-// [[conj(c), conj(s)], [-s, c]], c = a/d, s = b/d, mapping (a, b) to (d, 0),
-// applied to g; est = |g[j+1]| / |b|.
-__global__ void __launch_bounds__(128) k_finish(double2* __restrict__ H, double2* __restrict__ cs,
-                                                double2* __restrict__ sn, double2* __restrict__ g,
-                                                const double* __restrict__ npart, double* __restrict__ nrm,
-                                                const double* __restrict__ bnorm, double* __restrict__ est,
-                                                const int* __restrict__ jdev, int nblk, int m, int nrhs) {
-  extern __shared__ double2 sh[];  // per warp: column [m+1], c [m], s [m]
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (b >= nrhs) return;
-  const int j = *jdev;
-  double2* col = sh + (long long)warp * (3 * m + 1);
-  double2* cc = col + m + 1;
-  double2* ss = cc + m;
-  double t = 0.0;
-  for (int blk = lane; blk < nblk; blk += 32) t += npart[(long long)b * nblk + blk];
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  const double hnext = sqrt(t);
-  double2* Hb = H + (long long)b * (m + 1) * m;
-  for (int i = lane; i <= j; i += 32) col[i] = Hb[(long long)i * m + j];
-  for (int i = lane; i < j; i += 32) {
-    cc[i] = cs[(long long)b * m + i];
-    ss[i] = sn[(long long)b * m + i];
-  }
-  __syncwarp();
-  if (lane == 0) {
-    nrm[b] = hnext;
-    col[j + 1] = make_double2(hnext, 0.0);
-    for (int i = 0; i < j; ++i) {
-      const double2 c = cc[i], s = ss[i], hi = col[i], hn = col[i + 1];
-      double2 u, v;
-      u.x = (c.x * hi.x + c.y * hi.y) + (s.x * hn.x + s.y * hn.y);
-      u.y = (c.x * hi.y - c.y * hi.x) + (s.x * hn.y - s.y * hn.x);
-      v.x = -(s.x * hi.x - s.y * hi.y) + (c.x * hn.x - c.y * hn.y);
-      v.y = -(s.x * hi.y + s.y * hi.x) + (c.x * hn.y + c.y * hn.x);
-      col[i] = u;
-      col[i + 1] = v;
-    }
-    const double2 a = col[j], bb = col[j + 1];
-    const double d = sqrt(a.x * a.x + a.y * a.y + bb.x * bb.x + bb.y * bb.y);
-    double2 c = make_double2(1.0, 0.0), s = make_double2(0.0, 0.0);
-    if (d > 0.0) {
-      c = make_double2(a.x / d, a.y / d);
-      s = make_double2(bb.x / d, bb.y / d);
-    }
-    cs[(long long)b * m + j] = c;
-    sn[(long long)b * m + j] = s;
-    col[j] = make_double2(d, 0.0);
-    col[j + 1] = make_double2(0.0, 0.0);
-    double2* gb = g + (long long)b * (m + 1);
-    const double2 gj = gb[j];
-    const double2 r = make_double2(-(s.x * gj.x - s.y * gj.y), -(s.x * gj.y + s.y * gj.x));
-    gb[j + 1] = r;
-    gb[j] = make_double2(c.x * gj.x + c.y * gj.y, c.x * gj.y - c.y * gj.x);
-    est[b] = bnorm[b] > 0.0 ? sqrt(r.x * r.x + r.y * r.y) / bnorm[b] : 0.0;
-  }
-  __syncwarp();
-  for (int i = lane; i <= j + 1; i += 32) Hb[(long long)i * m + j] = col[i];
-}
-
-// g = (beta, 0, ...), one thread per rhs
-__global__ void k_ginit(double2* __restrict__ g, const double* __restrict__ beta, int m, int nrhs) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nrhs) return;
-  for (int i = 0; i <= m; ++i) g[(long long)b * (m + 1) + i] = make_double2(i == 0 ? beta[b] : 0.0, 0.0);
-}
-
-// back substitution H y = g on the leading kk x kk block, one thread per rhs
-__global__ void k_backsolve(const double2* __restrict__ H, const double2* __restrict__ g, double2* __restrict__ y,
-                            int m, int kk, int nrhs) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nrhs) return;
-  const double2* Hb = H + (long long)b * (m + 1) * m;
-  const double2* gb = g + (long long)b * (m + 1);
-  double2* yb = y + (long long)b * m;
-  for (int i = kk - 1; i >= 0; --i) {
-    double2 s = gb[i];
-    for (int l = i + 1; l < kk; ++l) {
-      const double2 h = Hb[(long long)i * m + l], yl = yb[l];
-      s.x -= h.x * yl.x - h.y * yl.y;
-      s.y -= h.x * yl.y + h.y * yl.x;
-    }
-    const double2 d = Hb[(long long)i * m + i];
-    const double dd = d.x * d.x + d.y * d.y;
-    yb[i] = dd > 0.0 ? make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd) : make_double2(0, 0);
   }
 }
 
@@ -372,16 +301,13 @@ int alloc_krylov(aim_ctx* c) {
   AIM_CUDA_TRY(cudaMalloc(&k.H, sizeof(double2) * B * (m + 1) * m));
   AIM_CUDA_TRY(cudaMalloc(&k.hcol, sizeof(double2) * B * (m + 1)));
   AIM_CUDA_TRY(cudaMalloc(&k.partial, sizeof(double2) * B * nb * (m + 1 + kDotGroup)));
-  AIM_CUDA_TRY(cudaMalloc(&k.cs, sizeof(double2) * B * m));
-  AIM_CUDA_TRY(cudaMalloc(&k.sn, sizeof(double2) * B * m));
-  AIM_CUDA_TRY(cudaMalloc(&k.g, sizeof(double2) * B * (m + 1)));
   AIM_CUDA_TRY(cudaMalloc(&k.y, sizeof(double2) * B * m));
-  AIM_CUDA_TRY(cudaMalloc(&k.nrm, sizeof(double) * B * (3 + nb)));
+  AIM_CUDA_TRY(cudaMalloc(&k.nrm, sizeof(double) * B * (2 + nb)));
   AIM_CUDA_TRY(cudaMalloc(&k.bnorm, sizeof(double) * B));
   AIM_CUDA_TRY(cudaMalloc(&k.active, sizeof(int) * B));
   AIM_CUDA_TRY(cudaMalloc(&k.reorth, sizeof(int) * B));
   AIM_CUDA_TRY(cudaMalloc(&k.jdev, sizeof(int)));
-  AIM_CUDA_TRY(cudaMallocHost(&k.h_est, sizeof(double) * B));
+  AIM_CUDA_TRY(cudaMallocHost(&k.h_H, sizeof(double2) * (size_t)B * (m + 1) * m));
   AIM_CUDA_TRY(cudaStreamCreateWithFlags(&k.cap_stream, cudaStreamNonBlocking));
   return AIM_OK;
 }
@@ -396,9 +322,9 @@ void free_krylov(aim_ctx* c) {
   if (k.step_exec) cudaGraphExecDestroy(k.step_exec);
   if (k.cap_stream) cudaStreamDestroy(k.cap_stream);
   cudaFree(k.V); cudaFree(k.w); cudaFree(k.r); cudaFree(k.H); cudaFree(k.hcol); cudaFree(k.partial);
-  cudaFree(k.cs); cudaFree(k.sn); cudaFree(k.g); cudaFree(k.y); cudaFree(k.nrm); cudaFree(k.bnorm);
+  cudaFree(k.y); cudaFree(k.nrm); cudaFree(k.bnorm);
   cudaFree(k.active); cudaFree(k.reorth); cudaFree(k.jdev);
-  if (k.h_est) cudaFreeHost(k.h_est);
+  if (k.h_H) cudaFreeHost(k.h_H);
   k = KrylovWork{};
 }
 
@@ -408,13 +334,11 @@ struct Solver {
   KrylovWork& k;
   int B, N, m;
   cudaStream_t st;
-  double* est;       // device [B]
   double* w0;        // device [B]
   double* npart;     // device [B][nblk]
   Solver(aim_ctx* cc, int nrhs) : c(cc), k(cc->kw), B(nrhs), N(cc->N), m(cc->kw.m), st(cc->stream) {
-    est = k.nrm + B;
-    w0 = k.nrm + 2 * B;
-    npart = k.nrm + 3 * B;
+    w0 = k.nrm + B;
+    npart = k.nrm + 2 * B;
   }
   dim3 vgrid() const { return dim3((unsigned)std::min(1024, std::max(1, (N + 255) / 256)), B); }
   int chk(const char* w) { return launch_check(c, w); }
@@ -431,8 +355,8 @@ struct Solver {
   }
 
   // One Arnoldi step for the column j held in device memory (k.jdev):
-  // w = Z~ (dinv .* v_j) in `precision`, CGS with selective second pass,
-  // H column, Givens rotation, v_{j+1} = w / |w|, j += 1.
+  // w = Z~ (dinv .* v_j) in `precision`, CGS with selective second pass into
+  // the Hessenberg column H[j], v_{j+1} = w / |w|, j += 1.
   int step(int precision) {
     if (precision == AIM_C64) {
       AIM_LAUNCH(c, "k_precond", k_precond<float><<<vgrid(), 256, 0, st>>>(k.V, c->dinv64, c->p32.xbuf, k.jdev, N, ldV()));
@@ -459,12 +383,9 @@ struct Solver {
       AIM_TRY(chk("k_update"));
     }
     AIM_TRY(norm_partials(k.w, N));
-    const size_t fsm = sizeof(double2) * 4 * (3 * m + 1);
-    AIM_LAUNCH(c, "k_finish", k_finish<<<(B + 3) / 4, 128, fsm, st>>>(k.H, k.cs, k.sn, k.g, npart, k.nrm, k.bnorm, est,
-                                                                      k.jdev, k.nblk, m, B));
-    AIM_TRY(chk("k_finish"));
-    AIM_LAUNCH(c, "k_scale", k_scale_next<<<vgrid(), 256, 0, st>>>(k.w, k.V, k.nrm, k.jdev, N, ldV()));
-    AIM_TRY(chk("k_scale"));
+    AIM_LAUNCH(c, "k_normalize", k_normalize<<<vgrid(), 256, 0, st>>>(k.w, k.V, npart, k.H, k.jdev, N, ldV(), k.nblk,
+                                                                     m, B));
+    AIM_TRY(chk("k_normalize"));
     AIM_LAUNCH(c, "k_next_j", k_next_j<<<1, 1, 0, st>>>(k.jdev));
     return chk("k_next_j");
   }
@@ -513,6 +434,56 @@ struct Solver {
 };
 }  // namespace
 
+// Givens QR of one right-hand side's Hessenberg matrix, on the host in FP64
+// (the rotations are a sequential chain of a few flops each: on the device it
+// would keep one warp on GB300's narrow FP64 pipe for every step).  Rotation
+// [[conj(c), conj(s)], [-s, c]], c = a/d, s = b/d, maps (a, b) to (d, 0).
+struct HostLsq {
+  using cd = std::complex<double>;
+  int m;
+  std::vector<cd> R, cs, sn, g;  // R column-major [m][m+1]
+  explicit HostLsq(int mm) : m(mm), R((size_t)mm * (mm + 1)), cs(mm), sn(mm), g(mm + 1) {}
+  void start(double beta) {
+    std::fill(g.begin(), g.end(), cd(0.0, 0.0));
+    g[0] = cd(beta, 0.0);
+  }
+  // column j (rows 0..j+1 of the raw Hessenberg matrix); returns |g[j+1]|
+  double add_column(int j, const double2* col) {
+    cd* r = &R[(size_t)j * (m + 1)];
+    for (int i = 0; i <= j + 1; ++i) r[i] = cd(col[i].x, col[i].y);
+    for (int i = 0; i < j; ++i) {
+      const cd t = std::conj(cs[i]) * r[i] + std::conj(sn[i]) * r[i + 1];
+      const cd u = -sn[i] * r[i] + cs[i] * r[i + 1];
+      r[i] = t;
+      r[i + 1] = u;
+    }
+    const double d = std::sqrt(std::norm(r[j]) + std::norm(r[j + 1]));
+    cd cc(1.0, 0.0), ss(0.0, 0.0);
+    if (d > 0.0) {
+      cc = r[j] / d;
+      ss = r[j + 1] / d;
+    }
+    cs[j] = cc;
+    sn[j] = ss;
+    r[j] = cd(d, 0.0);
+    r[j + 1] = cd(0.0, 0.0);
+    g[j + 1] = -ss * g[j];
+    g[j] = std::conj(cc) * g[j];
+    return std::abs(g[j + 1]);
+  }
+  // back substitution R y = g on the leading kk x kk block
+  void solve(int kk, double2* y) const {
+    std::vector<cd> yy(kk);
+    for (int i = kk - 1; i >= 0; --i) {
+      cd sum = g[i];
+      for (int l = i + 1; l < kk; ++l) sum -= R[(size_t)l * (m + 1) + i] * yy[l];
+      const cd dii = R[(size_t)i * (m + 1) + i];
+      yy[i] = std::norm(dii) > 0.0 ? sum / dii : cd(0.0, 0.0);
+    }
+    for (int i = 0; i < kk; ++i) y[i] = make_double2(yy[i].real(), yy[i].imag());
+  }
+};
+
 int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_solve_info* info) {
   AIM_TRY(alloc_krylov(c));
   Solver s(c, nrhs);
@@ -525,6 +496,9 @@ int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_so
   AIM_TRY(prepare_product(c, exact));
   std::vector<int> act(nrhs, 1);
   std::vector<double> bn(nrhs), rel(nrhs, 1.0);
+  std::vector<HostLsq> lsq(nrhs, HostLsq(m));
+  std::vector<double2> ybuf((size_t)nrhs * m);
+  const size_t colsz = (size_t)nrhs * (m + 1);  // one Hessenberg column of every right-hand side
   AIM_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double2) * (size_t)nrhs * N, c->stream));
   AIM_TRY(s.norms(V, N, k.bnorm));
   AIM_CUDA_TRY(cudaMemcpyAsync(bn.data(), k.bnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->stream));
@@ -565,11 +539,28 @@ int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_so
     // v0 = r / beta, g = (beta, 0, ...), j = 0
     AIM_LAUNCH(c, "k_scale", k_scale<<<s.vgrid(), 256, 0, c->stream>>>(k.r, k.V, k.nrm, N, N, s.ldV()));
     AIM_TRY(s.chk("k_scale"));
-    AIM_LAUNCH(c, "k_ginit", k_ginit<<<(nrhs + 127) / 128, 128, 0, c->stream>>>(k.g, k.nrm, m, nrhs));
-    AIM_TRY(s.chk("k_ginit"));
     AIM_LAUNCH(c, "k_set_j", k_set_j<<<1, 1, 0, c->stream>>>(k.jdev, 0));
     AIM_TRY(s.chk("k_set_j"));
-    int kk = 0;
+    for (int b = 0; b < nrhs; ++b) lsq[b].start(beta[b]);
+    int kk = 0, done_cols = 0;
+    // Hessenberg columns done_cols .. kk-1 to the host, Givens rotations; true when every active RHS is converged
+    auto absorb = [&](bool* converged) -> int {
+      const int ncol = kk - done_cols;
+      if (ncol > 0) {
+        AIM_CUDA_TRY(cudaMemcpyAsync(k.h_H, k.H + (size_t)done_cols * colsz, sizeof(double2) * colsz * ncol,
+                                     cudaMemcpyDeviceToHost, c->stream));
+        AIM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+      }
+      bool done = true;
+      for (int q = 0; q < ncol; ++q)
+        for (int b = 0; b < nrhs; ++b) {
+          const double r = lsq[b].add_column(done_cols + q, k.h_H + ((size_t)q * nrhs + b) * (m + 1));
+          if (q == ncol - 1 && act[b] && !(bn[b] > 0.0 && r / bn[b] <= tol)) done = false;
+        }
+      done_cols = kk;
+      *converged = done;
+      return AIM_OK;
+    };
     for (int j = 0; j < m && iters < c->opts.maxit; ++j) {
       // the very first step runs uncaptured (first launches set kernel attributes)
       AIM_TRY(s.run_step(prec, stepped));
@@ -577,16 +568,16 @@ int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_so
       ++iters;
       kk = j + 1;
       if ((j + 1) % check == 0 || j == m - 1) {
-        AIM_CUDA_TRY(cudaMemcpyAsync(k.h_est, s.est, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->stream));
-        AIM_CUDA_TRY(cudaStreamSynchronize(c->stream));
-        bool done = true;
-        for (int b = 0; b < nrhs; ++b)
-          if (act[b] && !(k.h_est[b] <= tol)) done = false;
+        bool done = false;
+        AIM_TRY(absorb(&done));
         if (done) break;
       }
     }
-    AIM_LAUNCH(c, "k_backsolve", k_backsolve<<<(nrhs + 127) / 128, 128, 0, c->stream>>>(k.H, k.g, k.y, m, kk, nrhs));
-    AIM_TRY(s.chk("k_backsolve"));
+    bool unused = false;
+    AIM_TRY(absorb(&unused));
+    for (int b = 0; b < nrhs; ++b) lsq[b].solve(kk, &ybuf[(size_t)b * m]);
+    AIM_CUDA_TRY(cudaMemcpyAsync(k.y, ybuf.data(), sizeof(double2) * (size_t)nrhs * m, cudaMemcpyHostToDevice,
+                                 c->stream));
     AIM_LAUNCH(c, "k_xupdate", k_xupdate<<<s.vgrid(), 256, 0, c->stream>>>(k.V, k.y, c->dinv64, X, N, kk, m, m + 1, k.active));
     AIM_TRY(s.chk("k_xupdate"));
   }

@@ -112,11 +112,11 @@ __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restr
                                                    const int32_t* __restrict__ base, const int32_t* __restrict__ nptr,
                                                    const int32_t* __restrict__ ncol,
                                                    const cplx<typename MD::R>* __restrict__ nval, int N, long long Nc,
-                                                   int nx, int ny, int nrhs, typename MD::R fvec, typename MD::R frho) {
+                                                   int nx, int ny, int nrhs, typename MD::R fvec, typename MD::R frho,
+                                                   int S) {
   using R = typename MD::R;
   using C = cplx<R>;
   constexpr int P = M + 1;
-  constexpr int S = P * P * P;
   const int lane = threadIdx.x & 7;
   const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
   const bool live = m < N;
@@ -220,11 +220,10 @@ __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R
                                                        const int32_t* __restrict__ ncol,
                                                        const cplx<typename MI::R>* __restrict__ nval, int N,
                                                        long long Nc, int nx, int ny, int B, typename MI::R fvec,
-                                                       typename MI::R frho) {
+                                                       typename MI::R frho, int S) {
   using R = typename MI::R;
   using C = cplx<R>;
   constexpr int P = M + 1;
-  constexpr int S = P * P * P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* ys = reinterpret_cast<C*>(smem_raw);  // [8][B]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -379,9 +378,8 @@ __global__ void __launch_bounds__(256) interp_near_ff(const float4* __restrict__
                                                       const int32_t* __restrict__ base, const int32_t* __restrict__ nptr,
                                                       const int32_t* __restrict__ ncol,
                                                       const float4* __restrict__ nval, int N, long long Nc, int nx,
-                                                      int ny, int nrhs, float2 fvec, float2 frho) {
+                                                      int ny, int nrhs, float2 fvec, float2 frho, int S) {
   constexpr int P = M + 1;
-  constexpr int S = P * P * P;
   const int lane = threadIdx.x & 7;
   const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
   const bool live = m < N;
@@ -477,7 +475,7 @@ static int run_product_ff(aim_ctx* c, const double2* x, double2* y, int nrhs) {
   AIM_LAUNCH(c, "interp_near",                                                                                     \
              (interp_near_ff<MM><<<blocks, 256, 0, c->stream>>>(p.grid0, p.xff, y, p.lam, c->base, c->near_ptr,    \
                                                                 c->near_col, p.near_val, c->N, Nc, c->n[0], c->n[1], \
-                                                                nrhs, fvec, frho)))
+                                                                nrhs, fvec, frho, c->S)))
     switch (c->M) {
       case 1: AIM_INTERP_FF(1); break;
       case 2: AIM_INTERP_FF(2); break;
@@ -524,7 +522,7 @@ static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename 
   AIM_LAUNCH(c, "interp_near",                                                                                   \
              (interp_near_rhs<MI, MM, RL><<<blocks, 256, sm, c->stream>>>(pd.phiT, pd.xT, y, lam, c->base,        \
                                                                           c->near_ptr, c->near_col, nval, c->N, Nc, \
-                                                                          c->n[0], c->n[1], nrhs, fvec, frho)))
+                                                                          c->n[0], c->n[1], nrhs, fvec, frho, c->S)))
     switch (c->M * 2 + (two ? 1 : 0)) {
       case 2: AIM_INTERP_RHS(1, 1); break;
       case 3: AIM_INTERP_RHS(1, 2); break;
@@ -544,7 +542,7 @@ static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename 
   AIM_LAUNCH(c, "interp_near",                                                                                  \
              (interp_near<MI, MM><<<blocks, 256, 0, c->stream>>>(phi, x, y, lam, c->base, c->near_ptr,          \
                                                                  c->near_col, nval, c->N, Nc, c->n[0], c->n[1], \
-                                                                 nrhs, fvec, frho)))
+                                                                 nrhs, fvec, frho, c->S)))
     switch (c->M) {
       case 1: AIM_INTERP(1); break;
       case 2: AIM_INTERP(2); break;
@@ -657,7 +655,7 @@ int matvec_c64_bufs(aim_ctx* c, const float2* x, float2* y, int nrhs, float2* g0
   AIM_LAUNCH(c, "interp_near",                                                                                \
              (interp_near<M32, MM><<<blocks, 256, 0, c->stream>>>(g0, x, y, c->p32.lam, c->base, c->near_ptr, \
                                                                   c->near_col, c->p32.near_val, c->N, Nc,     \
-                                                                  c->n[0], c->n[1], nrhs, fvec, frho)))
+                                                                  c->n[0], c->n[1], nrhs, fvec, frho, c->S)))
     switch (c->M) {
       case 1: AIM_INTERP32(1); break;
       case 2: AIM_INTERP32(2); break;

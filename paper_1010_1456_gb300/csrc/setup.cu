@@ -475,25 +475,62 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
     }
   });
 
+  // ---- plane collapse: every weight off one z plane of the grid is zero
+  // (a planar scatterer at constant z on a node plane).  Q and Phi vanish off
+  // that plane, so the grid keeps only it and the convolution becomes 2-D with
+  // G_h(dx, dy, 0); the near entries above used the full stencil and are
+  // unchanged.
+  int S_run = S;
+  if (c->opts.planar) {
+    bool same = true;
+    for (int m = 1; m < N && same; ++m) same = c->h_anchor[3 * (size_t)m + 2] == c->h_anchor[2];
+    std::vector<char> used(P, 0);
+    if (same)
+      for (size_t mc = 0; mc < (size_t)N * 4; ++mc)
+        for (int s = 0; s < S; ++s)
+          if (c->h_lam[mc * S + s] != 0.0) used[s / (P * P)] = 1;
+    int nused = 0, kk0 = 0;
+    for (int kk = 0; kk < P; ++kk)
+      if (used[kk]) {
+        ++nused;
+        kk0 = kk;
+      }
+    if (same && nused == 1) {
+      const int S2 = P * P;
+      std::vector<double> lam2((size_t)N * 4 * S2);
+      for (size_t mc = 0; mc < (size_t)N * 4; ++mc)
+        for (int t = 0; t < S2; ++t) lam2[mc * S2 + t] = c->h_lam[mc * S + (size_t)kk0 * S2 + t];
+      c->h_lam.swap(lam2);
+      c->planar = 1;
+      c->kk0 = kk0;
+      c->S = S_run = S2;
+      c->lo[2] = c->h_anchor[2] + kk0;
+      c->n[2] = 1;
+      c->L[2] = 1;
+      c->plan[2] = make_plan(1);
+      Nc = (long long)c->n[0] * c->n[1];
+    }
+  }
+
   // ---- projection lists (node-ordered transpose of the weights)
   const int nx = c->n[0], ny = c->n[1];
   std::vector<int32_t> base(N);
   for (int m = 0; m < N; ++m) {
     const int ix = c->h_anchor[3 * (size_t)m] - c->lo[0], iy = c->h_anchor[3 * (size_t)m + 1] - c->lo[1],
-              iz = c->h_anchor[3 * (size_t)m + 2] - c->lo[2];
+              iz = c->h_anchor[3 * (size_t)m + 2] + c->kk0 - c->lo[2];
     base[m] = (int32_t)(((int64_t)iz * ny + iy) * nx + ix);
   }
   std::vector<int32_t> pptr(Nc + 1, 0);
   auto nonzero = [&](int m, int s) {
-    const double* lm = &c->h_lam[(size_t)m * 4 * S];
-    return lm[s] != 0.0 || lm[S + s] != 0.0 || lm[2 * S + s] != 0.0 || lm[3 * S + s] != 0.0;
+    const double* lm = &c->h_lam[(size_t)m * 4 * S_run];
+    return lm[s] != 0.0 || lm[S_run + s] != 0.0 || lm[2 * S_run + s] != 0.0 || lm[3 * S_run + s] != 0.0;
   };
   auto node_of = [&](int m, int s) {
     const int i = s % P, j = (s / P) % P, kk = s / (P * P);
     return (int64_t)base[m] + ((int64_t)kk * ny + j) * nx + i;
   };
   for (int m = 0; m < N; ++m)
-    for (int s = 0; s < S; ++s)
+    for (int s = 0; s < S_run; ++s)
       if (nonzero(m, s)) pptr[node_of(m, s) + 1]++;
   for (long long u = 0; u < Nc; ++u) pptr[u + 1] += pptr[u];
   const int64_t nent = pptr[Nc];
@@ -504,12 +541,12 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
   {
     std::vector<int32_t> fill(pptr.begin(), pptr.end() - 1);
     for (int m = 0; m < N; ++m)
-      for (int s = 0; s < S; ++s)
+      for (int s = 0; s < S_run; ++s)
         if (nonzero(m, s)) {
           const int64_t e = fill[node_of(m, s)]++;
           pm[e] = m;
           for (int cc = 0; cc < 4; ++cc) {
-            pw64[4 * e + cc] = c->h_lam[(size_t)m * 4 * S + cc * S + s];
+            pw64[4 * e + cc] = c->h_lam[(size_t)m * 4 * S_run + cc * S_run + s];
             pw32[4 * e + cc] = (float)pw64[4 * e + cc];
           }
         }

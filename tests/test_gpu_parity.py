@@ -41,17 +41,25 @@ def _cuda():
     g.load()
 
 
-def make(verts, tris, M=2, radius=None, max_rhs=1, precision=g.AIM_C128, near_rows=None):
+def make(verts, tris, M=2, radius=None, max_rhs=1, precision=g.AIM_C128, near_rows=None, planar=True):
     r = 3 * H if radius is None else radius
-    ctx = g.aim_setup(verts, tris, K0, H, M=M, near_radius=r, max_rhs=max_rhs, precision=precision)
+    ctx = g.aim_setup(verts, tris, K0, H, M=M, near_radius=r, max_rhs=max_rhs, precision=precision, planar=planar)
     op = oaim.AIMOperator(RWG(verts, tris), K0, H, M, near_radius=r, near_rows=near_rows)
     return ctx, op
 
 
 @pytest.fixture(scope="module")
 def plate_a():
+    """1 lambda plate on the full three-dimensional grid (no plane collapse)."""
     v, t = plate_mesh(1.0, 9)
-    return make(v, t, max_rhs=3)
+    return make(v, t, max_rhs=3, planar=False)
+
+
+@pytest.fixture(scope="module")
+def plate_a_planar():
+    """The same plate with its grid collapsed to the z = 0 plane."""
+    v, t = plate_mesh(1.0, 9)
+    return make(v, t, max_rhs=17)
 
 
 @pytest.fixture(scope="module")
@@ -138,11 +146,13 @@ def test_other_stencil_orders(M):
         assert rel(y, op.matvec(x)) <= 1e-12
 
 
+@pytest.mark.parametrize("planar", [True, False])
 @pytest.mark.parametrize("nrhs", [8, 9, 17, 70])
-def test_many_rhs_products(nrhs):
-    """Batches of 8 to 70 right-hand sides (lanes, tiles and grid chunks cover every RHS)."""
+def test_many_rhs_products(nrhs, planar):
+    """Batches of 8 to 70 right-hand sides (lanes, tiles and grid chunks cover every RHS),
+    on the plate's collapsed and full grids."""
     v, t = plate_mesh(1.0, 9)
-    ctx, op = make(v, t, max_rhs=nrhs)
+    ctx, op = make(v, t, max_rhs=nrhs, planar=planar)
     x = random_complex((nrhs, ctx.N), 40 + nrhs)
     ref = op.matvec(x)
     for prec in WIDE:
@@ -160,9 +170,9 @@ FFT_CHOICES = [g.AIM_FFT_STOCKHAM, g.AIM_FFT_FOURSTEP, g.AIM_FFT_FOURSTEP_SMALL]
 
 
 @pytest.mark.parametrize("kernel", FFT_CHOICES)
-def test_every_fft_kernel_choice(plate_a, sphere_small, kernel):
+def test_every_fft_kernel_choice(plate_a, plate_a_planar, sphere_small, kernel):
     """Each FFT kernel, forced on all five passes, gives the oracle's product in every precision."""
-    for (ctx, op), nrhs, seed in ((plate_a, 3, 31), (sphere_small, 2, 32)):
+    for (ctx, op), nrhs, seed in ((plate_a, 3, 31), (plate_a_planar, 3, 34), (sphere_small, 2, 32)):
         x = random_complex((nrhs, ctx.N), seed)
         ref = op.matvec(x)
         for prec in WIDE + [g.AIM_C64]:
@@ -212,7 +222,7 @@ def test_fft_config_rejects_bad_choices(plate_a):
 def test_stockham_fallback_length():
     """A padded length outside the four-step menu (18) runs the Stockham kernels."""
     v, t = plate_mesh(0.7, 6)
-    ctx, op = make(v, t, max_rhs=2)
+    ctx, op = make(v, t, max_rhs=2, planar=False)
     n, L, _ = g.aim_grid_info(ctx)
     assert L[0] == 18 and L[1] == 18 and L[2] == 5
     x = random_complex((2, ctx.N), 18)
@@ -312,3 +322,41 @@ def test_float_float_accuracy_beats_complex64_by_far(sphere_small):
     a = g.aim_matvec(ctx, x, precision=g.AIM_C128).cpu().numpy()
     b = g.aim_matvec(ctx, x, precision=g.AIM_C128_F64).cpu().numpy()
     assert rel(a, b) <= 1e-13
+
+
+def test_planar_grid_collapses_to_one_plane(plate_a, plate_a_planar):
+    """A plate on the z = 0 node plane: only that plane of the grid is kept, the
+    convolution is two-dimensional, and the product is the oracle's (full 3-D
+    grid) in every precision and batch size, including the lanes-over-RHS path."""
+    ctx, op = plate_a_planar
+    n, L, _ = g.aim_grid_info(ctx)
+    assert n == [op.n[0], op.n[1], 1] and L == [op.L[0], op.L[1], 1]
+    lam = g.aim_export(ctx, g.AIM_EXPORT_WEIGHTS)
+    assert np.abs(lam - op.lam).max() <= 1e-12 * np.abs(op.lam).max()
+    for nrhs, seed in ((1, 51), (3, 52), (17, 53)):
+        x = random_complex((nrhs, ctx.N), seed)
+        ref = op.matvec(x)
+        for prec in WIDE:
+            y = g.aim_matvec(ctx, torch.from_numpy(x).cuda(), precision=prec).cpu().numpy()
+            assert rel(y, ref) <= 1e-12
+        y32 = g.aim_matvec(ctx, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
+        assert rel(y32, op.matvec(x.astype(np.complex64).astype(np.complex128))) <= 1e-5
+    # same product as the three-dimensional grid, to rounding
+    ctx3, _ = plate_a
+    x = torch.from_numpy(random_complex((3, ctx.N), 54)).cuda()
+    a = g.aim_matvec(ctx, x, precision=g.AIM_C128_F64).cpu().numpy()
+    b = g.aim_matvec(ctx3, x, precision=g.AIM_C128_F64).cpu().numpy()
+    assert rel(a, b) <= 1e-13
+
+
+def test_plate_off_node_plane_keeps_three_dimensions():
+    """A plate between node planes has weights on every stencil plane: no collapse."""
+    v, t = plate_mesh(1.0, 9)
+    v = v.copy()
+    v[:, 2] += 0.037
+    ctx, op = make(v, t)
+    n, L, _ = g.aim_grid_info(ctx)
+    assert n == list(op.n) and n[2] == 3
+    x = random_complex((1, ctx.N), 55)
+    y = g.aim_matvec(ctx, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, op.matvec(x)) <= 1e-12
