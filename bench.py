@@ -637,7 +637,8 @@ def run_ours(args, rank, world, local_rank):
     pptr = g.aim_export(ctx, g.AIM_EXPORT_PROJ_PTR)
     nent = int(pptr[-1])
     touched = int(np.count_nonzero(np.diff(pptr)))
-    models = kernel_models(N, n, L, nnz, nent, 27, nrhs, e, touched)
+    S = 9 if L[2] == 1 else 27  # stencil nodes (M = 2; a planar grid keeps one plane)
+    models = kernel_models(N, n, L, nnz, nent, S, nrhs, e, touched)
     kernels = {k: {"launches": c, "avg_ms": ms / max(c, 1), "share": ms / max(sum(v[1] for v in prof.values()), 1e-30)}
                for k, (c, ms) in prof.items()}
     dom = max(kernels, key=lambda k: kernels[k]["share"])

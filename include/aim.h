@@ -79,7 +79,7 @@ typedef struct {
   int maxit;       /* total inner iteration cap per solve (default 3000) */
   int check_every; /* host reads the residual estimate every k iterations (default 5) */
   int max_rhs;     /* largest nrhs the context is sized for (default 1, <= 256) */
-  int verbose;     /* 0: silent (default) */
+  int verbose;     /* 0: silent (default); 1: aim_setup prints the wall time of its phases to stderr */
   void* stream;    /* cudaStream_t; NULL = the legacy default stream */
   int planar;      /* 1 (default): when every basis function's weights vanish off one z plane of
                       the grid (a planar scatterer at constant z on a node plane), keep only that
@@ -152,9 +152,12 @@ int aim_matvec_host(aim_ctx* ctx, const void* x_host, void* y_host, int nrhs, in
 /*
  * Solve Z~ X = V for nrhs right-hand sides (paper Section 2.2: diagonal
  * preconditioner, stop on the relative residual).  Right-preconditioned
- * restarted GMRES(m), M^-1 = diag(Z~)^-1, classical Gram-Schmidt with one
- * re-orthogonalisation, FP64 dot products and Givens rotations on the
- * device.  The Arnoldi products use opts.precision; every restart computes
+ * restarted GMRES(m), M^-1 = diag(Z~)^-1.  On the device: the products,
+ * classical Gram-Schmidt with FP64 dot products and a second pass where the
+ * Daniel-Gragg-Kaufman-Stewart test asks for it, one Arnoldi step replayed
+ * from a CUDA graph.  On the host, every opts.check_every steps: Givens
+ * rotations of the new Hessenberg columns in FP64 and the residual estimate.
+ * The Arnoldi products use opts.precision; every restart computes
  * the true residual with an FP64-accurate product (AIM_C128, or AIM_C128_F64
  * when that is opts.precision), so AIM_C64 is FP64 iterative refinement
  * around a complex64 inner solve.  Stops when every right-hand

@@ -92,7 +92,7 @@ def aim_default_opts():
 
 
 def aim_setup(verts, tris, k, h, M=2, near_radius=None, precision=AIM_C128, restart=50, maxit=3000,
-              check_every=5, max_rhs=1, stream=None, planar=True):
+              check_every=5, max_rhs=1, stream=None, planar=True, verbose=False):
     """Build a context (host FP64 setup + device spectrum); see aim_setup in aim.h."""
     lib = load()
     mesh, keep = _mesh(verts, tris)
@@ -104,6 +104,7 @@ def aim_setup(verts, tris, k, h, M=2, near_radius=None, precision=AIM_C128, rest
     o.max_rhs = max_rhs
     o.stream = _stream(stream)
     o.planar = 1 if planar else 0
+    o.verbose = 1 if verbose else 0
     h_ = C.c_void_p()
     r = 3.0 * h if near_radius is None else float(near_radius)
     check(lib.aim_setup(C.byref(mesh), float(k), float(h), int(M), r, C.byref(o), C.byref(h_)), "aim_setup")

@@ -285,6 +285,64 @@ __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R
   }
 }
 
+// Projection for many right-hand sides: one warp per grid node, lanes over
+// right-hand sides (RL consecutive ones per lane) on the RHS-minor x, so each
+// entry's x values are one contiguous run; the entry's four weights are
+// warp-uniform.  A block's 32 nodes are staged in shared memory (node-major,
+// rows padded by one element against bank conflicts) and written back in the
+// [B][4][Nc] layout, 32 consecutive nodes per (RHS, component) row.  One
+// launch covers B right-hand sides of an x with ldx of them per row.
+template <class MD, int RL>
+__global__ void __launch_bounds__(256) proj_gather_rhs(const cplx<typename MD::R>* __restrict__ xT,
+                                                       typename MD::S* __restrict__ Q, const int32_t* __restrict__ ptr,
+                                                       const int32_t* __restrict__ mm,
+                                                       const typename MD::R* __restrict__ w, long long Nc, int B,
+                                                       int ldx) {
+  using R = typename MD::R;
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* qs = reinterpret_cast<C*>(smem_raw);  // [32][4 B + 1]
+  const int NS = 4 * B + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long u0 = blockIdx.x * 32LL;
+  for (int i = warp; i < 32; i += 8) {
+    const long long u = u0 + i;
+    if (u >= Nc) break;
+    const int e0 = ptr[u], e1 = ptr[u + 1];
+    for (int bc = 0; bc < B; bc += 32 * RL) {
+      const int b = bc + RL * lane;  // B is a multiple of RL
+      if (b >= B) continue;
+      C a[4][RL];
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) a[cc][q] = cmake<C>(0, 0);
+      for (int e = e0; e < e1; ++e) {
+        const W4<R> ww = load_w4(w, e);
+        const Run<C, RL> xv = load_run<C, RL>(xT + (long long)mm[e] * ldx + b);
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+          a[0][q].x += ww.x * xv.v[q].x; a[0][q].y += ww.x * xv.v[q].y;
+          a[1][q].x += ww.y * xv.v[q].x; a[1][q].y += ww.y * xv.v[q].y;
+          a[2][q].x += ww.z * xv.v[q].x; a[2][q].y += ww.z * xv.v[q].y;
+          a[3][q].x += ww.w * xv.v[q].x; a[3][q].y += ww.w * xv.v[q].y;
+        }
+      }
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) qs[i * NS + cc * B + b + q] = a[cc][q];
+    }
+  }
+  __syncthreads();
+  const int nodes = (int)min(32LL, Nc - u0);
+  for (int t = threadIdx.x; t < 32 * 4 * B; t += blockDim.x) {
+    const int i = t & 31, row = t >> 5;  // row = b * 4 + component
+    const int b = row >> 2, cc = row & 3;
+    if (i < nodes) Q[((long long)b * 4 + cc) * Nc + u0 + i] = MD::put(qs[i * NS + cc * B + b]);
+  }
+}
+
 // Right-hand sides from which the interpolation runs with lanes over them.
 constexpr int kRhsLanesMin = 16;
 
@@ -498,26 +556,52 @@ static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename 
                        const typename MD::R* lam, const cplx<typename MD::R>* nval, int (*convolve)(aim_ctx*, int)) {
   using R = typename MD::R;
   const long long Nc = (long long)c->n[0] * c->n[1] * c->n[2];
-  {
+  const bool many = nrhs >= kRhsLanesMin;
+  // two right-hand sides per lane once a warp has 64 to cover
+  const bool two = nrhs >= 64 && nrhs % 2 == 0;
+  PrecData<R>& pd = prec_data<R>(c);
+  if (many) {
+    if (!pd.phiT) {
+      AIM_CUDA_TRY(cudaMalloc(&pd.phiT, sizeof(cplx<R>) * c->max_rhs * 4 * Nc));
+      AIM_CUDA_TRY(cudaMalloc(&pd.xT, sizeof(cplx<R>) * c->max_rhs * c->N));
+    }
+    AIM_TRY(transpose(c, "transpose_x", x, pd.xT, nrhs, (long long)c->N));
+    // right-hand sides per launch: up to 64, shared memory 32 (4 B + 1) elements
+    const int chunk = std::min(nrhs, 64);
+    const size_t sm = sizeof(cplx<R>) * 32 * (4 * chunk + 1);
+    const int blocks = (int)((Nc + 31) / 32);
+    static const cudaError_t attr1 = cudaFuncSetAttribute(proj_gather_rhs<MD, 1>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    static const cudaError_t attr2 = cudaFuncSetAttribute(proj_gather_rhs<MD, 2>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    AIM_CUDA_TRY(attr1);
+    AIM_CUDA_TRY(attr2);
+    for (int b0 = 0; b0 < nrhs; b0 += chunk) {
+      const int nb = std::min(chunk, nrhs - b0);
+      const cplx<R>* xs = pd.xT + b0;
+      typename MD::S* qd = grid0 + (long long)b0 * 4 * Nc;
+      if (nb == 64 && nrhs % 2 == 0)  // two per lane: 16-byte loads need an even row stride
+        AIM_LAUNCH(c, "proj_gather", (proj_gather_rhs<MD, 2><<<blocks, 256, sm, c->stream>>>(xs, qd, c->pnode_ptr,
+                                                                                            c->pnode_m, pw, Nc, nb,
+                                                                                            nrhs)));
+      else
+        AIM_LAUNCH(c, "proj_gather", (proj_gather_rhs<MD, 1><<<blocks, 256, sm, c->stream>>>(xs, qd, c->pnode_ptr,
+                                                                                            c->pnode_m, pw, Nc, nb,
+                                                                                            nrhs)));
+      AIM_TRY(launch_check(c, "proj_gather"));
+    }
+  } else {
     const int blocks = (int)std::min<long long>((4 * Nc + 255) / 256, 152LL * 16);
     AIM_LAUNCH(c, "proj_gather",
                proj_gather<MD><<<blocks, 256, 0, c->stream>>>(x, grid0, c->pnode_ptr, c->pnode_m, pw, c->N, Nc, nrhs));
     AIM_TRY(launch_check(c, "proj_gather"));
   }
   AIM_TRY(convolve(c, 4 * nrhs));
-  if (nrhs >= kRhsLanesMin) {
-    PrecData<R>& pd = prec_data<R>(c);
-    if (!pd.phiT) {
-      AIM_CUDA_TRY(cudaMalloc(&pd.phiT, sizeof(cplx<R>) * c->max_rhs * 4 * Nc));
-      AIM_CUDA_TRY(cudaMalloc(&pd.xT, sizeof(cplx<R>) * c->max_rhs * c->N));
-    }
+  if (many) {
     AIM_TRY(transpose(c, "transpose_phi", reinterpret_cast<const cplx<R>*>(phi), pd.phiT, nrhs, 4 * Nc));
-    AIM_TRY(transpose(c, "transpose_x", x, pd.xT, nrhs, (long long)c->N));
     const int blocks = (c->N + 7) / 8;
     const size_t sm = sizeof(cplx<R>) * 8 * nrhs;
     const R fvec = (R)(c->k * kEta0), frho = (R)(kEta0 / c->k);
-    // two right-hand sides per lane once a warp has 64 to cover
-    const bool two = nrhs >= 64 && nrhs % 2 == 0;
 #define AIM_INTERP_RHS(MM, RL)                                                                                   \
   AIM_LAUNCH(c, "interp_near",                                                                                   \
              (interp_near_rhs<MI, MM, RL><<<blocks, 256, sm, c->stream>>>(pd.phiT, pd.xT, y, lam, c->base,        \

@@ -17,6 +17,7 @@
 //   6. node-ordered projection lists (the transpose of the weights).
 // Device: uploads, twiddles and the Green's function spectrum (fft.cu).
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -227,9 +228,24 @@ template <typename T> static int up(T** dst, const std::vector<T>& v) {
   return upload(reinterpret_cast<void**>(dst), v.data(), v.size() * sizeof(T));
 }
 
+// Wall time of the setup phases, printed to stderr when opts.verbose is set.
+struct PhaseClock {
+  bool on;
+  std::chrono::steady_clock::time_point t0;
+  explicit PhaseClock(bool v) : on(v), t0(std::chrono::steady_clock::now()) {}
+  void mark(const char* what) {
+    if (!on) return;
+    const auto t = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "aim_setup: %-28s %8.3f s\n", what, std::chrono::duration<double>(t - t0).count());
+    t0 = t;
+  }
+};
+
 int build_context(aim_ctx* c, const aim_mesh* mesh) {
+  PhaseClock clk(c->opts.verbose != 0);
   Topo T;
   AIM_TRY(build_topology(mesh, T));
+  clk.mark("topology");
   const int N = T.N, M = c->M, P = M + 1, S = P * P * P;
   c->N = N;
   c->S = S;
@@ -306,8 +322,10 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
     }
   });
 
+  clk.mark("moment weights");
   // ---- near list
   near_list(T, c->radius, c->h_near_ptr, c->h_near_col);
+  clk.mark("near list");
   const int64_t nnz = c->h_near_ptr[N];
   c->nnz = nnz;
 
@@ -373,6 +391,7 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
     }
   }, 4);
 
+  clk.mark("near MoM entries");
   // ---- symmetrise, subtract the grid approximation
   int dmax = 0;
   for (int m = 0; m < N; ++m)
@@ -475,6 +494,7 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
     }
   });
 
+  clk.mark("near grid approximation");
   // ---- plane collapse: every weight off one z plane of the grid is zero
   // (a planar scatterer at constant z on a node plane).  Q and Phi vanish off
   // that plane, so the grid keeps only it and the convolution becomes 2-D with
@@ -552,6 +572,7 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
         }
   }
 
+  clk.mark("projection lists");
   // ---- uploads
   std::vector<float> lam32(c->h_lam.size());
   for (size_t i = 0; i < lam32.size(); ++i) lam32[i] = (float)c->h_lam[i];
@@ -629,10 +650,12 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
   AIM_TRY(upload((void**)&c->p64.ghat, nullptr, oct * sizeof(double2)));
   AIM_TRY(upload((void**)&c->p32.ghat, nullptr, oct * sizeof(float2)));
   AIM_TRY(upload((void**)&c->pff.ghat, nullptr, oct * sizeof(float4)));
+  clk.mark("uploads");
   AIM_TRY(build_ghat(c));
   c->h_ghat.resize(2 * oct);
   AIM_CUDA_TRY(cudaMemcpyAsync(c->h_ghat.data(), c->p64.ghat, oct * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
   AIM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  clk.mark("Green's function spectrum");
   return AIM_OK;
 }
 

@@ -147,7 +147,7 @@ def test_other_stencil_orders(M):
 
 
 @pytest.mark.parametrize("planar", [True, False])
-@pytest.mark.parametrize("nrhs", [8, 9, 17, 70])
+@pytest.mark.parametrize("nrhs", [8, 9, 17, 65, 70])
 def test_many_rhs_products(nrhs, planar):
     """Batches of 8 to 70 right-hand sides (lanes, tiles and grid chunks cover every RHS),
     on the plate's collapsed and full grids."""
