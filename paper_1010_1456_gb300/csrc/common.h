@@ -249,6 +249,28 @@ int matvec_c64_bufs(aim_ctx* c, const float2* x, float2* y, int nrhs, float2* g0
 int build_ghat(aim_ctx* c);
 // krylov.cu
 int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_solve_info* info);
+
+// Host arrays for the device near-zone fill (nearfill.cu): geometry, the
+// triangle pairs (CSR by test triangle, sorted by source triangle; ids lists
+// the nsing singular pairs first), the near list, anchors, FP64 weights on
+// the full (M+1)^3 stencil and G_h on offsets [-TE, TE]^3.
+struct TriRule;
+struct NearFillArgs {
+  int N = 0, nv = 0, nt = 0, P = 3, S = 27, TE = 0;
+  int64_t nnz = 0, npairs = 0, nsing = 0, ntab = 0;
+  const double* vert = nullptr;
+  const int32_t* tri = nullptr;
+  const double* area = nullptr;
+  const int32_t *tp = nullptr, *tm = nullptr, *sp = nullptr, *sm = nullptr;
+  const double* len = nullptr;
+  const int32_t *tptr = nullptr, *pP = nullptr, *pQ = nullptr, *ids = nullptr;
+  const int32_t *erow = nullptr, *ecol = nullptr, *nptr = nullptr, *anchor = nullptr;
+  const double* lam = nullptr;
+  const double2* gtab = nullptr;
+  const TriRule *rule_test = nullptr, *rule_test_sing = nullptr, *rule_src = nullptr;
+};
+// Writes the near values [nnz] (c128) and the MoM diagonal [N] (c128).
+int near_fill_device(aim_ctx* c, const NearFillArgs& a, double* val_out, double* diag_out);
 int alloc_krylov(aim_ctx* c);
 // Allocates everything a product of this precision allocates lazily, so a
 // product can be captured into a CUDA graph.

@@ -166,8 +166,8 @@ AIM_HD inline Cd green_smooth(double k, double R) {
 //   T_ab = sum_i W_i [ (r_i - P_a).V_b(r_i) / (4 A_P A_Q) - S0(r_i) / (k^2 A_P A_Q) ]
 //   S0(r) = int_Q G dS',  V_b(r) = int_Q (r' - Q_b) G dS'
 // so that Z_mn += j k eta s_m s_n l_m l_n T[a(m)][b(n)].
-inline void pair_block(const V3 P[3], const V3 Q[3], double AP, double AQ, bool singular, double k,
-                       const TriRule& test, const TriRule& src, Cd T[3][3]) {
+AIM_HD inline void pair_block(const V3 P[3], const V3 Q[3], double AP, double AQ, bool singular, double k,
+                              const TriRule& test, const TriRule& src, Cd T[3][3]) {
   Cd acc[3][3];
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) acc[a][b] = cd(0, 0);

@@ -1,0 +1,250 @@
+// Near-zone fill on the device (paper Section 2.2: near-zone correction with
+// gamma = 3; Section 2.4: the near-field matrix is filled in O(N) time).
+//
+//   1. EFIE triangle-pair blocks T[a][b] for every (test triangle, source
+//      triangle) pair that some near RWG pair touches (geom.h pair_block:
+//      collapsed Gauss-Legendre rules, singular extraction for pairs that
+//      share a vertex), one thread per pair;
+//   2. each near entry's two test halves, Z_mn = j k eta l_m l_n
+//      sum s_m s_n T[a(m)][b(n)], one thread per (entry, half);
+//   3. symmetrisation (Z_mn + Z_nm) / 2 and the subtraction of the pair's
+//      grid approximation j k eta [sum_xyz L_m G_h L_n - k^-2 L^rho_m G_h L^rho_n],
+//      one warp per entry (lanes over the test stencil nodes).
+// Every value is FP64.  The host builds the pair lists; the results come
+// back to the host arrays the rest of setup reads.
+#include <algorithm>
+
+#include "common.h"
+#include "geom.h"
+
+namespace aim {
+
+// The three rules (test, test near a singularity, source) as raw bytes:
+// TriRule has a default member initializer, which __constant__ storage does
+// not allow.
+__constant__ double c_rules[3 * (sizeof(TriRule) / sizeof(double) + 1)];
+constexpr size_t kRuleStride = (sizeof(TriRule) / sizeof(double) + 1) * sizeof(double);
+__device__ __forceinline__ const TriRule& rule(int i) {
+  return *reinterpret_cast<const TriRule*>(reinterpret_cast<const char*>(c_rules) + i * kRuleStride);
+}
+
+struct FillGeom {
+  const double* vert;     // [nv][3]
+  const int32_t* tri;     // [nt][3]
+  const double* area;     // [nt]
+  const int32_t* tp;      // [N] "+" triangle
+  const int32_t* tm;      // [N] "-" triangle
+  const int32_t* sp;      // [N] slot of the free vertex in the "+" triangle
+  const int32_t* sm;      // [N] slot in the "-" triangle
+  const double* len;      // [N] edge length
+};
+
+__device__ __forceinline__ V3 vtx(const FillGeom& g, int t, int s) {
+  const double* p = g.vert + 3 * (size_t)g.tri[3 * (size_t)t + s];
+  return v3(p[0], p[1], p[2]);
+}
+
+// Triangle-pair blocks: pair i = (pP[i], pQ[i]); out[i][a][b].
+template <bool SING>
+__global__ void __launch_bounds__(128) k_pair_blocks(FillGeom g, const int32_t* __restrict__ ids,
+                                                     const int32_t* __restrict__ pP, const int32_t* __restrict__ pQ,
+                                                     int n, double k, Cd* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int i = ids[t];
+  const int P = pP[i], Q = pQ[i];
+  const V3 Pv[3] = {vtx(g, P, 0), vtx(g, P, 1), vtx(g, P, 2)};
+  const V3 Qv[3] = {vtx(g, Q, 0), vtx(g, Q, 1), vtx(g, Q, 2)};
+  Cd T[3][3];
+  pair_block(Pv, Qv, g.area[P], g.area[Q], SING, k, rule(SING ? 1 : 0), rule(2), T);
+  Cd* o = out + (size_t)i * 9;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) o[a * 3 + b] = T[a][b];
+}
+
+// Index of triangle Q in the sorted pair list of test triangle P.
+__device__ __forceinline__ int64_t pair_of(const int32_t* tptr, const int32_t* pQ, int P, int Q) {
+  int64_t lo = tptr[P], hi = tptr[P + 1];
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (pQ[mid] < Q) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// zhalf[half][e] = j k eta l_m l_n sum over n's two triangles of s_m s_n T[a][b]
+__global__ void k_near_halves(FillGeom g, const int32_t* __restrict__ erow, const int32_t* __restrict__ ecol,
+                              const int32_t* __restrict__ tptr, const int32_t* __restrict__ pQ,
+                              const Cd* __restrict__ blk, int64_t nnz, double jke, double2* __restrict__ zhalf) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 2 * nnz; t += (int64_t)gridDim.x * blockDim.x) {
+    const int half = (int)(t / nnz);
+    const int64_t e = t - half * nnz;
+    const int m = erow[e], n = ecol[e];
+    const int P = half ? g.tm[m] : g.tp[m];
+    const int a = half ? g.sm[m] : g.sp[m];
+    const double sm_ = half ? -1.0 : 1.0;
+    double re = 0.0, im = 0.0;
+    for (int th = 0; th < 2; ++th) {
+      const int Qt = th ? g.tm[n] : g.tp[n];
+      const int b = th ? g.sm[n] : g.sp[n];
+      const double sn_ = th ? -1.0 : 1.0;
+      const Cd v = blk[(size_t)pair_of(tptr, pQ, P, Qt) * 9 + a * 3 + b];
+      re += sm_ * sn_ * v.re;
+      im += sm_ * sn_ * v.im;
+    }
+    const double f = jke * g.len[m] * g.len[n];
+    zhalf[half * nnz + e] = make_double2(-f * im, f * re);
+  }
+}
+
+// Symmetrised entry minus the grid approximation; one warp per entry, lane s
+// over the test stencil nodes.  gtab: G_h on offsets [-TE, TE]^3.
+__global__ void __launch_bounds__(256) k_near_values(const int32_t* __restrict__ erow, const int32_t* __restrict__ ecol,
+                                                     const int32_t* __restrict__ nptr, const double2* __restrict__ zhalf,
+                                                     const double* __restrict__ lam, const int32_t* __restrict__ anchor,
+                                                     const double2* __restrict__ gtab, int TE, int P, int64_t nnz,
+                                                     double k, double jke, double2* __restrict__ val,
+                                                     double2* __restrict__ diag) {
+  const int lane = threadIdx.x & 31;
+  const int S = P * P * P, TW = 2 * TE + 1;
+  for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < nnz;
+       e += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int m = erow[e], n = ecol[e];
+    // transposed entry (n, m) in row n
+    int64_t lo = nptr[n], hi = nptr[n + 1];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (ecol[mid] < m) lo = mid + 1;
+      else hi = mid;
+    }
+    const int64_t et = lo;
+    const double2 a0 = zhalf[e], a1 = zhalf[nnz + e], b0 = zhalf[et], b1 = zhalf[nnz + et];
+    const double zr = 0.5 * ((a0.x + a1.x) + (b0.x + b1.x));
+    const double zi = 0.5 * ((a0.y + a1.y) + (b0.y + b1.y));
+    const int dx = anchor[3 * (size_t)m] - anchor[3 * (size_t)n];
+    const int dy = anchor[3 * (size_t)m + 1] - anchor[3 * (size_t)n + 1];
+    const int dz = anchor[3 * (size_t)m + 2] - anchor[3 * (size_t)n + 2];
+    const double* lm = lam + (size_t)m * 4 * S;
+    const double* ln = lam + (size_t)n * 4 * S;
+    double sr = 0.0, si = 0.0;  // sum over c of +-(lm^T G ln), vector minus k^-2 charge
+    for (int s = lane; s < S; s += 32) {
+      const int si_ = s % P, sj = (s / P) % P, sk = s / (P * P);
+      double ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
+      for (int t = 0; t < S; ++t) {
+        const int ti = t % P, tj = (t / P) % P, tk = t / (P * P);
+        const double2 gv = gtab[((size_t)(dz + sk - tk + TE) * TW + (dy + sj - tj + TE)) * TW + (dx + si_ - ti + TE)];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const double l = ln[c * S + t];
+          ar[c] += gv.x * l;
+          ai[c] += gv.y * l;
+        }
+      }
+      const double kinv2 = 1.0 / (k * k);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const double f = (c < 3 ? 1.0 : -kinv2) * lm[c * S + s];
+        sr += f * ar[c];
+        si += f * ai[c];
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) {
+      // j k eta (sr + j si) = k eta (-si + j sr)
+      val[e] = make_double2(zr + jke * si, zi - jke * sr);
+      if (m == n) diag[m] = make_double2(zr, zi);
+    }
+  }
+}
+
+// Device part of the near fill; arguments are host arrays (see setup.cu).
+int near_fill_device(aim_ctx* c, const NearFillArgs& A, double* val_out, double* diag_out) {
+  const int64_t nnz = A.nnz, npairs = A.npairs;
+  const size_t N = (size_t)A.N;
+  std::vector<void*> bufs;
+  auto dev = [&](void** p, const void* src, size_t bytes) -> int {
+    AIM_CUDA_TRY(cudaMalloc(p, std::max<size_t>(bytes, 16)));
+    bufs.push_back(*p);
+    if (src && bytes) AIM_CUDA_TRY(cudaMemcpyAsync(*p, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    return AIM_OK;
+  };
+  int rc = AIM_OK;
+  do {
+    FillGeom g{};
+    double *vert = nullptr, *area = nullptr, *len = nullptr, *lam = nullptr;
+    int32_t *tri = nullptr, *tp = nullptr, *tm = nullptr, *sp = nullptr, *sm = nullptr;
+    int32_t *tptr = nullptr, *pP = nullptr, *pQ = nullptr, *ids = nullptr, *erow = nullptr, *ecol = nullptr,
+            *nptr = nullptr, *anc = nullptr;
+    double2 *gtab = nullptr, *zhalf = nullptr, *val = nullptr, *diag = nullptr;
+    Cd* blk = nullptr;
+    if ((rc = dev((void**)&vert, A.vert, sizeof(double) * 3 * A.nv)) ||
+        (rc = dev((void**)&tri, A.tri, sizeof(int32_t) * 3 * A.nt)) ||
+        (rc = dev((void**)&area, A.area, sizeof(double) * A.nt)) ||
+        (rc = dev((void**)&tp, A.tp, sizeof(int32_t) * N)) || (rc = dev((void**)&tm, A.tm, sizeof(int32_t) * N)) ||
+        (rc = dev((void**)&sp, A.sp, sizeof(int32_t) * N)) || (rc = dev((void**)&sm, A.sm, sizeof(int32_t) * N)) ||
+        (rc = dev((void**)&len, A.len, sizeof(double) * N)) ||
+        (rc = dev((void**)&tptr, A.tptr, sizeof(int32_t) * (A.nt + 1))) ||
+        (rc = dev((void**)&pP, A.pP, sizeof(int32_t) * npairs)) ||
+        (rc = dev((void**)&pQ, A.pQ, sizeof(int32_t) * npairs)) ||
+        (rc = dev((void**)&ids, A.ids, sizeof(int32_t) * npairs)) ||
+        (rc = dev((void**)&erow, A.erow, sizeof(int32_t) * nnz)) ||
+        (rc = dev((void**)&ecol, A.ecol, sizeof(int32_t) * nnz)) ||
+        (rc = dev((void**)&nptr, A.nptr, sizeof(int32_t) * (N + 1))) ||
+        (rc = dev((void**)&anc, A.anchor, sizeof(int32_t) * 3 * N)) ||
+        (rc = dev((void**)&lam, A.lam, sizeof(double) * N * 4 * A.S)) ||
+        (rc = dev((void**)&gtab, A.gtab, sizeof(double2) * A.ntab)) ||
+        (rc = dev((void**)&blk, nullptr, sizeof(Cd) * 9 * npairs)) ||
+        (rc = dev((void**)&zhalf, nullptr, sizeof(double2) * 2 * nnz)) ||
+        (rc = dev((void**)&val, nullptr, sizeof(double2) * nnz)) || (rc = dev((void**)&diag, nullptr, sizeof(double2) * N)))
+      break;
+    if ((rc = [&]() -> int {
+           const TriRule* rs[3] = {A.rule_test, A.rule_test_sing, A.rule_src};
+           for (int i = 0; i < 3; ++i)
+             AIM_CUDA_TRY(cudaMemcpyToSymbolAsync(c_rules, rs[i], sizeof(TriRule), i * kRuleStride,
+                                                  cudaMemcpyHostToDevice, c->stream));
+           AIM_CUDA_TRY(cudaMemsetAsync(diag, 0, sizeof(double2) * N, c->stream));
+           return AIM_OK;
+         }()))
+      break;
+    g.vert = vert; g.tri = tri; g.area = area; g.tp = tp; g.tm = tm; g.sp = sp; g.sm = sm; g.len = len;
+    // ids: the nsing singular pairs first, then the regular ones
+    const int64_t nreg = npairs - A.nsing;
+    if (A.nsing > 0) {
+      AIM_LAUNCH(c, "near_pair_blocks", (k_pair_blocks<true><<<(unsigned)((A.nsing + 127) / 128), 128, 0, c->stream>>>(
+                                            g, ids, pP, pQ, (int)A.nsing, c->k, blk)));
+      if ((rc = launch_check(c, "near_pair_blocks"))) break;
+    }
+    if (nreg > 0) {
+      AIM_LAUNCH(c, "near_pair_blocks", (k_pair_blocks<false><<<(unsigned)((nreg + 127) / 128), 128, 0, c->stream>>>(
+                                            g, ids + A.nsing, pP, pQ, (int)nreg, c->k, blk)));
+      if ((rc = launch_check(c, "near_pair_blocks"))) break;
+    }
+    const double jke = c->k * kEta0;
+    AIM_LAUNCH(c, "near_halves", (k_near_halves<<<152 * 16, 256, 0, c->stream>>>(g, erow, ecol, tptr, pQ, blk, nnz,
+                                                                                   jke, zhalf)));
+    if ((rc = launch_check(c, "near_halves"))) break;
+    AIM_LAUNCH(c, "near_values", (k_near_values<<<152 * 16, 256, 0, c->stream>>>(erow, ecol, nptr, zhalf, lam, anc, gtab,
+                                                                                   A.TE, A.P, nnz, c->k, jke, val,
+                                                                                   diag)));
+    if ((rc = launch_check(c, "near_values"))) break;
+    if ((rc = [&]() -> int {
+           AIM_CUDA_TRY(cudaMemcpyAsync(val_out, val, sizeof(double2) * nnz, cudaMemcpyDeviceToHost, c->stream));
+           AIM_CUDA_TRY(cudaMemcpyAsync(diag_out, diag, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
+           AIM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+           return AIM_OK;
+         }()))
+      break;
+  } while (false);
+  cudaStreamSynchronize(c->stream);
+  for (void* p : bufs) cudaFree(p);
+  return rc;
+}
+
+}  // namespace aim

@@ -329,70 +329,62 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
   const int64_t nnz = c->h_near_ptr[N];
   c->nnz = nnz;
 
-  // ---- near entries: triangle-pair blocks per test triangle
+  // ---- near entries on the device: triangle pairs touched by a near RWG pair
   const TriRule rt = make_tri_rule(3), rts = make_tri_rule(5), rs = make_tri_rule(4);
-  std::vector<double> zhalf(4 * (size_t)nnz, 0.0);  // [2 halves][nnz][re, im]
-  const double jke = k * kEta0;
-  parallel_for(T.nt, [&](int64_t Pi) {
-    const int Pt = (int)Pi;
-    int ms[3], as[3], nm = 0;
-    for (int a = 0; a < 3; ++a) {
-      int m = T.tri_rwg[3 * (size_t)Pt + a];
-      if (m >= 0) {
-        ms[nm] = m;
-        as[nm] = a;
-        ++nm;
-      }
-    }
-    if (nm == 0) return;
-    std::vector<int32_t> Qs;
-    for (int i = 0; i < nm; ++i)
-      for (int32_t e = c->h_near_ptr[ms[i]]; e < c->h_near_ptr[ms[i] + 1]; ++e) {
-        int n = c->h_near_col[e];
-        Qs.push_back(T.tp[n]);
-        Qs.push_back(T.tm[n]);
-      }
-    std::sort(Qs.begin(), Qs.end());
-    Qs.erase(std::unique(Qs.begin(), Qs.end()), Qs.end());
-    std::vector<Cd> blk(Qs.size() * 9);
-    const V3 Pv[3] = {T.vert[T.tri[3 * Pt]], T.vert[T.tri[3 * Pt + 1]], T.vert[T.tri[3 * Pt + 2]]};
-    for (size_t qi = 0; qi < Qs.size(); ++qi) {
-      const int Qt = Qs[qi];
-      const V3 Qv[3] = {T.vert[T.tri[3 * Qt]], T.vert[T.tri[3 * Qt + 1]], T.vert[T.tri[3 * Qt + 2]]};
-      bool sing = false;
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) sing |= (T.tri[3 * Pt + a] == T.tri[3 * Qt + b]);
-      Cd Tb[3][3];
-      pair_block(Pv, Qv, T.area[Pt], T.area[Qt], sing, k, sing ? rts : rt, rs, Tb);
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) blk[qi * 9 + a * 3 + b] = Tb[a][b];
-    }
-    auto find = [&](int Qt) { return (size_t)(std::lower_bound(Qs.begin(), Qs.end(), Qt) - Qs.begin()); };
-    for (int i = 0; i < nm; ++i) {
-      const int m = ms[i], a = as[i];
-      const int half = (T.tp[m] == Pt) ? 0 : 1;
-      const double sm_ = half ? -1.0 : 1.0;
-      for (int32_t e = c->h_near_ptr[m]; e < c->h_near_ptr[m + 1]; ++e) {
-        const int n = c->h_near_col[e];
-        double re = 0.0, im = 0.0;
-        for (int th = 0; th < 2; ++th) {
-          const int Qt = th ? T.tm[n] : T.tp[n];
-          const int b = th ? T.sm[n] : T.sp[n];
-          const double sn_ = th ? -1.0 : 1.0;
-          const Cd v = blk[find(Qt) * 9 + a * 3 + b];
-          re += sm_ * sn_ * v.re;
-          im += sm_ * sn_ * v.im;
+  std::vector<int32_t> tptr(T.nt + 1, 0), pQ;
+  {
+    std::vector<std::vector<int32_t>> qs(T.nt);
+    parallel_for(T.nt, [&](int64_t Pi) {
+      const int Pt = (int)Pi;
+      std::vector<int32_t>& Qs = qs[Pt];
+      for (int a = 0; a < 3; ++a) {
+        const int m = T.tri_rwg[3 * (size_t)Pt + a];
+        if (m < 0) continue;
+        for (int32_t e = c->h_near_ptr[m]; e < c->h_near_ptr[m + 1]; ++e) {
+          const int n = c->h_near_col[e];
+          Qs.push_back(T.tp[n]);
+          Qs.push_back(T.tm[n]);
         }
-        // j k eta l_m l_n (re + j im)
-        const double f = jke * T.len[m] * T.len[n];
-        zhalf[(size_t)half * 2 * nnz + 2 * e] = -f * im;
-        zhalf[(size_t)half * 2 * nnz + 2 * e + 1] = f * re;
       }
-    }
-  }, 4);
+      std::sort(Qs.begin(), Qs.end());
+      Qs.erase(std::unique(Qs.begin(), Qs.end()), Qs.end());
+    }, 16);
+    for (int t = 0; t < T.nt; ++t) tptr[t + 1] = tptr[t] + (int32_t)qs[t].size();
+    pQ.resize(tptr[T.nt]);
+    for (int t = 0; t < T.nt; ++t) std::copy(qs[t].begin(), qs[t].end(), pQ.begin() + tptr[t]);
+  }
+  const int64_t npairs = (int64_t)pQ.size();
+  if (npairs >= (1LL << 31)) {
+    set_error("aim_setup: too many near triangle pairs");
+    return AIM_EINVAL;
+  }
+  std::vector<int32_t> pP(npairs), ids(npairs);
+  int64_t nsing = 0;
+  {
+    std::vector<char> sing(npairs, 0);
+    parallel_for(T.nt, [&](int64_t Pi) {
+      const int Pt = (int)Pi;
+      for (int32_t i = tptr[Pt]; i < tptr[Pt + 1]; ++i) {
+        pP[i] = Pt;
+        const int Qt = pQ[i];
+        bool sg = false;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) sg |= (T.tri[3 * (size_t)Pt + a] == T.tri[3 * (size_t)Qt + b]);
+        sing[i] = sg ? 1 : 0;
+      }
+    }, 64);
+    for (int64_t i = 0; i < npairs; ++i)
+      if (sing[i]) ids[nsing++] = (int32_t)i;
+    int64_t r = nsing;
+    for (int64_t i = 0; i < npairs; ++i)
+      if (!sing[i]) ids[r++] = (int32_t)i;
+  }
+  std::vector<int32_t> erow(nnz);
+  for (int m = 0; m < N; ++m)
+    for (int32_t e = c->h_near_ptr[m]; e < c->h_near_ptr[m + 1]; ++e) erow[e] = m;
+  clk.mark("near triangle pairs");
 
-  clk.mark("near MoM entries");
-  // ---- symmetrise, subtract the grid approximation
+  // G_h on the anchor offsets of near pairs plus the stencil extent
   int dmax = 0;
   for (int m = 0; m < N; ++m)
     for (int32_t e = c->h_near_ptr[m]; e < c->h_near_ptr[m + 1]; ++e) {
@@ -401,100 +393,43 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
         dmax = std::max(dmax, std::abs(c->h_anchor[3 * (size_t)m + d] - c->h_anchor[3 * (size_t)n + d]));
     }
   const int TE = dmax + M, TW = 2 * TE + 1;
-  std::vector<double> gtab;  // G_h on offsets [-TE, TE]^3, [re, im]
-  const bool use_tab = (int64_t)TW * TW * TW <= (1LL << 26);
-  auto gh = [&](int ox, int oy, int oz, double* re, double* im) {
-    if ((ox | oy | oz) == 0) {
-      *re = 0.0;
-      *im = 0.0;
-      return;
-    }
-    double r = h * std::sqrt((double)ox * ox + (double)oy * oy + (double)oz * oz);
-    double s = 1.0 / (4.0 * kPi * r);
-    *re = std::cos(k * r) * s;
-    *im = -std::sin(k * r) * s;
-  };
-  if (use_tab) {
-    gtab.resize(2 * (size_t)TW * TW * TW);
-    parallel_for((int64_t)TW * TW * TW, [&](int64_t i) {
-      int ox = (int)(i % TW) - TE, oy = (int)((i / TW) % TW) - TE, oz = (int)(i / ((int64_t)TW * TW)) - TE;
-      gh(ox, oy, oz, &gtab[2 * i], &gtab[2 * i + 1]);
-    });
+  if ((int64_t)TW * TW * TW > (1LL << 26)) {
+    set_error("aim_setup: near radius too large for the grid Green's function table");
+    return AIM_EINVAL;
   }
-  std::vector<int64_t> soff((size_t)S * S);  // table offset of u_s - u_t
-  for (int s = 0; s < S; ++s)
-    for (int t = 0; t < S; ++t) {
-      const int ox = s % P - t % P, oy = (s / P) % P - (t / P) % P, oz = s / (P * P) - t / (P * P);
-      soff[(size_t)s * S + t] = ((int64_t)oz * TW + oy) * TW + ox;
+  std::vector<double2> gtab((size_t)TW * TW * TW);
+  parallel_for((int64_t)TW * TW * TW, [&](int64_t i) {
+    const int ox = (int)(i % TW) - TE, oy = (int)((i / TW) % TW) - TE, oz = (int)(i / ((int64_t)TW * TW)) - TE;
+    double re = 0.0, im = 0.0;
+    if ((ox | oy | oz) != 0) {  // G_h(0) = 0
+      const double r = h * std::sqrt((double)ox * ox + (double)oy * oy + (double)oz * oz);
+      const double sc = 1.0 / (4.0 * kPi * r);
+      re = std::cos(k * r) * sc;
+      im = -std::sin(k * r) * sc;
     }
-  c->h_near_val.assign(2 * (size_t)nnz, 0.0);
-  c->h_diag.assign(2 * (size_t)N, 0.0);
-  parallel_for(N, [&](int64_t mi) {
-    const int m = (int)mi;
-    const double* lm = &c->h_lam[(size_t)m * 4 * S];
-    for (int32_t e = c->h_near_ptr[m]; e < c->h_near_ptr[m + 1]; ++e) {
-      const int n = c->h_near_col[e];
-      // transposed entry (n, m)
-      const int32_t* rb = &c->h_near_col[c->h_near_ptr[n]];
-      const int32_t* re_ = &c->h_near_col[c->h_near_ptr[n + 1]];
-      const int64_t et = c->h_near_ptr[n] + (std::lower_bound(rb, re_, m) - rb);
-      const double zr = 0.5 * ((zhalf[2 * e] + zhalf[2 * nnz + 2 * e]) + (zhalf[2 * et] + zhalf[2 * nnz + 2 * et]));
-      const double zi = 0.5 * ((zhalf[2 * e + 1] + zhalf[2 * nnz + 2 * e + 1]) + (zhalf[2 * et + 1] + zhalf[2 * nnz + 2 * et + 1]));
-      // grid approximation: j k eta [sum_xyz L_m G L_n - k^-2 L^rho_m G L^rho_n]
-      const double* ln = &c->h_lam[(size_t)n * 4 * S];
-      int dd[3];
-      for (int d = 0; d < 3; ++d) dd[d] = c->h_anchor[3 * (size_t)m + d] - c->h_anchor[3 * (size_t)n + d];
-      double acc_re[4] = {0, 0, 0, 0}, acc_im[4] = {0, 0, 0, 0};
-      if (use_tab) {
-        const int64_t tb = ((int64_t)(dd[2] + TE) * TW + (dd[1] + TE)) * TW + (dd[0] + TE);
-        for (int s = 0; s < S; ++s) {
-          double ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
-          const int64_t* os = &soff[(size_t)s * S];
-          for (int t = 0; t < S; ++t) {
-            const double gr = gtab[2 * (tb + os[t])], gi = gtab[2 * (tb + os[t]) + 1];
-            for (int cc = 0; cc < 4; ++cc) {
-              ar[cc] += gr * ln[cc * S + t];
-              ai[cc] += gi * ln[cc * S + t];
-            }
-          }
-          for (int cc = 0; cc < 4; ++cc) {
-            acc_re[cc] += lm[cc * S + s] * ar[cc];
-            acc_im[cc] += lm[cc * S + s] * ai[cc];
-          }
-        }
-      } else {
-        for (int s = 0; s < S; ++s) {
-          const int si = s % P, sj = (s / P) % P, sk = s / (P * P);
-          double ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
-          for (int t = 0; t < S; ++t) {
-            const int ti = t % P, tj = (t / P) % P, tk = t / (P * P);
-            double gr, gi;
-            gh(dd[0] + si - ti, dd[1] + sj - tj, dd[2] + sk - tk, &gr, &gi);
-            for (int cc = 0; cc < 4; ++cc) {
-              ar[cc] += gr * ln[cc * S + t];
-              ai[cc] += gi * ln[cc * S + t];
-            }
-          }
-          for (int cc = 0; cc < 4; ++cc) {
-            acc_re[cc] += lm[cc * S + s] * ar[cc];
-            acc_im[cc] += lm[cc * S + s] * ai[cc];
-          }
-        }
-      }
-      const double sr = acc_re[0] + acc_re[1] + acc_re[2] - acc_re[3] / (k * k);
-      const double si_ = acc_im[0] + acc_im[1] + acc_im[2] - acc_im[3] / (k * k);
-      // j k eta (sr + j si) = k eta (-si + j sr)
-      const double ar_ = -jke * si_, ai_ = jke * sr;
-      c->h_near_val[2 * e] = zr - ar_;
-      c->h_near_val[2 * e + 1] = zi - ai_;
-      if (n == m) {
-        c->h_diag[2 * (size_t)m] = zr;
-        c->h_diag[2 * (size_t)m + 1] = zi;
-      }
-    }
+    gtab[i] = make_double2(re, im);
   });
-
-  clk.mark("near grid approximation");
+  {
+    std::vector<double> vv(3 * (size_t)T.nv);
+    for (int i = 0; i < T.nv; ++i) {
+      vv[3 * i] = T.vert[i].x;
+      vv[3 * i + 1] = T.vert[i].y;
+      vv[3 * i + 2] = T.vert[i].z;
+    }
+    NearFillArgs A;
+    A.N = N; A.nv = T.nv; A.nt = T.nt; A.P = P; A.S = S; A.TE = TE;
+    A.nnz = nnz; A.npairs = npairs; A.nsing = nsing; A.ntab = (int64_t)gtab.size();
+    A.vert = vv.data(); A.tri = T.tri.data(); A.area = T.area.data();
+    A.tp = T.tp.data(); A.tm = T.tm.data(); A.sp = T.sp.data(); A.sm = T.sm.data(); A.len = T.len.data();
+    A.tptr = tptr.data(); A.pP = pP.data(); A.pQ = pQ.data(); A.ids = ids.data();
+    A.erow = erow.data(); A.ecol = c->h_near_col.data(); A.nptr = c->h_near_ptr.data(); A.anchor = c->h_anchor.data();
+    A.lam = c->h_lam.data(); A.gtab = gtab.data();
+    A.rule_test = &rt; A.rule_test_sing = &rts; A.rule_src = &rs;
+    c->h_near_val.assign(2 * (size_t)nnz, 0.0);
+    c->h_diag.assign(2 * (size_t)N, 0.0);
+    AIM_TRY(near_fill_device(c, A, c->h_near_val.data(), c->h_diag.data()));
+  }
+  clk.mark("near entries (device)");
   // ---- plane collapse: every weight off one z plane of the grid is zero
   // (a planar scatterer at constant z on a node plane).  Q and Phi vanish off
   // that plane, so the grid keeps only it and the convolution becomes 2-D with

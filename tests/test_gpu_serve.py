@@ -37,7 +37,9 @@ def requests():
 def test_results_alone_equal_results_in_the_mix():
     reqs = requests()
     s = serve.Server(slots=3)
-    mixed, span = s.run(reqs, realtime=True)
+    # all requests queued at once, so the three slots fill and their work overlaps
+    # (with staggered arrivals these small solves can finish before the next arrives)
+    mixed, span = s.run(reqs, realtime=False)
     summ = serve.summarize(mixed, span)
     assert summ["failed"] == 0, [r.error for r in mixed]
     assert summ["max_rel_res"] <= 1e-6
