@@ -197,6 +197,21 @@ template <class P, bool INV> AIM_HD __forceinline__ void dft5(typename P::T* v) 
 constexpr int first_factor(int n) {
   return (n % 4 == 0) ? 4 : (n % 3 == 0) ? 3 : (n % 5 == 0) ? 5 : (n % 2 == 0) ? 2 : n;
 }
+constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+// A radix R in {4, 3, 5, 2} with N = R M and gcd(R, M) = 1 (a prime-factor
+// split, which needs no twiddle factors), or 0 when N has none.
+constexpr int coprime_factor(int n) {
+  const int rs[4] = {4, 3, 5, 2};
+  for (int i = 0; i < 4; ++i)
+    if (n % rs[i] == 0 && n / rs[i] > 1 && gcd_c(rs[i], n / rs[i]) == 1) return rs[i];
+  return 0;
+}
+// a^-1 mod m for gcd(a, m) = 1
+constexpr int inv_mod(int a, int m) {
+  for (int x = 1; x < m; ++x)
+    if ((a * x) % m == 1) return x;
+  return m == 1 ? 0 : -1;
+}
 
 // x * w_N^E (forward) or x * conj(w_N^E) (inverse), E compile-time
 template <class P, int N, int E, bool INV> AIM_HD __forceinline__ typename P::T twiddle_c(typename P::T x) {
@@ -229,6 +244,26 @@ template <class P, int N, bool INV> struct RegDFT {
       dft4<P, INV>(v);
     } else if constexpr (N == 5) {
       dft5<P, INV>(v);
+    } else if constexpr (coprime_factor(N) != 0) {
+      // Good-Thomas prime-factor split N = R M, gcd(R, M) = 1: input index
+      // n = (M j + R i) mod N, output index k = (M a k1 + R b k2) mod N with
+      // a = M^-1 mod R, b = R^-1 mod M; the two DFT stages need no twiddles.
+      constexpr int R = coprime_factor(N);
+      constexpr int M = N / R;
+      constexpr int A = inv_mod(M % R, R), B = inv_mod(R % M, M);
+      T sub[R][M];
+      static_for<0, R>([&](auto j) {
+        static_for<0, M>([&](auto i) { sub[j][i] = v[(M * decltype(j)::value + R * decltype(i)::value) % N]; });
+        RegDFT<P, M, INV>::run(sub[j]);
+      });
+      static_for<0, M>([&](auto k2) {
+        T t[R];
+        static_for<0, R>([&](auto j) { t[j] = sub[j][k2]; });
+        RegDFT<P, R, INV>::run(t);
+        static_for<0, R>([&](auto k1) {
+          v[(M * A * decltype(k1)::value + R * B * decltype(k2)::value) % N] = t[k1];
+        });
+      });
     } else {
       constexpr int R = first_factor(N);
       constexpr int M = N / R;
