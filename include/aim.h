@@ -105,7 +105,9 @@ void aim_default_opts(aim_opts* opts);
  * and near entries (symmetrised MoM entry minus its grid approximation).
  * Device: grid Green's function spectrum on the zero-padded grid (padded
  * length per axis = smallest 2,3,5-smooth integer >= 2n-1), kept resident.
- *   k > 0, h > 0, M in {1, 2, 3}, near_radius >= 0.  Synchronises.
+ *   k > 0, h > 0, M in {1, ..., 5} (M = 2: 27 nodes; the paper's production
+ *   setting is M = 3, its reference solutions go to M = 5), near_radius >= 0.
+ *   Synchronises.
  * Returns AIM_EINVAL for a non-manifold or degenerate mesh, a mesh without
  * interior edges, or a grid whose padded size exceeds 2^31 points.
  */

@@ -80,15 +80,13 @@ def moment_weights(rwg, h, M, anc):
 
     with g^c = f_x, f_y, f_z, div f.  The moments are integrated with the
     collapsed Gauss-Legendre rule ``n_weight_rule(M)``, exact for this
-    polynomial degree.  The (M+1)^3 x (M+1)^3 Vandermonde system is solved with
-    numpy.linalg.solve.
+    polynomial degree.  The (M+1)^3 x (M+1)^3 system is the Kronecker cube of
+    the 1-D Vandermonde matrix on the nodes 0..M and is solved axis by axis
+    with numpy.linalg.solve.
     """
     off = stencil_offsets(M)  # nodes u (in local units)
     S = len(off)
     xi1, xi2, w = triangle_rule(n_weight_rule(M))
-    V = np.ones((S, S))
-    for qi, q in enumerate(off):  # rows: exponent triples, same ordering
-        V[qi] = (off[:, 0] ** q[0]) * (off[:, 1] ** q[1]) * (off[:, 2] ** q[2])
     mom = np.zeros((S, rwg.N, 4))
     verts, tris = rwg.verts, rwg.tris
     for tri, free, _slot, sgn, area in rwg.halves():
@@ -103,7 +101,18 @@ def moment_weights(rwg, h, M, anc):
         for qi, q in enumerate(off):
             mono = loc[..., 0] ** q[0] * loc[..., 1] ** q[1] * loc[..., 2] ** q[2]
             mom[qi] += np.einsum("mq,mqc->mc", wa * mono, g)
-    lam = np.linalg.solve(V, mom.reshape(S, -1)).reshape(S, rwg.N, 4)
+    # The system matrix V[(p,q,r)][(i,j,k)] = i^p j^q k^r is the Kronecker
+    # product of the 1-D matrix V1[p][i] = i^p with itself (same node and
+    # exponent ordering on each axis), so V Lambda = mom is solved one axis at
+    # a time; the (M+1)^3 system itself is too ill-conditioned in FP64 from
+    # M = 4 on.
+    P = M + 1
+    V1 = np.vander(np.arange(P, dtype=np.float64), increasing=True).T  # V1[p][i] = i^p
+    lam = mom.reshape(P, P, P, -1)  # [exponent z, y, x][basis, component]
+    for axis in range(3):
+        moved = np.moveaxis(lam, axis, 0)
+        lam = np.moveaxis(np.linalg.solve(V1, moved.reshape(P, -1)).reshape(moved.shape), 0, axis)
+    lam = lam.reshape(S, rwg.N, 4)
     return np.ascontiguousarray(lam.transpose(1, 2, 0))
 
 

@@ -107,8 +107,8 @@ int aim_setup(const aim_mesh* mesh, double k, double h, int M, double near_radiu
     return AIM_EINVAL;
   }
   *out = nullptr;
-  if (!(k > 0.0) || !(h > 0.0) || M < 1 || M > 3 || !(near_radius >= 0.0)) {
-    set_error("aim_setup: need k > 0, h > 0, 1 <= M <= 3, near_radius >= 0");
+  if (!(k > 0.0) || !(h > 0.0) || M < 1 || M > 5 || !(near_radius >= 0.0)) {
+    set_error("aim_setup: need k > 0, h > 0, 1 <= M <= 5, near_radius >= 0");
     return AIM_EINVAL;
   }
   aim_opts o;
@@ -256,7 +256,7 @@ int aim_rcs(aim_ctx* ctx, const void* X_dev, int nrhs, int ndir, const double* t
 }
 
 int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int max_rhs, size_t* bytes) {
-  if (!mesh || !bytes || !(h > 0.0) || M < 1 || M > 3 || max_rhs < 1) {
+  if (!mesh || !bytes || !(h > 0.0) || M < 1 || M > 5 || max_rhs < 1) {
     set_error("aim_footprint: bad arguments");
     return AIM_EINVAL;
   }

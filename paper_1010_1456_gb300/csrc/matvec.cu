@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) proj_gather(const cplx<typename MD::R>* _
 }
 
 // 8 lanes per basis function.
-template <class MD, int M>
+template <class MD>
 __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restrict__ Phi,
                                                    const cplx<typename MD::R>* __restrict__ x,
                                                    cplx<typename MD::R>* __restrict__ y,
@@ -113,10 +113,9 @@ __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restr
                                                    const int32_t* __restrict__ ncol,
                                                    const cplx<typename MD::R>* __restrict__ nval, int N, long long Nc,
                                                    int nx, int ny, int nrhs, typename MD::R fvec, typename MD::R frho,
-                                                   int S) {
+                                                   int S, int P) {
   using R = typename MD::R;
   using C = cplx<R>;
-  constexpr int P = M + 1;
   const int lane = threadIdx.x & 7;
   const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
   const bool live = m < N;
@@ -210,7 +209,7 @@ template <class C, int RL> __device__ __forceinline__ Run<C, RL> load_run(const 
 // x value a warp reads is one contiguous run of right-hand sides; the weights
 // and near entries are warp-uniform.  The block's 8 rows of y are staged in
 // shared memory and written back in the [B][N] layout.
-template <class MI, int M, int RL>
+template <class MI, int RL>
 __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R>* __restrict__ PhiT,
                                                        const cplx<typename MI::R>* __restrict__ xT,
                                                        cplx<typename MI::R>* __restrict__ y,
@@ -220,10 +219,9 @@ __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R
                                                        const int32_t* __restrict__ ncol,
                                                        const cplx<typename MI::R>* __restrict__ nval, int N,
                                                        long long Nc, int nx, int ny, int B, typename MI::R fvec,
-                                                       typename MI::R frho, int S) {
+                                                       typename MI::R frho, int S, int P) {
   using R = typename MI::R;
   using C = cplx<R>;
-  constexpr int P = M + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* ys = reinterpret_cast<C*>(smem_raw);  // [8][B]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -430,14 +428,12 @@ __global__ void __launch_bounds__(256) proj_gather_ff(const float4* __restrict__
 }
 
 // Interpolation + near correction: 8 lanes per basis function, as interp_near.
-template <int M>
 __global__ void __launch_bounds__(256) interp_near_ff(const float4* __restrict__ Phi, const float4* __restrict__ x,
                                                       double2* __restrict__ y, const float2* __restrict__ lam,
                                                       const int32_t* __restrict__ base, const int32_t* __restrict__ nptr,
                                                       const int32_t* __restrict__ ncol,
                                                       const float4* __restrict__ nval, int N, long long Nc, int nx,
-                                                      int ny, int nrhs, float2 fvec, float2 frho, int S) {
-  constexpr int P = M + 1;
+                                                      int ny, int nrhs, float2 fvec, float2 frho, int S, int P) {
   const int lane = threadIdx.x & 7;
   const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
   const bool live = m < N;
@@ -529,17 +525,11 @@ static int run_product_ff(aim_ctx* c, const double2* x, double2* y, int nrhs) {
     const double fv = c->k * kEta0, fr = kEta0 / c->k;
     const float fvh = (float)fv, frh = (float)fr;
     const float2 fvec = make_float2(fvh, (float)(fv - (double)fvh)), frho = make_float2(frh, (float)(fr - (double)frh));
-#define AIM_INTERP_FF(MM)                                                                                          \
-  AIM_LAUNCH(c, "interp_near",                                                                                     \
-             (interp_near_ff<MM><<<blocks, 256, 0, c->stream>>>(p.grid0, p.xff, y, p.lam, c->base, c->near_ptr,    \
-                                                                c->near_col, p.near_val, c->N, Nc, c->n[0], c->n[1], \
-                                                                nrhs, fvec, frho, c->S)))
-    switch (c->M) {
-      case 1: AIM_INTERP_FF(1); break;
-      case 2: AIM_INTERP_FF(2); break;
-      default: AIM_INTERP_FF(3); break;
-    }
-#undef AIM_INTERP_FF
+    AIM_LAUNCH(c, "interp_near",
+             (interp_near_ff<<<blocks, 256, 0, c->stream>>>(p.grid0, p.xff, y, p.lam, c->base, c->near_ptr,
+                                                                c->near_col, p.near_val, c->N, Nc, c->n[0], c->n[1],
+                                                                nrhs, fvec, frho, c->S, c->M + 1)));
+
     AIM_TRY(launch_check(c, "interp_near"));
   }
   return AIM_OK;
@@ -602,37 +592,28 @@ static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename 
     const int blocks = (c->N + 7) / 8;
     const size_t sm = sizeof(cplx<R>) * 8 * nrhs;
     const R fvec = (R)(c->k * kEta0), frho = (R)(kEta0 / c->k);
-#define AIM_INTERP_RHS(MM, RL)                                                                                   \
-  AIM_LAUNCH(c, "interp_near",                                                                                   \
-             (interp_near_rhs<MI, MM, RL><<<blocks, 256, sm, c->stream>>>(pd.phiT, pd.xT, y, lam, c->base,        \
-                                                                          c->near_ptr, c->near_col, nval, c->N, Nc, \
-                                                                          c->n[0], c->n[1], nrhs, fvec, frho, c->S)))
-    switch (c->M * 2 + (two ? 1 : 0)) {
-      case 2: AIM_INTERP_RHS(1, 1); break;
-      case 3: AIM_INTERP_RHS(1, 2); break;
-      case 4: AIM_INTERP_RHS(2, 1); break;
-      case 5: AIM_INTERP_RHS(2, 2); break;
-      case 6: AIM_INTERP_RHS(3, 1); break;
-      default: AIM_INTERP_RHS(3, 2); break;
-    }
-#undef AIM_INTERP_RHS
+    if (two)
+      AIM_LAUNCH(c, "interp_near",
+             (interp_near_rhs<MI, 2><<<blocks, 256, sm, c->stream>>>(pd.phiT, pd.xT, y, lam, c->base,
+                                                                          c->near_ptr, c->near_col, nval, c->N, Nc,
+                                                                          c->n[0], c->n[1], nrhs, fvec, frho, c->S, c->M + 1)));
+    else
+      AIM_LAUNCH(c, "interp_near",
+             (interp_near_rhs<MI, 1><<<blocks, 256, sm, c->stream>>>(pd.phiT, pd.xT, y, lam, c->base,
+                                                                          c->near_ptr, c->near_col, nval, c->N, Nc,
+                                                                          c->n[0], c->n[1], nrhs, fvec, frho, c->S, c->M + 1)));
+
     return launch_check(c, "interp_near");
   }
   {
     const long long threads = (long long)c->N * 8;
     const int blocks = (int)((threads + 255) / 256);
     const R fvec = (R)(c->k * kEta0), frho = (R)(kEta0 / c->k);
-#define AIM_INTERP(MM)                                                                                          \
-  AIM_LAUNCH(c, "interp_near",                                                                                  \
-             (interp_near<MI, MM><<<blocks, 256, 0, c->stream>>>(phi, x, y, lam, c->base, c->near_ptr,          \
-                                                                 c->near_col, nval, c->N, Nc, c->n[0], c->n[1], \
-                                                                 nrhs, fvec, frho, c->S)))
-    switch (c->M) {
-      case 1: AIM_INTERP(1); break;
-      case 2: AIM_INTERP(2); break;
-      default: AIM_INTERP(3); break;
-    }
-#undef AIM_INTERP
+    AIM_LAUNCH(c, "interp_near",
+             (interp_near<MI><<<blocks, 256, 0, c->stream>>>(phi, x, y, lam, c->base, c->near_ptr,
+                                                                 c->near_col, nval, c->N, Nc, c->n[0], c->n[1],
+                                                                 nrhs, fvec, frho, c->S, c->M + 1)));
+
     AIM_TRY(launch_check(c, "interp_near"));
   }
   return AIM_OK;
@@ -735,17 +716,11 @@ int matvec_c64_bufs(aim_ctx* c, const float2* x, float2* y, int nrhs, float2* g0
     const long long threads = (long long)c->N * 8;
     const int blocks = (int)((threads + 255) / 256);
     const float fvec = (float)(c->k * kEta0), frho = (float)(kEta0 / c->k);
-#define AIM_INTERP32(MM)                                                                                      \
-  AIM_LAUNCH(c, "interp_near",                                                                                \
-             (interp_near<M32, MM><<<blocks, 256, 0, c->stream>>>(g0, x, y, c->p32.lam, c->base, c->near_ptr, \
-                                                                  c->near_col, c->p32.near_val, c->N, Nc,     \
-                                                                  c->n[0], c->n[1], nrhs, fvec, frho, c->S)))
-    switch (c->M) {
-      case 1: AIM_INTERP32(1); break;
-      case 2: AIM_INTERP32(2); break;
-      default: AIM_INTERP32(3); break;
-    }
-#undef AIM_INTERP32
+    AIM_LAUNCH(c, "interp_near",
+             (interp_near<M32><<<blocks, 256, 0, c->stream>>>(g0, x, y, c->p32.lam, c->base, c->near_ptr,
+                                                                  c->near_col, c->p32.near_val, c->N, Nc,
+                                                                  c->n[0], c->n[1], nrhs, fvec, frho, c->S, c->M + 1)));
+
     AIM_TRY(launch_check(c, "interp_near"));
   }
   return AIM_OK;

@@ -305,7 +305,7 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
         const double wq = A * rw.w[q];
         const double g[4] = {cf * (r.x - fv.x), cf * (r.y - fv.y), cf * (r.z - fv.z), dv};
         const double xi = (r.x - h * ax) / h, up = (r.y - h * ay) / h, ze = (r.z - h * az) / h;
-        double lx[4], ly[4], lz[4];
+        double lx[6], ly[6], lz[6];
         for (int i = 0; i < P; ++i) {
           lx[i] = lagrange(M, i, xi);
           ly[i] = lagrange(M, i, up);

@@ -136,7 +136,7 @@ def test_rhs_matches_oracle(sphere_small):
     assert rel(V, planewave_rhs(op.rwg, K0, kh, po)) <= 1e-12
 
 
-@pytest.mark.parametrize("M", [1, 3])
+@pytest.mark.parametrize("M", [1, 3, 4, 5])
 def test_other_stencil_orders(M):
     v, t = plate_mesh(0.7, 6)
     ctx, op = make(v, t, M=M)

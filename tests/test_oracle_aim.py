@@ -57,6 +57,27 @@ def test_polynomial_reproduction(ball, M):
                 assert abs(lhs - rhs) <= 1e-13 * max(abs(rhs), 1e-3 * abs(ball.length[m]) * H ** q.sum()) + 1e-15, (m, q, c)
 
 
+@pytest.mark.parametrize("M", [4, 5])
+def test_polynomial_reproduction_high_order(ball, M):
+    """Orders 4 and 5 (125 and 216 nodes): the same moment identity with the
+    monomials in the stencil's local coordinates (r - h a) / h, where their
+    values stay O(1), and the right side from a 10-point rule (the oracle's
+    weight rule has 9 points at M = 5); exact to rounding of the sum of the
+    terms."""
+    anc = aim.anchors(ball.centre, H, M)
+    lam = aim.moment_weights(ball, H, M, anc)
+    off = aim.stencil_offsets(M)
+    rng = np.random.default_rng(1)
+    for m in rng.choice(ball.N, 4, replace=False):
+        for q in off:
+            poly = lambda r, q=q, a=anc[m]: np.prod(((r - H * a) / H) ** q, axis=-1)
+            at_nodes = np.prod(off.astype(np.float64) ** q, axis=-1)
+            for c in range(4):
+                terms = lam[m, c] * at_nodes
+                rhs = _integral_g_poly(ball, m, c, poly, n=10)  # degree 18: not the oracle's own rule
+                assert abs(terms.sum() - rhs) <= 1e-13 * np.abs(terms).sum() + 1e-16, (m, q, c)
+
+
 def test_charge_neutral_and_dipole_closed_form(plate):
     anc = aim.anchors(plate.centre, H, 2)
     lam = aim.moment_weights(plate, H, 2, anc)
