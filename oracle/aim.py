@@ -74,18 +74,25 @@ def moment_weights(rwg, h, M, anc):
     """Moment-matching weights Lambda[N, 4, S] (components x, y, z, charge).
 
     For basis m with anchor a and local coordinates xi = (r - h a) / h, the
-    weights solve, for every exponent triple (p, q, r) with entries <= M,
+    weights match every moment of per-axis degree <= M:
 
-        sum_u Lambda^c_m(u) u_x^p u_y^q u_z^r = int g^c_m(r) xi^p upsilon^q zeta^r dS
+        sum_u Lambda^c_m(u) p(u) = int g^c_m(r) p(xi) dS
 
-    with g^c = f_x, f_y, f_z, div f.  The moments are integrated with the
-    collapsed Gauss-Legendre rule ``n_weight_rule(M)``, exact for this
-    polynomial degree.  The (M+1)^3 x (M+1)^3 system is the Kronecker cube of
-    the 1-D Vandermonde matrix on the nodes 0..M and is solved axis by axis
-    with numpy.linalg.solve.
+    for all polynomials p of per-axis degree <= M, with g^c = f_x, f_y, f_z,
+    div f.  The equations are imposed on the basis of monomials in the
+    centred, scaled coordinate s = (xi - M/2) / (M/2) on each axis (the same
+    polynomial space as the monomials in xi, so the same weights, but a
+    far better conditioned system: the 1-D matrix has condition number 64
+    at M = 5 against 5.8e4 for monomials in xi).  The moments are integrated
+    with the collapsed Gauss-Legendre rule ``n_weight_rule(M)``, exact for
+    this polynomial degree.  The (M+1)^3 x (M+1)^3 system is the Kronecker
+    cube of the 1-D Vandermonde matrix on the scaled nodes and is solved axis
+    by axis with numpy.linalg.solve.
     """
-    off = stencil_offsets(M)  # nodes u (in local units)
+    off = stencil_offsets(M)  # nodes u (in local units); exponent triples in the same order
     S = len(off)
+    P = M + 1
+    half = 0.5 * M
     xi1, xi2, w = triangle_rule(n_weight_rule(M))
     mom = np.zeros((S, rwg.N, 4))
     verts, tris = rwg.verts, rwg.tris
@@ -96,18 +103,15 @@ def moment_weights(rwg, h, M, anc):
         g = np.empty(pts.shape[:2] + (4,))
         g[..., :3] = coef[:, None, None] * (pts - verts[free][:, None, :])
         g[..., 3] = (sgn * rwg.length / area)[:, None]
-        loc = (pts - h * anc[:, None, :]) / h
+        sc = ((pts - h * anc[:, None, :]) / h - half) / half  # scaled local coordinates
         wa = area[:, None] * w[None, :]
         for qi, q in enumerate(off):
-            mono = loc[..., 0] ** q[0] * loc[..., 1] ** q[1] * loc[..., 2] ** q[2]
+            mono = sc[..., 0] ** q[0] * sc[..., 1] ** q[1] * sc[..., 2] ** q[2]
             mom[qi] += np.einsum("mq,mqc->mc", wa * mono, g)
-    # The system matrix V[(p,q,r)][(i,j,k)] = i^p j^q k^r is the Kronecker
-    # product of the 1-D matrix V1[p][i] = i^p with itself (same node and
-    # exponent ordering on each axis), so V Lambda = mom is solved one axis at
-    # a time; the (M+1)^3 system itself is too ill-conditioned in FP64 from
-    # M = 4 on.
-    P = M + 1
-    V1 = np.vander(np.arange(P, dtype=np.float64), increasing=True).T  # V1[p][i] = i^p
+    # V[(p,q,r)][(i,j,k)] = s_i^p s_j^q s_k^r is the Kronecker product of the
+    # 1-D matrix V1[p][i] = s_i^p with itself, so V Lambda = mom is solved one
+    # axis at a time.
+    V1 = np.vander((np.arange(P, dtype=np.float64) - half) / half, increasing=True).T
     lam = mom.reshape(P, P, P, -1)  # [exponent z, y, x][basis, component]
     for axis in range(3):
         moved = np.moveaxis(lam, axis, 0)
