@@ -103,6 +103,17 @@ __global__ void __launch_bounds__(256) proj_gather(const cplx<typename MD::R>* _
   }
 }
 
+// Grid-index offset of each stencil node s = (kk P + j) P + i from the
+// stencil's first node, staged once per block (S <= 216 for M <= 5).
+__device__ __forceinline__ void stencil_offsets_smem(int* s_off, int S, int P, int nx, int ny) {
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const int i = s % P, j = (s / P) % P, kk = s / (P * P);
+    s_off[s] = (kk * ny + j) * nx + i;
+  }
+  __syncthreads();
+}
+constexpr int kMaxStencil = 216;
+
 // 8 lanes per basis function.
 template <class MD>
 __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restrict__ Phi,
@@ -116,6 +127,8 @@ __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restr
                                                    int S, int P) {
   using R = typename MD::R;
   using C = cplx<R>;
+  __shared__ int s_off[kMaxStencil];
+  stencil_offsets_smem(s_off, S, P, nx, ny);
   const int lane = threadIdx.x & 7;
   const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
   const bool live = m < N;
@@ -127,8 +140,7 @@ __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restr
     const typename MD::S* Pb = Phi + (long long)b * 4 * Nc;
     C av = cmake<C>(0, 0), ar = av, an = av;
     for (int s = lane; s < S; s += 8) {
-      const int i = s % P, j = (s / P) % P, kk = s / (P * P);
-      const long long node = b0 + ((long long)kk * ny + j) * nx + i;
+      const long long node = b0 + (long long)s_off[s];
       const C px = MD::get(Pb[node]), py = MD::get(Pb[Nc + node]), pz = MD::get(Pb[2 * Nc + node]),
               pr = MD::get(Pb[3 * Nc + node]);
       const R wx = lm[s], wy = lm[S + s], wz = lm[2 * S + s], wr = lm[3 * S + s];
@@ -224,6 +236,8 @@ __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* ys = reinterpret_cast<C*>(smem_raw);  // [8][B]
+  __shared__ int s_off[kMaxStencil];
+  stencil_offsets_smem(s_off, S, P, nx, ny);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * 8, m = m0 + warp;
   if (m < N) {
@@ -239,8 +253,7 @@ __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R
         for (int q = 0; q < RL; ++q) av[q] = ar[q] = an[q] = cmake<C>(0, 0);
 #pragma unroll 3
         for (int s = 0; s < S; ++s) {
-          const int i = s % P, j = (s / P) % P, kk = s / (P * P);
-          const C* ph = PhiT + (b0 + ((long long)kk * ny + j) * nx + i) * B + b;
+          const C* ph = PhiT + (b0 + (long long)s_off[s]) * B + b;
           const Run<C, RL> px = load_run<C, RL>(ph), py = load_run<C, RL>(ph + cs), pz = load_run<C, RL>(ph + 2 * cs),
                            pr = load_run<C, RL>(ph + 3 * cs);
           const R wx = lm[s], wy = lm[S + s], wz = lm[2 * S + s], wr = lm[3 * S + s];
@@ -434,6 +447,8 @@ __global__ void __launch_bounds__(256) interp_near_ff(const float4* __restrict__
                                                       const int32_t* __restrict__ ncol,
                                                       const float4* __restrict__ nval, int N, long long Nc, int nx,
                                                       int ny, int nrhs, float2 fvec, float2 frho, int S, int P) {
+  __shared__ int s_off[kMaxStencil];
+  stencil_offsets_smem(s_off, S, P, nx, ny);
   const int lane = threadIdx.x & 7;
   const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
   const bool live = m < N;
@@ -446,8 +461,7 @@ __global__ void __launch_bounds__(256) interp_near_ff(const float4* __restrict__
     const float4* Pb = Phi + (long long)b * 4 * Nc;
     ff avr = ffv(0.f, 0.f), avi = avr, arr = avr, ari = avr, anr = avr, ani = avr;
     for (int s = lane; s < S; s += 8) {
-      const int i = s % P, j = (s / P) % P, kk = s / (P * P);
-      const long long node = b0 + ((long long)kk * ny + j) * nx + i;
+      const long long node = b0 + (long long)s_off[s];
       const float4 px = Pb[node], py = Pb[Nc + node], pz = Pb[2 * Nc + node], pr = Pb[3 * Nc + node];
       const float2 wx = lm[s], wy = lm[S + s], wz = lm[2 * S + s], wr = lm[3 * S + s];
       avr = ff_mad(ffv(wx.x, wx.y), ffv(px.x, px.y), avr);
