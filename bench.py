@@ -625,12 +625,14 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e_steps = max(3, args.steps)
-    g.aim_matvec_host(ctx, xh, precision=P)
+    xp = torch.from_numpy(xh).pin_memory()  # pinned host buffers: the copies run at full link speed
+    yp = torch.empty_like(xp).pin_memory()
+    g.aim_matvec_host(ctx, xp, precision=P, out=yp)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        g.aim_matvec_host(ctx, xh, precision=P)
+        g.aim_matvec_host(ctx, xp, precision=P, out=yp)
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * e2e_steps * nrhs / e2e_s, "unit": "matvec/s",
+    e2e = {"value": world * e2e_steps * nrhs / e2e_s, "unit": "matvec/s", "host_buffers": "pinned",
            "h2d_bytes_per_step": int(xh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
 
     # roofline of the dominant kernel

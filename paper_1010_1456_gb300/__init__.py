@@ -177,11 +177,26 @@ def aim_matvec(ctx, x, y=None, precision=None):
     return y
 
 
-def aim_matvec_host(ctx, x, precision=AIM_C128):
-    """Same product with host (numpy) buffers, copies included; synchronises."""
+def aim_matvec_host(ctx, x, precision=AIM_C128, out=None):
+    """Same product with host buffers, copies included; synchronises.
+
+    x: numpy array, or a CPU torch tensor (pinned memory copies fastest);
+    out: optional host buffer of the same kind and shape for the result."""
+    if hasattr(x, "data_ptr"):  # torch tensor in host memory
+        torch = _torch()
+        dt = torch.complex64 if precision == AIM_C64 else torch.complex128
+        if x.device.type != "cpu" or x.dtype != dt or not x.is_contiguous():
+            raise ValueError(f"x: contiguous host tensor of {dt} expected")
+        x2 = x.reshape(-1, ctx.N)
+        y = torch.empty_like(x2) if out is None else out
+        if y.shape != x2.shape or y.dtype != dt or y.device.type != "cpu" or not y.is_contiguous():
+            raise ValueError("out: contiguous host tensor shaped like x expected")
+        check(load().aim_matvec_host(ctx.handle, C.c_void_p(x2.data_ptr()), C.c_void_p(y.data_ptr()), x2.shape[0],
+                                     precision), "aim_matvec_host")
+        return y
     dt = np.complex64 if precision == AIM_C64 else np.complex128
     x = np.ascontiguousarray(np.atleast_2d(x), dtype=dt)
-    y = np.empty_like(x)
+    y = np.empty_like(x) if out is None else out
     check(load().aim_matvec_host(ctx.handle, x.ctypes.data_as(C.c_void_p), y.ctypes.data_as(C.c_void_p),
                                  x.shape[0], precision), "aim_matvec_host")
     return y

@@ -289,6 +289,9 @@ int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int
   b += (double)L[0] * L[1] * L[2] * 32;                                // setup transform scratch
   b += (double)max_rhs * 4 * (nc + L[2] * n[1] * n[0] + L[2] * L[1] * n[0]) * 24;  // grids, both precisions
   b += (double)max_rhs * N * (16 * 53 + 48);                           // Krylov basis (m = 50) and vectors
+  b += (double)N * 4 * S * 8 * 2 + (double)nnz * 16;                   // float-float weights and near values
+  if (max_rhs >= kRhsLanesMin) b += (double)max_rhs * (4.0 * nc + N) * 16;  // RHS-minor copies of Phi and x
+  b += (double)mesh->nt * 60 * (144 + 12) + (double)nnz * 56;          // near-fill scratch at setup (peak)
   *bytes = (size_t)b;
   return AIM_OK;
 }

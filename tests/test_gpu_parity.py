@@ -127,6 +127,11 @@ def test_matvec_host_entry_point(plate_a):
         assert rel(g.aim_matvec_host(ctx, x, precision=prec), op.matvec(x)) <= 1e-12
     y32 = g.aim_matvec_host(ctx, x.astype(np.complex64), precision=g.AIM_C64)
     assert rel(y32, op.matvec(x.astype(np.complex64).astype(np.complex128))) <= 1e-5
+    # pinned torch host buffers give the same bytes
+    xp = torch.from_numpy(x).pin_memory()
+    yp = torch.empty_like(xp).pin_memory()
+    g.aim_matvec_host(ctx, xp, precision=g.AIM_C128, out=yp)
+    assert np.array_equal(yp.numpy(), g.aim_matvec_host(ctx, x, precision=g.AIM_C128))
 
 
 def test_rhs_matches_oracle(sphere_small):
