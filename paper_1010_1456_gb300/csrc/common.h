@@ -275,6 +275,8 @@ int alloc_krylov(aim_ctx* c);
 // Allocates everything a product of this precision allocates lazily, so a
 // product can be captured into a CUDA graph.
 int prepare_product(aim_ctx* c, int precision);
+// Right-hand sides from which the products run with lanes over them.
+constexpr int kRhsLanesMin = 16;
 // Forgets the solver's captured Arnoldi step (after the kernel choice changed).
 void drop_step_graph(aim_ctx* c);
 void free_krylov(aim_ctx* c);

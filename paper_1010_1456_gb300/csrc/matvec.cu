@@ -354,8 +354,6 @@ __global__ void __launch_bounds__(256) proj_gather_rhs(const cplx<typename MD::R
   }
 }
 
-// Right-hand sides from which the interpolation runs with lanes over them.
-constexpr int kRhsLanesMin = 16;
 
 // ---- float-float projection and interpolation (AIM_C128) ----
 // The FP64-accurate product keeps its grids in float-float form for the FFT
