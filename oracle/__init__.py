@@ -13,6 +13,7 @@ Multi-Core Clusters", Sections 2.1-2.2 and 4.1, eq. 1):
 * ``quadrature``  collapsed Gauss-Legendre triangle rules
 * ``rwg``         RWG basis functions on triangle meshes (Section 2.1 meshes)
 * ``efie``        EFIE Galerkin entries with singularity extraction, dense Z
+* ``mfie``        MFIE Galerkin entries, CFIE, differentiated AIM weights
 * ``aim``         AIM: moment-matching projection, grid Green's function
                   convolution, interpolation, near-zone correction (Section 2.2)
 * ``excitation``  plane-wave right-hand side

@@ -219,13 +219,16 @@ def aim_pair_values(lam, anc, rows, cols, h, k, M):
 
 
 class AIMOperator:
-    """Plain FP64 AIM approximation of the EFIE matrix (Section 2.2)."""
+    """Plain FP64 AIM approximation of the EFIE matrix (Section 2.2), or of the
+    CFIE matrix alpha ZE + (1 - alpha) eta ZM when alpha < 1 (closed bodies;
+    the MFIE part is in ``mfie``)."""
 
-    def __init__(self, rwg, k, h, M=2, near_radius=None, near_rows=None):
+    def __init__(self, rwg, k, h, M=2, near_radius=None, near_rows=None, alpha=1.0):
         self.rwg = rwg
         self.k = float(k)
         self.h = float(h)
         self.M = int(M)
+        self.alpha = float(alpha)
         self.radius = 3.0 * h if near_radius is None else float(near_radius)
         self.N = rwg.N
         self.anc = anchors(rwg.centre, h, M)
@@ -233,6 +236,10 @@ class AIMOperator:
         self.L = np.array([smooth_length(2 * v - 1) for v in self.n])
         self.loc = self.anc - self.lo  # anchor in grid index space
         self.lam = moment_weights(rwg, h, M, self.anc)
+        if self.alpha != 1.0:
+            from .mfie import mfie_weights
+
+            self.W = mfie_weights(rwg, h, M, self.anc)
         self.Ghat = scipy.fft.fftn(green_grid(self.n, self.L, h, k), workers=-1)
         rows, cols = near_pairs(rwg.centre, self.radius)
         if near_rows is not None:  # restrict the correction to some rows
@@ -246,7 +253,15 @@ class AIMOperator:
         zmn = mom_entries(self.rwg, rows, cols, self.k)
         znm = mom_entries(self.rwg, cols, rows, self.k)
         zsym = 0.5 * (zmn + znm)
-        return zsym - aim_pair_values(self.lam, self.anc, rows, cols, self.h, self.k, self.M)
+        ze = zsym - aim_pair_values(self.lam, self.anc, rows, cols, self.h, self.k, self.M)
+        if self.alpha == 1.0:
+            return ze
+        from .mfie import mfie_entries, mfie_pair_values
+
+        # ZM exact minus its grid form -<f_m, n x curl A_n>  (= -sum_c W^c_m G Lambda^c_n)
+        zm = mfie_entries(self.rwg, rows, cols, self.k) + mfie_pair_values(
+            self.W, self.lam, self.anc, rows, cols, self.h, self.k, self.M)
+        return self.alpha * ze + (1.0 - self.alpha) * ETA0 * zm
 
     # --- the four steps of one product -----------------------------------
     def project(self, x):
@@ -278,7 +293,14 @@ class AIMOperator:
         y = np.zeros((B, self.N), dtype=np.complex128)
         for c in range(4):
             y += fac[c] * np.einsum("ms,bms->bm", self.lam[:, c, :], P[:, c][:, flat])
-        return (1j * self.k * ETA0) * y
+        y = (1j * self.k * ETA0) * y
+        if self.alpha == 1.0:
+            return y
+        # MFIE: -<f_m, n x curl A> with the differentiated interpolation weights
+        ym = np.zeros((B, self.N), dtype=np.complex128)
+        for c in range(3):
+            ym -= np.einsum("ms,bms->bm", self.W[:, c, :], P[:, c][:, flat])
+        return self.alpha * y + (1.0 - self.alpha) * ETA0 * ym
 
     def matvec(self, x):
         """One AIM product: projection, FFT convolution, interpolation, near correction."""
@@ -295,5 +317,11 @@ class AIMOperator:
     def diagonal(self):
         """diag(Z~): grid self term plus the near (self) correction = MoM self term."""
         d = self.Znear.diagonal().copy()
-        d += aim_pair_values(self.lam, self.anc, np.arange(self.N), np.arange(self.N), self.h, self.k, self.M)
-        return d
+        idx = np.arange(self.N)
+        ge = aim_pair_values(self.lam, self.anc, idx, idx, self.h, self.k, self.M)
+        if self.alpha == 1.0:
+            return d + ge
+        from .mfie import mfie_pair_values
+
+        gm = -mfie_pair_values(self.W, self.lam, self.anc, idx, idx, self.h, self.k, self.M)
+        return d + self.alpha * ge + (1.0 - self.alpha) * ETA0 * gm
