@@ -273,10 +273,12 @@ def oracle_matvec_rate(verts, tris, nrhs, budget_s=20.0, sample_rows=192, seed=0
 
 
 # ---------------------------------------------------------------- solves
-def solve_section(g, ctx, kind, size, nrhs, P0):
+def solve_section(g, ctx, kind, size, nrhs, P0, verts=None, tris=None):
     """Plain (complex128) and mixed (complex64 + FP64 refinement) solves of
     the workload's excitation, tol 1e-6; err_thth of the mixed RCS against
-    the plain RCS by eq. (1)."""
+    the plain RCS by eq. (1).  For a sphere (closed) also the mixed CFIE
+    solve (alpha = 0.6, Section 2.2) on its own context: set-up time,
+    iterations, and its RCS against the plain EFIE one."""
     import torch
 
     from aim_inputs import planewave_minus_z_xpol, random_incidence
@@ -325,6 +327,27 @@ def solve_section(g, ctx, kind, size, nrhs, P0):
     out["err_thth_float_float_vs_plain"] = float(np.max(g.err_thth(sig["fp64_float_float_fft"], sig["plain_fp64"], w)))
     out["speedup_mixed_over_plain"] = out["plain_fp64"]["time_s"] / out["mixed_c64_fp64_refined"]["time_s"]
     out["rcs_directions"] = int(len(th))
+    if kind == "sphere" and verts is not None:
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cc = g.aim_setup(verts, tris, K0, H, M=2, near_radius=3 * H, max_rhs=nrhs, precision=g.AIM_C64,
+                         stream=stream.cuda_stream, cfie_alpha=0.6)
+        setup_s = time.perf_counter() - t0
+        Vc = g.aim_rhs_planewave(cc, kh, po)
+        g.aim_solve(cc, Vc, 1e-6, raise_on_noconv=False)  # first solve: one-time conversions, graph capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xc, info = g.aim_solve(cc, Vc, 1e-6, raise_on_noconv=False)
+        t = time.perf_counter() - t0
+        sc = g.aim_rcs(cc, Xc, th, ph)[0]
+        g.aim_destroy(cc)
+        out["cfie_mixed_alpha0.6"] = {
+            "setup_s": setup_s, "time_s": t, "solves_per_s": 1.0 / t, "iterations": info["iterations"],
+            "efie_iterations": out["mixed_c64_fp64_refined"]["iterations"], "restarts": info["restarts"],
+            "max_rel_res": float(info["rel_res"].max()), "converged": bool(info["converged"].all()),
+            "speedup_over_efie_mixed": out["mixed_c64_fp64_refined"]["time_s"] / t,
+            "err_thth_vs_efie_plain": float(np.max(g.err_thth(sc, sig["plain_fp64"], w)))}
     return out
 
 
@@ -621,7 +644,7 @@ def run_ours(args, rank, world, local_rank):
                                "matvec_per_s": nrhs * 1e3 / vms, "ms_per_step": vms, "steps": vsteps}
         ctx3.close()
         del ctx3
-    solve = solve_section(g, ctx, kind, size, nrhs, P) if args.solve else None
+    solve = solve_section(g, ctx, kind, size, nrhs, P, verts, tris) if args.solve else None
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e_steps = max(3, args.steps)

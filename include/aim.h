@@ -86,6 +86,11 @@ typedef struct {
                       plane: the grid becomes nx x ny x 1 and the convolution two-dimensional
                       (same product up to rounding; aim_grid_info reports the reduced grid).
                       0: always three-dimensional. */
+  double cfie_alpha; /* 1 (default): EFIE.  0 < alpha < 1: combined-field equation (paper Section
+                      2.2, alpha = 0.6 for closed bodies) alpha EFIE + (1 - alpha) eta MFIE, for a
+                      closed surface with outward-oriented triangles (vertex order (r0, r1, r2)
+                      with (r1 - r0) x (r2 - r0) pointing out); aim_setup returns AIM_EINVAL for an
+                      open mesh.  Products, right-hand sides and solves then use the CFIE. */
 } aim_opts;
 
 /* Per-solve report. rel_res and iters are caller arrays of length nrhs. */
@@ -130,7 +135,8 @@ int aim_grid_info(const aim_ctx* ctx, int32_t n[3], int32_t L[3], int64_t* nnz_n
 /*
  * Plane-wave right-hand sides V_m = int f_m . pol exp(-j k khat . r) dS
  * (paper Section 2.1 excitation), collapsed Gauss-Legendre 4x4 rule per
- * triangle.  khat, pol: host [nrhs][3].  V_dev: device c128 [nrhs][N].
+ * triangle; with CFIE, alpha V_m + (1 - alpha) int f_m . (n x (khat x pol))
+ * exp(-j k khat . r) dS.  khat, pol: host [nrhs][3].  V_dev: device c128 [nrhs][N].
  */
 int aim_rhs_planewave(aim_ctx* ctx, int nrhs, const double* khat, const double* pol, void* V_dev);
 
@@ -190,7 +196,10 @@ int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int
  *       AIM_EXPORT_NEAR_VAL c128 [nnz], AIM_EXPORT_DIAG c128 [N],
  *       AIM_EXPORT_GHAT c128 octant [Lz/2+1][Ly/2+1][Lx/2+1] (scaled by 1/(Lx Ly Lz)),
  *       AIM_EXPORT_PROJ_PTR int32 [nx*ny*nz + 1] (per grid node, offsets into
- *       the node-ordered projection entries; the last value is their count).
+ *       the node-ordered projection entries; the last value is their count),
+ *       AIM_EXPORT_MFIE_WEIGHTS f64 [N][3][(M+1)^3] (CFIE contexts only: the
+ *       differentiated-interpolation weights W^c_m(u) = int f_m . (n x (grad L_u x e_c)),
+ *       c = x, y, z; AIM_EINVAL for an EFIE context).
  * bytes must equal the array size exactly.  Synchronises.
  */
 enum {
@@ -201,7 +210,8 @@ enum {
   AIM_EXPORT_NEAR_VAL = 5,
   AIM_EXPORT_DIAG = 6,
   AIM_EXPORT_GHAT = 7,
-  AIM_EXPORT_PROJ_PTR = 8
+  AIM_EXPORT_PROJ_PTR = 8,
+  AIM_EXPORT_MFIE_WEIGHTS = 9
 };
 int aim_export(aim_ctx* ctx, int what, void* host_dst, size_t bytes);
 

@@ -20,6 +20,7 @@ from ._lib import (  # noqa: F401
     AIM_EXPORT_ANCHORS,
     AIM_EXPORT_DIAG,
     AIM_EXPORT_GHAT,
+    AIM_EXPORT_MFIE_WEIGHTS,
     AIM_EXPORT_NEAR_COL,
     AIM_EXPORT_NEAR_PTR,
     AIM_EXPORT_NEAR_VAL,
@@ -92,7 +93,7 @@ def aim_default_opts():
 
 
 def aim_setup(verts, tris, k, h, M=2, near_radius=None, precision=AIM_C128, restart=50, maxit=3000,
-              check_every=5, max_rhs=1, stream=None, planar=True, verbose=False):
+              check_every=5, max_rhs=1, stream=None, planar=True, verbose=False, cfie_alpha=1.0):
     """Build a context (host FP64 setup + device spectrum); see aim_setup in aim.h."""
     lib = load()
     mesh, keep = _mesh(verts, tris)
@@ -105,6 +106,7 @@ def aim_setup(verts, tris, k, h, M=2, near_radius=None, precision=AIM_C128, rest
     o.stream = _stream(stream)
     o.planar = 1 if planar else 0
     o.verbose = 1 if verbose else 0
+    o.cfie_alpha = float(cfie_alpha)
     h_ = C.c_void_p()
     r = 3.0 * h if near_radius is None else float(near_radius)
     check(lib.aim_setup(C.byref(mesh), float(k), float(h), int(M), r, C.byref(o), C.byref(h_)), "aim_setup")
@@ -262,6 +264,7 @@ def aim_export(ctx, what):
         AIM_EXPORT_DIAG: ((N,), np.complex128),
         AIM_EXPORT_GHAT: ((L[2] // 2 + 1, L[1] // 2 + 1, L[0] // 2 + 1), np.complex128),
         AIM_EXPORT_PROJ_PTR: ((n[0] * n[1] * n[2] + 1,), np.int32),
+        AIM_EXPORT_MFIE_WEIGHTS: ((N, 3, S), np.float64),
     }
     shape, dt = shapes[what]
     a = np.empty(shape, dtype=dt)

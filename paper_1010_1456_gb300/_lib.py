@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libaim.so")
 AIM_OK, AIM_EINVAL, AIM_ENOMEM, AIM_ECUDA, AIM_ENOCONV, AIM_ETIMEOUT, AIM_ENODEV = range(7)
 AIM_C64, AIM_C128, AIM_C128_F64 = 1, 2, 3
 (AIM_EXPORT_ANCHORS, AIM_EXPORT_WEIGHTS, AIM_EXPORT_NEAR_PTR, AIM_EXPORT_NEAR_COL, AIM_EXPORT_NEAR_VAL,
- AIM_EXPORT_DIAG, AIM_EXPORT_GHAT, AIM_EXPORT_PROJ_PTR) = range(1, 9)
+ AIM_EXPORT_DIAG, AIM_EXPORT_GHAT, AIM_EXPORT_PROJ_PTR, AIM_EXPORT_MFIE_WEIGHTS) = range(1, 10)
 
 
 class aim_mesh(C.Structure):
@@ -30,6 +30,7 @@ class aim_opts(C.Structure):
         ("verbose", C.c_int),
         ("stream", C.c_void_p),
         ("planar", C.c_int),
+        ("cfie_alpha", C.c_double),
     ]
 
 

@@ -23,7 +23,7 @@ template <typename R> static int ensure_buffers(aim_ctx* c, PrecData<R>& p) {
 }
 
 template <typename R> static void free_prec(PrecData<R>& p) {
-  cudaFree(p.lam); cudaFree(p.pnode_w); cudaFree(p.ghat); cudaFree(p.near_val);
+  cudaFree(p.lam); cudaFree(p.lamM); cudaFree(p.pnode_w); cudaFree(p.ghat); cudaFree(p.near_val);
   for (int d = 0; d < 3; ++d) cudaFree(p.tw[d]);
   cudaFree(p.grid0); cudaFree(p.grid1); cudaFree(p.grid2); cudaFree(p.xbuf); cudaFree(p.ybuf);
   cudaFree(p.phiT); cudaFree(p.xT);
@@ -38,13 +38,14 @@ static void free_ctx(aim_ctx* c) {
   cudaFree(c->pff.ghat);
   for (int d = 0; d < 3; ++d) cudaFree(c->pff.tw[d]);
   cudaFree(c->pff.grid0); cudaFree(c->pff.grid1); cudaFree(c->pff.grid2);
-  cudaFree(c->pff.pnode_w); cudaFree(c->pff.lam); cudaFree(c->pff.near_val); cudaFree(c->pff.xff);
+  cudaFree(c->pff.pnode_w); cudaFree(c->pff.lam); cudaFree(c->pff.lamM); cudaFree(c->pff.near_val);
+  cudaFree(c->pff.xff);
   cudaFree(c->plan_dev);
   free_krylov(c);
   profile_free(c);
   cudaFree(c->base); cudaFree(c->near_ptr); cudaFree(c->near_col); cudaFree(c->pnode_ptr); cudaFree(c->pnode_m);
   cudaFree(c->diag); cudaFree(c->dinv64); cudaFree(c->d_verts); cudaFree(c->d_tris); cudaFree(c->rwg_tri);
-  cudaFree(c->rwg_free); cudaFree(c->rwg_len); cudaFree(c->tri_area);
+  cudaFree(c->rwg_free); cudaFree(c->rwg_len); cudaFree(c->tri_area); cudaFree(c->tri_nrm);
   delete c;
 }
 
@@ -98,6 +99,7 @@ void aim_default_opts(aim_opts* o) {
   o->verbose = 0;
   o->stream = nullptr;
   o->planar = 1;
+  o->cfie_alpha = 1.0;
 }
 
 int aim_setup(const aim_mesh* mesh, double k, double h, int M, double near_radius, const aim_opts* opts,
@@ -116,6 +118,10 @@ int aim_setup(const aim_mesh* mesh, double k, double h, int M, double near_radiu
   if (opts) o = *opts;
   if (o.precision != AIM_C64 && o.precision != AIM_C128 && o.precision != AIM_C128_F64) {
     set_error("aim_setup: precision must be AIM_C64, AIM_C128 or AIM_C128_F64");
+    return AIM_EINVAL;
+  }
+  if (!(o.cfie_alpha > 0.0 && o.cfie_alpha <= 1.0)) {
+    set_error("aim_setup: cfie_alpha must be in (0, 1]");
     return AIM_EINVAL;
   }
   if (o.restart < 1 || o.restart > 200 || o.max_rhs < 1 || o.max_rhs > 256 || o.maxit < 1 || o.check_every < 1) {
@@ -322,6 +328,14 @@ int aim_export(aim_ctx* c, int what, void* dst, size_t bytes) {
     case AIM_EXPORT_DIAG: src = c->h_diag.data(); need = c->h_diag.size() * 8; break;
     case AIM_EXPORT_GHAT: src = c->h_ghat.data(); need = c->h_ghat.size() * 8; break;
     case AIM_EXPORT_PROJ_PTR: src = c->h_pnode_ptr.data(); need = c->h_pnode_ptr.size() * 4; break;
+    case AIM_EXPORT_MFIE_WEIGHTS:
+      if (c->h_lamM.empty()) {
+        set_error("aim_export: MFIE weights exist only for a CFIE context (cfie_alpha < 1)");
+        return AIM_EINVAL;
+      }
+      src = c->h_lamM.data();
+      need = c->h_lamM.size() * 8;
+      break;
     default: set_error("aim_export: unknown array"); return AIM_EINVAL;
   }
   if (!dst || bytes != need) {

@@ -78,6 +78,7 @@ FftPlan make_plan(int L);  // radices from {4, 3, 5, 2}
 // ---------------------------------------------------------------- per-precision device data
 template <typename R> struct PrecData {
   R* lam = nullptr;               // [N][4][S] moment weights
+  R* lamM = nullptr;              // [N][3][S] MFIE weights (CFIE only)
   R* pnode_w = nullptr;           // [nent][4] projection weights, node-ordered
   cplx<R>* ghat = nullptr;        // octant [Lz/2+1][Ly/2+1][Lx/2+1], scaled by 1/(LxLyLz)
   cplx<R>* near_val = nullptr;    // [nnz]
@@ -104,6 +105,7 @@ struct FFData {
   float4* grid2 = nullptr;
   float4* pnode_w = nullptr;   // [nent][2]: (x, y, z, charge) high parts, then low parts
   float2* lam = nullptr;       // [N][4][S]
+  float2* lamM = nullptr;      // [N][3][S] (CFIE only)
   float4* near_val = nullptr;  // [nnz]
   float4* xff = nullptr;       // [B][N] the product's input
 };
@@ -153,6 +155,7 @@ struct aim_ctx {
   // problem
   int N = 0, M = 2, S = 27;  // S: stencil nodes per basis function ((M+1)^3, or (M+1)^2 on a planar grid)
   int planar = 0;            // grid reduced to the one z plane that holds every nonzero weight
+  double alpha = 1.0;        // CFIE weight of the EFIE (1: EFIE)
   int kk0 = 0;               // that plane's offset in the stencil
   double k = 0, h = 0, radius = 0;
   int lo[3] = {0, 0, 0};
@@ -175,6 +178,7 @@ struct aim_ctx {
   // host copies (inspection, RHS/RCS geometry)
   std::vector<int32_t> h_anchor;  // [N][3] absolute
   std::vector<double> h_lam;      // [N][4][S]
+  std::vector<double> h_lamM;     // [N][3][S] CFIE: differentiated-interpolation (MFIE) weights
   std::vector<int32_t> h_near_ptr, h_near_col;
   std::vector<double> h_near_val; // [nnz][2]
   std::vector<double> h_diag;     // [N][2]
@@ -191,6 +195,7 @@ struct aim_ctx {
   double2* dinv64 = nullptr;      // [N] 1/diag
   // RWG geometry on device (for RHS and far field)
   double* d_verts = nullptr;      // [nv][3]
+  double* tri_nrm = nullptr;      // [nt][3] unit normals (CFIE right-hand side)
   int32_t* d_tris = nullptr;      // [nt][3]
   int32_t* rwg_tri = nullptr;     // [N][2] (T+, T-)
   int32_t* rwg_free = nullptr;    // [N][2] free vertex of T+, T-
@@ -268,6 +273,8 @@ struct NearFillArgs {
   const double* lam = nullptr;
   const double2* gtab = nullptr;
   const TriRule *rule_test = nullptr, *rule_test_sing = nullptr, *rule_src = nullptr;
+  double alpha = 1.0;            // CFIE weight of the EFIE (1: EFIE only)
+  const double* lamM = nullptr;  // [N][3][S] MFIE weights (CFIE only)
 };
 // Writes the near values [nnz] (c128) and the MoM diagonal [N] (c128).
 int near_fill_device(aim_ctx* c, const NearFillArgs& a, double* val_out, double* diag_out);

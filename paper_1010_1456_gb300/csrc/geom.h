@@ -220,6 +220,19 @@ AIM_HD inline void pair_block(const V3 P[3], const V3 Q[3], double AP, double AQ
     for (int b = 0; b < 3; ++b) T[a][b] = cd(f1 * acc[a][b].re - f2 * s0acc.re, f1 * acc[a][b].im - f2 * s0acc.im);
 }
 
+// Derivative of the 1-D Lagrange basis on nodes 0..M at t.
+AIM_HD inline double lagrange_d(int M, int i, double t) {
+  double sum = 0.0;
+  for (int q = 0; q <= M; ++q) {
+    if (q == i) continue;
+    double v = 1.0 / (double)(i - q);
+    for (int p = 0; p <= M; ++p)
+      if (p != i && p != q) v *= (t - p) / (double)(i - p);
+    sum += v;
+  }
+  return sum;
+}
+
 // 1-D Lagrange basis on nodes 0..M evaluated at t.
 AIM_HD inline double lagrange(int M, int i, double t) {
   double v = 1.0;

@@ -18,6 +18,8 @@
 // accumulation) has its own kernels below.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "common.h"
 #include "ff.h"
 #include "geom.h"
@@ -115,7 +117,7 @@ __device__ __forceinline__ void stencil_offsets_smem(int* s_off, int S, int P, i
 constexpr int kMaxStencil = 216;
 
 // 8 lanes per basis function.
-template <class MD>
+template <class MD, bool MF>
 __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restrict__ Phi,
                                                    const cplx<typename MD::R>* __restrict__ x,
                                                    cplx<typename MD::R>* __restrict__ y,
@@ -124,7 +126,8 @@ __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restr
                                                    const int32_t* __restrict__ ncol,
                                                    const cplx<typename MD::R>* __restrict__ nval, int N, long long Nc,
                                                    int nx, int ny, int nrhs, typename MD::R fvec, typename MD::R frho,
-                                                   int S, int P) {
+                                                   int S, int P, const typename MD::R* __restrict__ lamM,
+                                                   typename MD::R fmf) {
   using R = typename MD::R;
   using C = cplx<R>;
   __shared__ int s_off[kMaxStencil];
@@ -135,10 +138,11 @@ __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restr
   const int mm = live ? m : N - 1;
   const int b0 = base[mm];
   const R* lm = lam + (long long)mm * 4 * S;
+  const R* wm = MF ? lamM + (long long)mm * 3 * S : nullptr;
   const int r0 = nptr[mm], r1 = nptr[mm + 1];
   for (int b = 0; b < nrhs; ++b) {
     const typename MD::S* Pb = Phi + (long long)b * 4 * Nc;
-    C av = cmake<C>(0, 0), ar = av, an = av;
+    C av = cmake<C>(0, 0), ar = av, an = av, am = av;
     for (int s = lane; s < S; s += 8) {
       const long long node = b0 + (long long)s_off[s];
       const C px = MD::get(Pb[node]), py = MD::get(Pb[Nc + node]), pz = MD::get(Pb[2 * Nc + node]),
@@ -148,6 +152,11 @@ __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restr
       av.y += wx * px.y + wy * py.y + wz * pz.y;
       ar.x += wr * pr.x;
       ar.y += wr * pr.y;
+      if constexpr (MF) {
+        const R mx = wm[s], my = wm[S + s], mz = wm[2 * S + s];
+        am.x += mx * px.x + my * py.x + mz * pz.x;
+        am.y += mx * px.y + my * py.y + mz * pz.y;
+      }
     }
     const C* xb = x + (long long)b * N;
     for (int e = r0 + lane; e < r1; e += 8) {
@@ -155,13 +164,18 @@ __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restr
       an.x += v.x * xv.x - v.y * xv.y;
       an.y += v.x * xv.y + v.y * xv.x;
     }
-    // grid part: j (fvec av - frho ar)  with fvec = k eta, frho = eta / k
+    // grid part: j (fvec av - frho ar) - fmf am  with fvec = alpha k eta,
+    // frho = alpha eta / k, fmf = (1 - alpha) eta (am: the MFIE weights' sum)
     C t;
     t.x = fvec * av.x - frho * ar.x;
     t.y = fvec * av.y - frho * ar.y;
     C out;
     out.x = an.x - t.y;
     out.y = an.y + t.x;
+    if constexpr (MF) {
+      out.x -= fmf * am.x;
+      out.y -= fmf * am.y;
+    }
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) {
       out.x += __shfl_xor_sync(0xffffffffu, out.x, o, 8);
@@ -221,7 +235,7 @@ template <class C, int RL> __device__ __forceinline__ Run<C, RL> load_run(const 
 // x value a warp reads is one contiguous run of right-hand sides; the weights
 // and near entries are warp-uniform.  The block's 8 rows of y are staged in
 // shared memory and written back in the [B][N] layout.
-template <class MI, int RL>
+template <class MI, int RL, bool MF>
 __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R>* __restrict__ PhiT,
                                                        const cplx<typename MI::R>* __restrict__ xT,
                                                        cplx<typename MI::R>* __restrict__ y,
@@ -231,7 +245,8 @@ __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R
                                                        const int32_t* __restrict__ ncol,
                                                        const cplx<typename MI::R>* __restrict__ nval, int N,
                                                        long long Nc, int nx, int ny, int B, typename MI::R fvec,
-                                                       typename MI::R frho, int S, int P) {
+                                                       typename MI::R frho, int S, int P,
+                                                       const typename MI::R* __restrict__ lamM, typename MI::R fmf) {
   using R = typename MI::R;
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -243,14 +258,15 @@ __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R
   if (m < N) {
     const int b0 = base[m];
     const R* lm = lam + (long long)m * 4 * S;
+    const R* wm = MF ? lamM + (long long)m * 3 * S : nullptr;
     const int r0 = nptr[m], r1 = nptr[m + 1];
     const long long cs = Nc * B;  // component stride of PhiT
     for (int bc = 0; bc < B; bc += 32 * RL) {
       const int b = bc + RL * lane;  // B is a multiple of RL
       if (b < B) {
-        C av[RL], ar[RL], an[RL];
+        C av[RL], ar[RL], an[RL], am[RL];
 #pragma unroll
-        for (int q = 0; q < RL; ++q) av[q] = ar[q] = an[q] = cmake<C>(0, 0);
+        for (int q = 0; q < RL; ++q) av[q] = ar[q] = an[q] = am[q] = cmake<C>(0, 0);
 #pragma unroll 3
         for (int s = 0; s < S; ++s) {
           const C* ph = PhiT + (b0 + (long long)s_off[s]) * B + b;
@@ -263,6 +279,14 @@ __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R
             av[q].y += wx * px.v[q].y + wy * py.v[q].y + wz * pz.v[q].y;
             ar[q].x += wr * pr.v[q].x;
             ar[q].y += wr * pr.v[q].y;
+          }
+          if constexpr (MF) {
+            const R mx = wm[s], my = wm[S + s], mz = wm[2 * S + s];
+#pragma unroll
+            for (int q = 0; q < RL; ++q) {
+              am[q].x += mx * px.v[q].x + my * py.v[q].x + mz * pz.v[q].x;
+              am[q].y += mx * px.v[q].y + my * py.v[q].y + mz * pz.v[q].y;
+            }
           }
         }
 #pragma unroll 4
@@ -283,6 +307,10 @@ __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R
           C out;
           out.x = an[q].x - t.y;
           out.y = an[q].y + t.x;
+          if constexpr (MF) {
+            out.x -= fmf * am[q].x;
+            out.y -= fmf * am[q].y;
+          }
           ys[warp * B + b + q] = out;
         }
       }
@@ -439,12 +467,14 @@ __global__ void __launch_bounds__(256) proj_gather_ff(const float4* __restrict__
 }
 
 // Interpolation + near correction: 8 lanes per basis function, as interp_near.
+template <bool MF>
 __global__ void __launch_bounds__(256) interp_near_ff(const float4* __restrict__ Phi, const float4* __restrict__ x,
                                                       double2* __restrict__ y, const float2* __restrict__ lam,
                                                       const int32_t* __restrict__ base, const int32_t* __restrict__ nptr,
                                                       const int32_t* __restrict__ ncol,
                                                       const float4* __restrict__ nval, int N, long long Nc, int nx,
-                                                      int ny, int nrhs, float2 fvec, float2 frho, int S, int P) {
+                                                      int ny, int nrhs, float2 fvec, float2 frho, int S, int P,
+                                                      const float2* __restrict__ lamM, float2 fmf) {
   __shared__ int s_off[kMaxStencil];
   stencil_offsets_smem(s_off, S, P, nx, ny);
   const int lane = threadIdx.x & 7;
@@ -453,11 +483,12 @@ __global__ void __launch_bounds__(256) interp_near_ff(const float4* __restrict__
   const int mm = live ? m : N - 1;
   const int b0 = base[mm];
   const float2* lm = lam + (long long)mm * 4 * S;
+  const float2* wm = MF ? lamM + (long long)mm * 3 * S : nullptr;
   const int r0 = nptr[mm], r1 = nptr[mm + 1];
-  const ff kv = ffv(fvec.x, fvec.y), kr = ffv(frho.x, frho.y);
+  const ff kv = ffv(fvec.x, fvec.y), kr = ffv(frho.x, frho.y), km = ffv(fmf.x, fmf.y);
   for (int b = 0; b < nrhs; ++b) {
     const float4* Pb = Phi + (long long)b * 4 * Nc;
-    ff avr = ffv(0.f, 0.f), avi = avr, arr = avr, ari = avr, anr = avr, ani = avr;
+    ff avr = ffv(0.f, 0.f), avi = avr, arr = avr, ari = avr, anr = avr, ani = avr, amr = avr, ami = avr;
     for (int s = lane; s < S; s += 8) {
       const long long node = b0 + (long long)s_off[s];
       const float4 px = Pb[node], py = Pb[Nc + node], pz = Pb[2 * Nc + node], pr = Pb[3 * Nc + node];
@@ -470,6 +501,15 @@ __global__ void __launch_bounds__(256) interp_near_ff(const float4* __restrict__
       avi = ff_mad(ffv(wz.x, wz.y), ffv(pz.z, pz.w), avi);
       arr = ff_mad(ffv(wr.x, wr.y), ffv(pr.x, pr.y), arr);
       ari = ff_mad(ffv(wr.x, wr.y), ffv(pr.z, pr.w), ari);
+      if constexpr (MF) {
+        const float2 mx = wm[s], my = wm[S + s], mz = wm[2 * S + s];
+        amr = ff_mad(ffv(mx.x, mx.y), ffv(px.x, px.y), amr);
+        ami = ff_mad(ffv(mx.x, mx.y), ffv(px.z, px.w), ami);
+        amr = ff_mad(ffv(my.x, my.y), ffv(py.x, py.y), amr);
+        ami = ff_mad(ffv(my.x, my.y), ffv(py.z, py.w), ami);
+        amr = ff_mad(ffv(mz.x, mz.y), ffv(pz.x, pz.y), amr);
+        ami = ff_mad(ffv(mz.x, mz.y), ffv(pz.z, pz.w), ami);
+      }
     }
     const float4* xb = x + (long long)b * N;
     for (int e = r0 + lane; e < r1; e += 8) {
@@ -484,6 +524,10 @@ __global__ void __launch_bounds__(256) interp_near_ff(const float4* __restrict__
     const ff tr = ff_sub(ff_mul(kv, avr), ff_mul(kr, arr));
     const ff ti = ff_sub(ff_mul(kv, avi), ff_mul(kr, ari));
     ff outr = ff_sub(anr, ti), outi = ff_add(ani, tr);
+    if constexpr (MF) {
+      outr = ff_sub(outr, ff_mul(km, amr));
+      outi = ff_sub(outi, ff_mul(km, ami));
+    }
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) {
       outr = ff_add(outr, ffv(__shfl_xor_sync(0xffffffffu, outr.hi, o, 8), __shfl_xor_sync(0xffffffffu, outr.lo, o, 8)));
@@ -506,6 +550,12 @@ static int ensure_ff_arrays(aim_ctx* c) {
   AIM_TRY(launch_check(c, "weights_to_ff"));
   AIM_LAUNCH(c, "weights_to_ff", (k_real_to_ff<<<blocks, 256, 0, c->stream>>>(c->p64.lam, p.lam, nl)));
   AIM_TRY(launch_check(c, "weights_to_ff"));
+  if (c->p64.lamM) {
+    const long long nm = (long long)c->N * 3 * c->S;
+    AIM_CUDA_TRY(cudaMalloc(&p.lamM, sizeof(float2) * nm));
+    AIM_LAUNCH(c, "weights_to_ff", (k_real_to_ff<<<blocks, 256, 0, c->stream>>>(c->p64.lamM, p.lamM, nm)));
+    AIM_TRY(launch_check(c, "weights_to_ff"));
+  }
   if (c->nnz > 0) {
     AIM_LAUNCH(c, "weights_to_ff", (k_cplx_to_ff<<<blocks, 256, 0, c->stream>>>(c->p64.near_val, p.near_val, c->nnz)));
     AIM_TRY(launch_check(c, "weights_to_ff"));
@@ -534,13 +584,17 @@ static int run_product_ff(aim_ctx* c, const double2* x, double2* y, int nrhs) {
   {
     const long long threads = (long long)c->N * 8;
     const int blocks = (int)((threads + 255) / 256);
-    const double fv = c->k * kEta0, fr = kEta0 / c->k;
-    const float fvh = (float)fv, frh = (float)fr;
+    const double fv = c->alpha * c->k * kEta0, fr = c->alpha * kEta0 / c->k, fm = (1.0 - c->alpha) * kEta0;
+    const float fvh = (float)fv, frh = (float)fr, fmh = (float)fm;
     const float2 fvec = make_float2(fvh, (float)(fv - (double)fvh)), frho = make_float2(frh, (float)(fr - (double)frh));
-    AIM_LAUNCH(c, "interp_near",
-             (interp_near_ff<<<blocks, 256, 0, c->stream>>>(p.grid0, p.xff, y, p.lam, c->base, c->near_ptr,
+    const float2 fmf = make_float2(fmh, (float)(fm - (double)fmh));
+    const auto go = [&](auto mf) {
+      AIM_LAUNCH(c, "interp_near",
+             (interp_near_ff<decltype(mf)::value><<<blocks, 256, 0, c->stream>>>(p.grid0, p.xff, y, p.lam, c->base, c->near_ptr,
                                                                 c->near_col, p.near_val, c->N, Nc, c->n[0], c->n[1],
-                                                                nrhs, fvec, frho, c->S, c->M + 1)));
+                                                                nrhs, fvec, frho, c->S, c->M + 1, p.lamM, fmf)));
+    };
+    if (p.lamM) go(std::true_type{}); else go(std::false_type{});
 
     AIM_TRY(launch_check(c, "interp_near"));
   }
@@ -603,28 +657,36 @@ static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename 
     AIM_TRY(transpose(c, "transpose_phi", reinterpret_cast<const cplx<R>*>(phi), pd.phiT, nrhs, 4 * Nc));
     const int blocks = (c->N + 7) / 8;
     const size_t sm = sizeof(cplx<R>) * 8 * nrhs;
-    const R fvec = (R)(c->k * kEta0), frho = (R)(kEta0 / c->k);
+    const R fvec = (R)(c->alpha * c->k * kEta0), frho = (R)(c->alpha * kEta0 / c->k),
+            fmf = (R)((1.0 - c->alpha) * kEta0);
+    const auto go = [&](auto mf) {
     if (two)
       AIM_LAUNCH(c, "interp_near",
-             (interp_near_rhs<MI, 2><<<blocks, 256, sm, c->stream>>>(pd.phiT, pd.xT, y, lam, c->base,
+             (interp_near_rhs<MI, 2, decltype(mf)::value><<<blocks, 256, sm, c->stream>>>(pd.phiT, pd.xT, y, lam, c->base,
                                                                           c->near_ptr, c->near_col, nval, c->N, Nc,
-                                                                          c->n[0], c->n[1], nrhs, fvec, frho, c->S, c->M + 1)));
+                                                                          c->n[0], c->n[1], nrhs, fvec, frho, c->S, c->M + 1, pd.lamM, fmf)));
     else
       AIM_LAUNCH(c, "interp_near",
-             (interp_near_rhs<MI, 1><<<blocks, 256, sm, c->stream>>>(pd.phiT, pd.xT, y, lam, c->base,
+             (interp_near_rhs<MI, 1, decltype(mf)::value><<<blocks, 256, sm, c->stream>>>(pd.phiT, pd.xT, y, lam, c->base,
                                                                           c->near_ptr, c->near_col, nval, c->N, Nc,
-                                                                          c->n[0], c->n[1], nrhs, fvec, frho, c->S, c->M + 1)));
+                                                                          c->n[0], c->n[1], nrhs, fvec, frho, c->S, c->M + 1, pd.lamM, fmf)));
+    };
+    if (pd.lamM) go(std::true_type{}); else go(std::false_type{});
 
     return launch_check(c, "interp_near");
   }
   {
     const long long threads = (long long)c->N * 8;
     const int blocks = (int)((threads + 255) / 256);
-    const R fvec = (R)(c->k * kEta0), frho = (R)(kEta0 / c->k);
+    const R fvec = (R)(c->alpha * c->k * kEta0), frho = (R)(c->alpha * kEta0 / c->k),
+            fmf = (R)((1.0 - c->alpha) * kEta0);
+    const auto go = [&](auto mf) {
     AIM_LAUNCH(c, "interp_near",
-             (interp_near<MI><<<blocks, 256, 0, c->stream>>>(phi, x, y, lam, c->base, c->near_ptr,
+             (interp_near<MI, decltype(mf)::value><<<blocks, 256, 0, c->stream>>>(phi, x, y, lam, c->base, c->near_ptr,
                                                                  c->near_col, nval, c->N, Nc, c->n[0], c->n[1],
-                                                                 nrhs, fvec, frho, c->S, c->M + 1)));
+                                                                 nrhs, fvec, frho, c->S, c->M + 1, pd.lamM, fmf)));
+    };
+    if (pd.lamM) go(std::true_type{}); else go(std::false_type{});
 
     AIM_TRY(launch_check(c, "interp_near"));
   }
@@ -727,11 +789,15 @@ int matvec_c64_bufs(aim_ctx* c, const float2* x, float2* y, int nrhs, float2* g0
   {
     const long long threads = (long long)c->N * 8;
     const int blocks = (int)((threads + 255) / 256);
-    const float fvec = (float)(c->k * kEta0), frho = (float)(kEta0 / c->k);
+    const float fvec = (float)(c->alpha * c->k * kEta0), frho = (float)(c->alpha * kEta0 / c->k),
+                fmf = (float)((1.0 - c->alpha) * kEta0);
+    const auto go = [&](auto mf) {
     AIM_LAUNCH(c, "interp_near",
-             (interp_near<M32><<<blocks, 256, 0, c->stream>>>(g0, x, y, c->p32.lam, c->base, c->near_ptr,
+             (interp_near<M32, decltype(mf)::value><<<blocks, 256, 0, c->stream>>>(g0, x, y, c->p32.lam, c->base, c->near_ptr,
                                                                   c->near_col, c->p32.near_val, c->N, Nc,
-                                                                  c->n[0], c->n[1], nrhs, fvec, frho, c->S, c->M + 1)));
+                                                                  c->n[0], c->n[1], nrhs, fvec, frho, c->S, c->M + 1, c->p32.lamM, fmf)));
+    };
+    if (c->p32.lamM) go(std::true_type{}); else go(std::false_type{});
 
     AIM_TRY(launch_check(c, "interp_near"));
   }

@@ -10,6 +10,10 @@
 //   3. symmetrisation (Z_mn + Z_nm) / 2 and the subtraction of the pair's
 //      grid approximation j k eta [sum_xyz L_m G_h L_n - k^-2 L^rho_m G_h L^rho_n],
 //      one warp per entry (lanes over the test stencil nodes).
+// With CFIE (alpha < 1, Section 2.2 for closed bodies) the same kernels also
+// produce the MFIE blocks 1/2 <f_m, f_n> - <f_m, n x int grad G x f_n>
+// (unsymmetrised) and subtract their grid form -sum_c W^c_m . G Lambda^c_n;
+// the entry is alpha EFIE + (1 - alpha) eta MFIE.
 // Every value is FP64.  The host builds the pair lists; the results come
 // back to the host arrays the rest of setup reads.
 #include <algorithm>
@@ -44,11 +48,73 @@ __device__ __forceinline__ V3 vtx(const FillGeom& g, int t, int s) {
   return v3(p[0], p[1], p[2]);
 }
 
-// Triangle-pair blocks: pair i = (pP[i], pQ[i]); out[i][a][b].
+// MFIE triangle-pair block T[a][b] = C[a][b] / 2 - B[a][b] with
+//   B[a][b] = 1/(4 A_P A_Q) int_P int_Q (r - P_a) . (n_P x (grad G(r - r') x (r' - Q_b))) dS' dS,
+//   grad G(D) = -(1 + j k R) exp(-j k R) / (4 pi R^3) D,   D = r - r',
+//   C[a][b] = 1/(4 A_P^2) int_P (r - P_a) . (r - P_b) dS   (equal triangles only);
+// so that <f_m, f_n>/2 - <f_m, n x int grad G x f_n> += s_m s_n l_m l_n T[a][b].
+// Coplanar triangles (a triangle with itself included) have B = 0: every
+// vector of the integrand lies in their plane.
+__device__ void mfie_block(const V3 Pv[3], const V3 Qv[3], double AP, double AQ, bool same, double k,
+                           const TriRule& test, const TriRule& src, Cd T[3][3]) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) T[a][b] = cd(0, 0);
+  if (same) {
+    const TriRule& g3 = rule(0);  // 3 x 3 points: exact for the degree-2 Gram integrand
+    for (int i = 0; i < g3.q; ++i) {
+      const V3 r = tri_point(Pv[0], Pv[1], Pv[2], g3.xi1[i], g3.xi2[i]);
+      const double W = AP * g3.w[i] * 0.5 / (4.0 * AP * AP);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) T[a][b].re += W * dot(r - Pv[a], r - Pv[b]);
+    }
+    return;
+  }
+  const V3 nP0 = cross(Pv[1] - Pv[0], Pv[2] - Pv[0]), nQ0 = cross(Qv[1] - Qv[0], Qv[2] - Qv[0]);
+  const V3 nP = (1.0 / norm(nP0)) * nP0, nQ = (1.0 / norm(nQ0)) * nQ0;
+  const V3 nx = cross(nP, nQ);
+  if (fmax(fabs(nx.x), fmax(fabs(nx.y), fabs(nx.z))) == 0.0 && fabs(dot(Qv[0] - Pv[0], nP)) == 0.0) return;
+  Cd acc[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) acc[a][b] = cd(0, 0);
+  for (int i = 0; i < test.q; ++i) {
+    const V3 r = tri_point(Pv[0], Pv[1], Pv[2], test.xi1[i], test.xi2[i]);
+    const double W = AP * test.w[i];
+    const V3 ra[3] = {r - Pv[0], r - Pv[1], r - Pv[2]};
+    for (int q = 0; q < src.q; ++q) {
+      const V3 rq = tri_point(Qv[0], Qv[1], Qv[2], src.xi1[q], src.xi2[q]);
+      const V3 D = r - rq;
+      const double R = norm(D);
+      const double kr = k * R, s = W * AQ * src.w[q] / (4.0 * kPi * R * R * R);
+      const double cr = cos(kr), sr = sin(kr);
+      // -(1 + j kR)(cos kR - j sin kR) = -(cos + kR sin) + j (sin - kR cos)
+      const Cd gw = cd(-(cr + kr * sr) * s, (sr - kr * cr) * s);
+      const double nD = dot(nP, D);
+      double nb[3];
+      V3 rb[3];
+      for (int b = 0; b < 3; ++b) {
+        rb[b] = rq - Qv[b];
+        nb[b] = dot(nP, rb[b]);
+      }
+      for (int a = 0; a < 3; ++a) {
+        const double aD = dot(ra[a], D);
+        for (int b = 0; b < 3; ++b) {
+          const double integ = aD * nb[b] - dot(ra[a], rb[b]) * nD;
+          acc[a][b] = acc[a][b] + integ * gw;
+        }
+      }
+    }
+  }
+  const double f = -1.0 / (4.0 * AP * AQ);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) T[a][b] = f * acc[a][b];
+}
+
+// Triangle-pair blocks: pair i = (pP[i], pQ[i]); out[i][a][b] (EFIE) and,
+// when outM is set, outM[i][a][b] (MFIE).
 template <bool SING>
 __global__ void __launch_bounds__(128) k_pair_blocks(FillGeom g, const int32_t* __restrict__ ids,
                                                      const int32_t* __restrict__ pP, const int32_t* __restrict__ pQ,
-                                                     int n, double k, Cd* __restrict__ out) {
+                                                     int n, double k, Cd* __restrict__ out, Cd* __restrict__ outM) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int i = ids[t];
@@ -62,6 +128,12 @@ __global__ void __launch_bounds__(128) k_pair_blocks(FillGeom g, const int32_t* 
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) o[a * 3 + b] = T[a][b];
+  if (outM) {
+    mfie_block(Pv, Qv, g.area[P], g.area[Q], P == Q, k, rule(SING ? 1 : 0), rule(2), T);
+    Cd* oM = outM + (size_t)i * 9;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) oM[a * 3 + b] = T[a][b];
+  }
 }
 
 // Index of triangle Q in the sorted pair list of test triangle P.
@@ -76,9 +148,11 @@ __device__ __forceinline__ int64_t pair_of(const int32_t* tptr, const int32_t* p
 }
 
 // zhalf[half][e] = j k eta l_m l_n sum over n's two triangles of s_m s_n T[a][b]
+// and, with blkM, zMhalf[half][e] = l_m l_n sum s_m s_n TM[a][b] (the MFIE entry's halves).
 __global__ void k_near_halves(FillGeom g, const int32_t* __restrict__ erow, const int32_t* __restrict__ ecol,
                               const int32_t* __restrict__ tptr, const int32_t* __restrict__ pQ,
-                              const Cd* __restrict__ blk, int64_t nnz, double jke, double2* __restrict__ zhalf) {
+                              const Cd* __restrict__ blk, int64_t nnz, double jke, double2* __restrict__ zhalf,
+                              const Cd* __restrict__ blkM, double2* __restrict__ zMhalf) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 2 * nnz; t += (int64_t)gridDim.x * blockDim.x) {
     const int half = (int)(t / nnz);
     const int64_t e = t - half * nnz;
@@ -86,28 +160,38 @@ __global__ void k_near_halves(FillGeom g, const int32_t* __restrict__ erow, cons
     const int P = half ? g.tm[m] : g.tp[m];
     const int a = half ? g.sm[m] : g.sp[m];
     const double sm_ = half ? -1.0 : 1.0;
-    double re = 0.0, im = 0.0;
+    double re = 0.0, im = 0.0, mre = 0.0, mim = 0.0;
     for (int th = 0; th < 2; ++th) {
       const int Qt = th ? g.tm[n] : g.tp[n];
       const int b = th ? g.sm[n] : g.sp[n];
       const double sn_ = th ? -1.0 : 1.0;
-      const Cd v = blk[(size_t)pair_of(tptr, pQ, P, Qt) * 9 + a * 3 + b];
+      const size_t ib = (size_t)pair_of(tptr, pQ, P, Qt) * 9 + a * 3 + b;
+      const Cd v = blk[ib];
       re += sm_ * sn_ * v.re;
       im += sm_ * sn_ * v.im;
+      if (blkM) {
+        const Cd w = blkM[ib];
+        mre += sm_ * sn_ * w.re;
+        mim += sm_ * sn_ * w.im;
+      }
     }
-    const double f = jke * g.len[m] * g.len[n];
+    const double ll = g.len[m] * g.len[n], f = jke * ll;
     zhalf[half * nnz + e] = make_double2(-f * im, f * re);
+    if (blkM) zMhalf[half * nnz + e] = make_double2(ll * mre, ll * mim);
   }
 }
 
 // Symmetrised entry minus the grid approximation; one warp per entry, lane s
 // over the test stencil nodes.  gtab: G_h on offsets [-TE, TE]^3.
+// CFIE (lamM set): alpha (symmetrised EFIE entry - its grid form) + (1 - alpha) eta
+// (MFIE entry - its grid form -sum_c W^c_m . G Lambda^c_n).
 __global__ void __launch_bounds__(256) k_near_values(const int32_t* __restrict__ erow, const int32_t* __restrict__ ecol,
                                                      const int32_t* __restrict__ nptr, const double2* __restrict__ zhalf,
                                                      const double* __restrict__ lam, const int32_t* __restrict__ anchor,
                                                      const double2* __restrict__ gtab, int TE, int P, int64_t nnz,
                                                      double k, double jke, double2* __restrict__ val,
-                                                     double2* __restrict__ diag) {
+                                                     double2* __restrict__ diag, const double2* __restrict__ zMhalf,
+                                                     const double* __restrict__ lamM, double alpha) {
   const int lane = threadIdx.x & 31;
   const int S = P * P * P, TW = 2 * TE + 1;
   for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < nnz;
@@ -130,6 +214,8 @@ __global__ void __launch_bounds__(256) k_near_values(const int32_t* __restrict__
     const double* lm = lam + (size_t)m * 4 * S;
     const double* ln = lam + (size_t)n * 4 * S;
     double sr = 0.0, si = 0.0;  // sum over c of +-(lm^T G ln), vector minus k^-2 charge
+    double mr = 0.0, mi = 0.0;  // CFIE: sum over c = x, y, z of W^c_m . G Lambda^c_n
+    const double* wm = lamM ? lamM + (size_t)m * 3 * S : nullptr;
     for (int s = lane; s < S; s += 32) {
       const int si_ = s % P, sj = (s / P) % P, sk = s / (P * P);
       double ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
@@ -150,16 +236,34 @@ __global__ void __launch_bounds__(256) k_near_values(const int32_t* __restrict__
         sr += f * ar[c];
         si += f * ai[c];
       }
+      if (wm) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          mr += wm[c * S + s] * ar[c];
+          mi += wm[c * S + s] * ai[c];
+        }
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       sr += __shfl_xor_sync(0xffffffffu, sr, o);
       si += __shfl_xor_sync(0xffffffffu, si, o);
+      mr += __shfl_xor_sync(0xffffffffu, mr, o);
+      mi += __shfl_xor_sync(0xffffffffu, mi, o);
     }
     if (lane == 0) {
       // j k eta (sr + j si) = k eta (-si + j sr)
-      val[e] = make_double2(zr + jke * si, zi - jke * sr);
-      if (m == n) diag[m] = make_double2(zr, zi);
+      double2 v = make_double2(zr + jke * si, zi - jke * sr);
+      double2 d = make_double2(zr, zi);
+      if (wm) {
+        const double2 zm0 = zMhalf[e], zm1 = zMhalf[nnz + e];
+        const double zmr = zm0.x + zm1.x, zmi = zm0.y + zm1.y;
+        const double be = (1.0 - alpha) * kEta0;
+        v = make_double2(alpha * v.x + be * (zmr + mr), alpha * v.y + be * (zmi + mi));
+        d = make_double2(alpha * d.x + be * zmr, alpha * d.y + be * zmi);
+      }
+      val[e] = v;
+      if (m == n) diag[m] = d;
     }
   }
 }
@@ -204,6 +308,13 @@ int near_fill_device(aim_ctx* c, const NearFillArgs& A, double* val_out, double*
         (rc = dev((void**)&zhalf, nullptr, sizeof(double2) * 2 * nnz)) ||
         (rc = dev((void**)&val, nullptr, sizeof(double2) * nnz)) || (rc = dev((void**)&diag, nullptr, sizeof(double2) * N)))
       break;
+    Cd* blkM = nullptr;
+    double2* zMhalf = nullptr;
+    double* lamM = nullptr;
+    if (A.lamM && ((rc = dev((void**)&blkM, nullptr, sizeof(Cd) * 9 * npairs)) ||
+                   (rc = dev((void**)&zMhalf, nullptr, sizeof(double2) * 2 * nnz)) ||
+                   (rc = dev((void**)&lamM, A.lamM, sizeof(double) * N * 3 * A.S))))
+      break;
     if ((rc = [&]() -> int {
            const TriRule* rs[3] = {A.rule_test, A.rule_test_sing, A.rule_src};
            for (int i = 0; i < 3; ++i)
@@ -218,21 +329,21 @@ int near_fill_device(aim_ctx* c, const NearFillArgs& A, double* val_out, double*
     const int64_t nreg = npairs - A.nsing;
     if (A.nsing > 0) {
       AIM_LAUNCH(c, "near_pair_blocks", (k_pair_blocks<true><<<(unsigned)((A.nsing + 127) / 128), 128, 0, c->stream>>>(
-                                            g, ids, pP, pQ, (int)A.nsing, c->k, blk)));
+                                            g, ids, pP, pQ, (int)A.nsing, c->k, blk, blkM)));
       if ((rc = launch_check(c, "near_pair_blocks"))) break;
     }
     if (nreg > 0) {
       AIM_LAUNCH(c, "near_pair_blocks", (k_pair_blocks<false><<<(unsigned)((nreg + 127) / 128), 128, 0, c->stream>>>(
-                                            g, ids + A.nsing, pP, pQ, (int)nreg, c->k, blk)));
+                                            g, ids + A.nsing, pP, pQ, (int)nreg, c->k, blk, blkM)));
       if ((rc = launch_check(c, "near_pair_blocks"))) break;
     }
     const double jke = c->k * kEta0;
     AIM_LAUNCH(c, "near_halves", (k_near_halves<<<152 * 16, 256, 0, c->stream>>>(g, erow, ecol, tptr, pQ, blk, nnz,
-                                                                                   jke, zhalf)));
+                                                                                   jke, zhalf, blkM, zMhalf)));
     if ((rc = launch_check(c, "near_halves"))) break;
     AIM_LAUNCH(c, "near_values", (k_near_values<<<152 * 16, 256, 0, c->stream>>>(erow, ecol, nptr, zhalf, lam, anc, gtab,
                                                                                    A.TE, A.P, nnz, c->k, jke, val,
-                                                                                   diag)));
+                                                                                   diag, zMhalf, lamM, A.alpha)));
     if ((rc = launch_check(c, "near_values"))) break;
     if ((rc = [&]() -> int {
            AIM_CUDA_TRY(cudaMemcpyAsync(val_out, val, sizeof(double2) * nnz, cudaMemcpyDeviceToHost, c->stream));

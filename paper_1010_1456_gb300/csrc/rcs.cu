@@ -52,7 +52,8 @@ __device__ __forceinline__ V3 ldv(const double* v, int i) { return v3(v[3 * i], 
 __global__ void k_rhs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
                       const int32_t* __restrict__ rtri, const int32_t* __restrict__ rfree,
                       const double* __restrict__ len, const double* __restrict__ area, const double* __restrict__ khat,
-                      const double* __restrict__ pol, double2* __restrict__ V, int N, double k) {
+                      const double* __restrict__ pol, double2* __restrict__ V, int N, double k,
+                      const double* __restrict__ nrm, double alpha) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (m >= N) return;
@@ -66,9 +67,13 @@ __global__ void k_rhs(const double* __restrict__ verts, const int32_t* __restric
     const V3 r0 = ldv(verts, tris[3 * t]), r1 = ldv(verts, tris[3 * t + 1]), r2 = ldv(verts, tris[3 * t + 2]);
     const double A = area[t];
     const double cf = (half ? -1.0 : 1.0) * len[m] / (2.0 * A);
+    // CFIE: alpha E_inc + (1 - alpha) eta n x H_inc, both tangential-tested;
+    // eta H_inc = khat x pol times the same phase, n constant on the triangle.
+    V3 pt = pe;
+    if (nrm) pt = alpha * pe + (1.0 - alpha) * cross(ldv(nrm, t), cross(kh, pe));
     for (int q = 0; q < nq; ++q) {
       const V3 r = tri_point(r0, r1, r2, c_rhs_rule[0][q], c_rhs_rule[1][q]);
-      const double fp = cf * dot(r - fv, pe) * A * c_rhs_rule[2][q];
+      const double fp = cf * dot(r - fv, pt) * A * c_rhs_rule[2][q];
       double s, c;
       sincos(k * dot(kh, r), &s, &c);
       re += fp * c;
@@ -176,7 +181,8 @@ int rhs_planewave(aim_ctx* c, int nrhs, const double* khat, const double* pol, d
   AIM_CUDA_TRY(cudaMemcpyAsync(dk + 3 * nrhs, pol, sizeof(double) * 3 * nrhs, cudaMemcpyHostToDevice, c->stream));
   dim3 grid((c->N + 127) / 128, nrhs);
   AIM_LAUNCH(c, "k_rhs", k_rhs<<<grid, 128, 0, c->stream>>>(c->d_verts, c->d_tris, c->rwg_tri, c->rwg_free, c->rwg_len, c->tri_area, dk,
-                                     dk + 3 * nrhs, V, c->N, c->k));
+                                     dk + 3 * nrhs, V, c->N, c->k, c->alpha < 1.0 ? c->tri_nrm : nullptr,
+                                     c->alpha));
   AIM_TRY(launch_check(c, "k_rhs"));
   AIM_CUDA_TRY(cudaFreeAsync(dk, c->stream));
   AIM_CUDA_TRY(cudaStreamSynchronize(c->stream));

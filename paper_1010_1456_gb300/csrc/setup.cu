@@ -252,6 +252,21 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
   c->nv = T.nv;
   c->nt = T.nt;
   const double h = c->h, k = c->k;
+  c->alpha = c->opts.cfie_alpha;
+  const bool cfie = c->alpha < 1.0;
+  if (cfie)
+    for (int t = 0; t < 3 * T.nt; ++t)
+      if (T.tri_rwg[t] < 0) {
+        set_error("aim_setup: CFIE (cfie_alpha < 1) needs a closed surface; the mesh has boundary edges");
+        return AIM_EINVAL;
+      }
+  // unit normals (r1 - r0) x (r2 - r0) / |.| (outward for an outward-oriented closed mesh)
+  std::vector<V3> nrm(T.nt);
+  for (int t = 0; t < T.nt; ++t) {
+    const V3 r0 = T.vert[T.tri[3 * t]], r1 = T.vert[T.tri[3 * t + 1]], r2 = T.vert[T.tri[3 * t + 2]];
+    const V3 cr = cross(r1 - r0, r2 - r0);
+    nrm[t] = (1.0 / norm(cr)) * cr;
+  }
 
   // ---- anchors and grid
   c->h_anchor.resize(3 * (size_t)N);
@@ -290,9 +305,11 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
   const int nw = (3 * M + 4) / 2;
   const TriRule rw = make_tri_rule(nw);
   c->h_lam.assign((size_t)N * 4 * S, 0.0);
+  if (cfie) c->h_lamM.assign((size_t)N * 3 * S, 0.0);
   parallel_for(N, [&](int64_t mi) {
     const int m = (int)mi;
     double* lm = &c->h_lam[(size_t)m * 4 * S];
+    double* wm = cfie ? &c->h_lamM[(size_t)m * 3 * S] : nullptr;
     const double ax = c->h_anchor[3 * (size_t)m], ay = c->h_anchor[3 * (size_t)m + 1], az = c->h_anchor[3 * (size_t)m + 2];
     for (int half = 0; half < 2; ++half) {
       const int t = half ? T.tm[m] : T.tp[m];
@@ -318,6 +335,25 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
               const double b = wq * lx[i] * ly[j] * lz[kk];
               for (int cc = 0; cc < 4; ++cc) lm[cc * S + s] += b * g[cc];
             }
+        if (cfie) {
+          // W^c = int f . (n x (grad L_u x e_c)) = int (f . grad L_u) n_c - f_c (n . grad L_u)
+          const V3 n = nrm[t];
+          double dx[6], dy[6], dz[6];
+          for (int i = 0; i < P; ++i) {
+            dx[i] = lagrange_d(M, i, xi) / h;
+            dy[i] = lagrange_d(M, i, up) / h;
+            dz[i] = lagrange_d(M, i, ze) / h;
+          }
+          const double nn[3] = {n.x, n.y, n.z};
+          for (int kk = 0; kk < P; ++kk)
+            for (int j = 0; j < P; ++j)
+              for (int i = 0; i < P; ++i) {
+                const int s = (kk * P + j) * P + i;
+                const double gx = dx[i] * ly[j] * lz[kk], gy = lx[i] * dy[j] * lz[kk], gz = lx[i] * ly[j] * dz[kk];
+                const double fg = g[0] * gx + g[1] * gy + g[2] * gz, ng = n.x * gx + n.y * gy + n.z * gz;
+                for (int cc = 0; cc < 3; ++cc) wm[cc * S + s] += wq * (fg * nn[cc] - g[cc] * ng);
+              }
+        }
       }
     }
   });
@@ -425,6 +461,8 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
     A.erow = erow.data(); A.ecol = c->h_near_col.data(); A.nptr = c->h_near_ptr.data(); A.anchor = c->h_anchor.data();
     A.lam = c->h_lam.data(); A.gtab = gtab.data();
     A.rule_test = &rt; A.rule_test_sing = &rts; A.rule_src = &rs;
+    A.alpha = c->alpha;
+    A.lamM = cfie ? c->h_lamM.data() : nullptr;
     c->h_near_val.assign(2 * (size_t)nnz, 0.0);
     c->h_diag.assign(2 * (size_t)N, 0.0);
     AIM_TRY(near_fill_device(c, A, c->h_near_val.data(), c->h_diag.data()));
@@ -436,7 +474,7 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
   // G_h(dx, dy, 0); the near entries above used the full stencil and are
   // unchanged.
   int S_run = S;
-  if (c->opts.planar) {
+  if (c->opts.planar && !cfie) {
     bool same = true;
     for (int m = 1; m < N && same; ++m) same = c->h_anchor[3 * (size_t)m + 2] == c->h_anchor[2];
     std::vector<char> used(P, 0);
@@ -529,6 +567,19 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
   AIM_TRY(upload((void**)&c->p64.pnode_w, pw64.data(), pw64.size() * sizeof(double)));
   AIM_TRY(upload((void**)&c->p32.pnode_w, pw32.data(), pw32.size() * sizeof(float)));
   AIM_TRY(upload((void**)&c->p64.lam, c->h_lam.data(), c->h_lam.size() * sizeof(double)));
+  if (cfie) {
+    std::vector<float> lamM32(c->h_lamM.size());
+    for (size_t i = 0; i < lamM32.size(); ++i) lamM32[i] = (float)c->h_lamM[i];
+    AIM_TRY(upload((void**)&c->p64.lamM, c->h_lamM.data(), c->h_lamM.size() * sizeof(double)));
+    AIM_TRY(upload((void**)&c->p32.lamM, lamM32.data(), lamM32.size() * sizeof(float)));
+    std::vector<double> nv(3 * (size_t)T.nt);
+    for (int t = 0; t < T.nt; ++t) {
+      nv[3 * t] = nrm[t].x;
+      nv[3 * t + 1] = nrm[t].y;
+      nv[3 * t + 2] = nrm[t].z;
+    }
+    AIM_TRY(up(&c->tri_nrm, nv));
+  }
   AIM_TRY(upload((void**)&c->p32.lam, lam32.data(), lam32.size() * sizeof(float)));
   AIM_TRY(upload((void**)&c->p64.near_val, c->h_near_val.data(), c->h_near_val.size() * sizeof(double)));
   AIM_TRY(upload((void**)&c->p32.near_val, nv32.data(), nv32.size() * sizeof(float)));
