@@ -368,13 +368,13 @@ def run_serve(args):
     torch.cuda.set_device(0)
     plates, spheres = SERVE_SIZES[args.serve_sizes]
     cap_reqs = serve.make_stream(args.requests, rate=1.0, seed=2, plate_sides=plates, sphere_radii=spheres,
-                                 max_rhs=args.serve_max_rhs)
+                                 max_rhs=args.serve_max_rhs, sphere_cfie_alpha=args.serve_cfie)
     srv = serve.Server(slots=args.slots)
     res, span = srv.run(cap_reqs, realtime=False)
     cap = serve.summarize(res, span)
     rate = 0.7 * cap["solves_per_s"]
     reqs = serve.make_stream(args.requests, rate=rate, seed=1, plate_sides=plates, sphere_radii=spheres,
-                             max_rhs=args.serve_max_rhs)
+                             max_rhs=args.serve_max_rhs, sphere_cfie_alpha=args.serve_cfie)
     srv = serve.Server(slots=args.slots)
     t0 = time.perf_counter()
     with ClockSampler(0) as clk:
@@ -388,8 +388,9 @@ def run_serve(args):
         "n_gpus": 1,
         "higher_is_better": True,
         "data": "synthetic",
-        "config": {"workload": f"serving stream ({args.serve_sizes} sizes): plates {plates} lambda, spheres {spheres} "
-                               f"lambda, 1..{args.serve_max_rhs} RHS, Poisson seed 1 at 0.7 x capacity",
+        "config": {"workload": f"serving stream ({args.serve_sizes} sizes): plates {plates} lambda (EFIE), spheres "
+                               f"{spheres} lambda ({'CFIE alpha %g' % args.serve_cfie if args.serve_cfie < 1 else 'EFIE'}), "
+                               f"1..{args.serve_max_rhs} RHS, Poisson seed 1 at 0.7 x capacity",
                    "requests": args.requests, "slots": args.slots},
         "p50_s": summ["p50_s"],
         "p99_s": summ["p99_s"],
@@ -768,6 +769,8 @@ def main():
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-max-rhs", type=int, default=16)
+    ap.add_argument("--serve-cfie", type=float, default=0.6,
+                    help="alpha of the CFIE the spheres of the serving stream are solved with (1: EFIE)")
     args = ap.parse_args()
     if args.sweep:
         return run_sweep(args)

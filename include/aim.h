@@ -185,8 +185,10 @@ int aim_solve(aim_ctx* ctx, const void* V_dev, void* X_dev, int nrhs, double tol
 int aim_rcs(aim_ctx* ctx, const void* X_dev, int nrhs, int ndir, const double* theta,
             const double* phi, double* sig_tt, double* sig_pp);
 
-/* Bytes of device memory a context for this mesh would hold (estimate, +-10 %). */
-int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int max_rhs, size_t* bytes);
+/* Bytes of device memory a context for this mesh would hold (estimate, +-10 %);
+ * cfie_alpha as in aim_opts (1: EFIE; < 1 adds the MFIE arrays). */
+int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int max_rhs, double cfie_alpha,
+                  size_t* bytes);
 
 /*
  * Copy internal setup arrays to host memory for inspection and testing.

@@ -242,11 +242,12 @@ def aim_rcs(ctx, X, theta, phi):
     return stt, spp
 
 
-def aim_footprint(verts, tris, h, M=2, near_radius=None, max_rhs=1):
+def aim_footprint(verts, tris, h, M=2, near_radius=None, max_rhs=1, cfie_alpha=1.0):
     mesh, keep = _mesh(verts, tris)
     b = C.c_size_t()
     r = 3.0 * h if near_radius is None else float(near_radius)
-    check(load().aim_footprint(C.byref(mesh), float(h), int(M), r, int(max_rhs), C.byref(b)), "aim_footprint")
+    check(load().aim_footprint(C.byref(mesh), float(h), int(M), r, int(max_rhs), float(cfie_alpha), C.byref(b)),
+          "aim_footprint")
     return int(b.value)
 
 

@@ -261,8 +261,9 @@ int aim_rcs(aim_ctx* ctx, const void* X_dev, int nrhs, int ndir, const double* t
   return rcs(ctx, (const double2*)X_dev, nrhs, ndir, theta, phi, sig_tt, sig_pp);
 }
 
-int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int max_rhs, size_t* bytes) {
-  if (!mesh || !bytes || !(h > 0.0) || M < 1 || M > 5 || max_rhs < 1) {
+int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int max_rhs, double cfie_alpha,
+                  size_t* bytes) {
+  if (!mesh || !bytes || !(h > 0.0) || M < 1 || M > 5 || max_rhs < 1 || !(cfie_alpha > 0.0 && cfie_alpha <= 1.0)) {
     set_error("aim_footprint: bad arguments");
     return AIM_EINVAL;
   }
@@ -298,6 +299,8 @@ int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int
   b += (double)N * 4 * S * 8 * 2 + (double)nnz * 16;                   // float-float weights and near values
   if (max_rhs >= kRhsLanesMin) b += (double)max_rhs * (4.0 * nc + N) * 16;  // RHS-minor copies of Phi and x
   b += (double)mesh->nt * 60 * (144 + 12) + (double)nnz * 56;          // near-fill scratch at setup (peak)
+  if (cfie_alpha < 1.0)  // MFIE weights in three precisions, MFIE pair blocks and halves at setup
+    b += (double)N * 3 * S * (8 + 4 + 8) + (double)mesh->nt * 60 * 144 + (double)nnz * 32;
   *bytes = (size_t)b;
   return AIM_OK;
 }

@@ -47,6 +47,7 @@ class Request:
     arrival: float = 0.0  # seconds after the stream start
     rcs_dirs: tuple = None  # optional (theta, phi) arrays
     label: str = ""
+    cfie_alpha: float = 1.0  # < 1: CFIE (closed bodies only)
 
 
 @dataclasses.dataclass
@@ -135,7 +136,8 @@ class Server:
             with torch.cuda.stream(stream):
                 nrhs = len(req.khat)
                 ctx = aim_setup(req.verts, req.tris, req.k, req.h, M=req.M, near_radius=req.near_radius,
-                                precision=self.precision, max_rhs=nrhs, stream=stream.cuda_stream)
+                                precision=self.precision, max_rhs=nrhs, stream=stream.cuda_stream,
+                                cfie_alpha=req.cfie_alpha)
                 try:
                     V = aim_rhs_planewave(ctx, req.khat, req.pol)
                     X, info = aim_solve(ctx, V, req.tol, raise_on_noconv=False)
@@ -152,7 +154,7 @@ class Server:
                           error=repr(e))
 
     def _footprint(self, req):
-        return aim_footprint(req.verts, req.tris, req.h, req.M, req.near_radius, len(req.khat))
+        return aim_footprint(req.verts, req.tris, req.h, req.M, req.near_radius, len(req.khat), req.cfie_alpha)
 
     # -------------------------------------------------------------- driver
     def run(self, requests, realtime=True):
@@ -195,12 +197,14 @@ def summarize(results, makespan):
 
 
 def make_stream(n_requests, rate, seed=1, plate_sides=(2, 4, 8, 16, 32), sphere_radii=(1, 2, 4, 8), max_rhs=16,
-                theta_max_deg=80.0):
+                theta_max_deg=80.0, sphere_cfie_alpha=1.0):
     """Synthetic request stream: Poisson arrivals at ``rate`` per second.
 
     Draw order per request: inter-arrival time, kind (plate or sphere, 50/50),
     size, number of right-hand sides (uniform 1..max_rhs), then the incidence
-    angles and polarisations (``aim_inputs.random_incidence``).
+    angles and polarisations (``aim_inputs.random_incidence``).  Spheres are
+    solved with CFIE when ``sphere_cfie_alpha`` < 1 (Section 2.2 uses 0.6 for
+    closed bodies); plates are open and always take the EFIE.
     """
     from aim_inputs import icosphere_frequency, icosphere_mesh, plate_mesh, random_incidence
 
@@ -220,5 +224,6 @@ def make_stream(n_requests, rate, seed=1, plate_sides=(2, 4, 8, 16, 32), sphere_
         if key not in cache:
             cache[key] = plate_mesh(size, int(round(9 * size))) if plate else icosphere_mesh(size, icosphere_frequency(size))
         v, tr = cache[key]
-        reqs.append(Request(i, v, tr, kh, po, arrival=t, label=f"{'plate' if plate else 'sphere'}{size:g}x{nrhs}"))
+        reqs.append(Request(i, v, tr, kh, po, arrival=t, label=f"{'plate' if plate else 'sphere'}{size:g}x{nrhs}",
+                            cfie_alpha=1.0 if plate else float(sphere_cfie_alpha)))
     return reqs

@@ -102,3 +102,4 @@ def test_footprint_is_host_only(lib):
     b1 = aim_footprint(v, t, 0.1, 2, 0.3, 1)
     b8 = aim_footprint(v, t, 0.1, 2, 0.3, 8)
     assert 0 < b1 < b8
+    assert aim_footprint(v, t, 0.1, 2, 0.3, 1, cfie_alpha=0.6) > b1

@@ -88,3 +88,15 @@ def test_poisson_stream_draws_are_seeded():
     assert [r.label for r in a] == [r.label for r in b]
     assert all(1 <= len(r.khat) <= 3 for r in a)
     assert np.all(np.diff([r.arrival for r in a]) > 0)
+
+
+def test_cfie_is_requested_for_spheres_only():
+    """The stream's closed bodies (spheres) take the CFIE alpha; plates are open
+    and stay on the EFIE; the draws do not depend on alpha."""
+    a = serve.make_stream(12, rate=2.0, seed=3, plate_sides=(1,), sphere_radii=(0.5,), max_rhs=2,
+                          sphere_cfie_alpha=0.6)
+    b = serve.make_stream(12, rate=2.0, seed=3, plate_sides=(1,), sphere_radii=(0.5,), max_rhs=2)
+    assert [r.label for r in a] == [r.label for r in b]
+    assert {r.cfie_alpha for r in a if r.label.startswith("plate")} == {1.0}
+    assert {r.cfie_alpha for r in a if r.label.startswith("sphere")} == {0.6}
+    assert {r.cfie_alpha for r in b} == {1.0}
