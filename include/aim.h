@@ -253,11 +253,22 @@ int aim_probe_fma_peak(int which, double* tflops);
  *   AIM_FFT_FOURSTEP        four-step register kernel (compiled lengths; any
  *                           other length falls back to the Stockham kernel);
  *   AIM_FFT_FOURSTEP_SMALL  four-step with blocks of at most 128 threads
- *                           (the x pass; elsewhere as AIM_FFT_FOURSTEP).
+ *                           (the x pass; elsewhere as AIM_FFT_FOURSTEP);
+ *   AIM_FFT_FOURSTEP_WARP   four-step x pass whose pencils go through the
+ *                           three steps in groups of 1-8 warps, each group
+ *                           with its own barrier (the x pass; elsewhere as
+ *                           AIM_FFT_FOURSTEP).
  * aim_fft_config sets (set != NULL, [5]) and/or reads (get != NULL, [5]) the
  * choices of one precision; get receives them with AUTO resolved by the rule.
  */
-enum { AIM_FFT_AUTO = 0, AIM_FFT_STOCKHAM = 1, AIM_FFT_FOURSTEP = 2, AIM_FFT_FOURSTEP_SMALL = 3 };
+enum {
+  AIM_FFT_AUTO = 0,
+  AIM_FFT_STOCKHAM = 1,
+  AIM_FFT_FOURSTEP = 2,
+  AIM_FFT_FOURSTEP_SMALL = 3,
+  AIM_FFT_FOURSTEP_WARP = 4
+};
+#define AIM_FFT_KERNELS 5 /* AIM_FFT_AUTO .. AIM_FFT_FOURSTEP_WARP */
 #define AIM_FFT_PASSES 5
 int aim_fft_config(aim_ctx* ctx, int precision, const int32_t* set, int32_t* get);
 
@@ -269,7 +280,7 @@ int aim_fft_config(aim_ctx* ctx, int precision, const int32_t* set, int32_t* get
  * frees) one input and one output batch, and the precision's grids like the
  * first aim_matvec.  kernel_out [5] (may be NULL) receives the choices (a
  * planar grid has no z passes: those two keep their setting, untimed);
- * ms_out [5][4] (may be NULL) the mean time in ms of each pass under each
+ * ms_out [5][AIM_FFT_KERNELS] (may be NULL) the mean time in ms of each pass under each
  * AIM_FFT_* value (-1 where not tried).  The profiler's totals and on/off
  * state are left as they were.  Synchronises.
  */

@@ -304,7 +304,8 @@ def aim_probe_fma_peak(which=64):
     return float(t.value)
 
 
-AIM_FFT_AUTO, AIM_FFT_STOCKHAM, AIM_FFT_FOURSTEP, AIM_FFT_FOURSTEP_SMALL = 0, 1, 2, 3
+AIM_FFT_AUTO, AIM_FFT_STOCKHAM, AIM_FFT_FOURSTEP, AIM_FFT_FOURSTEP_SMALL, AIM_FFT_FOURSTEP_WARP = 0, 1, 2, 3, 4
+AIM_FFT_KERNELS = 5
 FFT_PASSES = ("fft_z_fwd", "fft_y_fwd", "fft_x_conv", "fft_y_inv", "fft_z_inv")
 
 
@@ -322,12 +323,12 @@ def aim_fft_config(ctx, precision=AIM_C128, kernels=None):
 
 
 def aim_autotune(ctx, precision=AIM_C128, nrhs=1, reps=3):
-    """Time each FFT kernel per pass, keep the fastest.  Returns (kernels, ms[5][4])."""
+    """Time each FFT kernel per pass, keep the fastest.  Returns (kernels, ms[5][AIM_FFT_KERNELS])."""
     lib = load()
     k = (C.c_int32 * 5)()
-    ms = (C.c_double * 20)()
+    ms = (C.c_double * (5 * AIM_FFT_KERNELS))()
     check(lib.aim_autotune(ctx.handle, int(precision), int(nrhs), int(reps), k, ms), "aim_autotune")
-    return [int(v) for v in k], np.array(list(ms)).reshape(5, 4)
+    return [int(v) for v in k], np.array(list(ms)).reshape(5, AIM_FFT_KERNELS)
 
 
 def rcs_direction_grid(n_theta, n_phi=None):

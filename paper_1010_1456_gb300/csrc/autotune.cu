@@ -71,10 +71,10 @@ static int autotune(aim_ctx* c, int precision, int nrhs, int reps, int32_t* kern
     rc = launch_check(c, "autotune_fill");
   }
   if (ms_out)
-    for (int i = 0; i < AIM_FFT_PASSES * 4; ++i) ms_out[i] = -1.0;
+    for (int i = 0; i < AIM_FFT_PASSES * AIM_FFT_KERNELS; ++i) ms_out[i] = -1.0;
   for (int pass = 0; pass < AIM_FFT_PASSES && rc == AIM_OK; ++pass) {
     if ((pass == 0 || pass == 4) && c->L[2] == 1) continue;  // a planar grid has no z passes
-    const int last = pass == 2 ? AIM_FFT_FOURSTEP_SMALL : AIM_FFT_FOURSTEP;
+    const int last = pass == 2 ? AIM_FFT_FOURSTEP_WARP : AIM_FFT_FOURSTEP;
     int best = AIM_FFT_AUTO;
     double best_ms = 0.0;
     for (int k = AIM_FFT_STOCKHAM; k <= last && rc == AIM_OK; ++k) {
@@ -82,7 +82,7 @@ static int autotune(aim_ctx* c, int precision, int nrhs, int reps, int32_t* kern
       double ms = 0.0;
       rc = time_pass(c, pass, x, y, nrhs, precision, reps, &ms);
       if (rc != AIM_OK) break;
-      if (ms_out) ms_out[pass * 4 + k] = ms;
+      if (ms_out) ms_out[pass * AIM_FFT_KERNELS + k] = ms;
       if (best == AIM_FFT_AUTO || ms < best_ms) {
         best = k;
         best_ms = ms;
@@ -110,8 +110,8 @@ extern "C" int aim_fft_config(aim_ctx* ctx, int precision, const int32_t* set, i
   const int pol = fft_policy_of(precision);
   if (set) {
     for (int i = 0; i < AIM_FFT_PASSES; ++i)
-      if (set[i] < AIM_FFT_AUTO || set[i] > AIM_FFT_FOURSTEP_SMALL) {
-        set_error("aim_fft_config: kernel choices are AIM_FFT_AUTO .. AIM_FFT_FOURSTEP_SMALL");
+      if (set[i] < AIM_FFT_AUTO || set[i] > AIM_FFT_FOURSTEP_WARP) {
+        set_error("aim_fft_config: kernel choices are AIM_FFT_AUTO .. AIM_FFT_FOURSTEP_WARP");
         return AIM_EINVAL;
       }
     for (int i = 0; i < AIM_FFT_PASSES; ++i) ctx->fft_kernel[pol][i] = set[i];

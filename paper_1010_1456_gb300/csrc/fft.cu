@@ -169,9 +169,9 @@ int fft4_strided_p64(aim_ctx*, const char*, bool, const double2*, double2*, cons
                      const double2*);
 int fft4_strided_pff(aim_ctx*, const char*, bool, const float4*, float4*, const StridedArgs4&, int, int,
                      const float4*);
-int fft4_x_p32(aim_ctx*, const char*, float2*, const XArgs4&, int, const float2*, const float2*, int);
-int fft4_x_p64(aim_ctx*, const char*, double2*, const XArgs4&, int, const double2*, const double2*, int);
-int fft4_x_pff(aim_ctx*, const char*, float4*, const XArgs4&, int, const float4*, const float4*, int);
+int fft4_x_p32(aim_ctx*, const char*, float2*, const XArgs4&, int, const float2*, const float2*, int, bool);
+int fft4_x_p64(aim_ctx*, const char*, double2*, const XArgs4&, int, const double2*, const double2*, int, bool);
+int fft4_x_pff(aim_ctx*, const char*, float4*, const XArgs4&, int, const float4*, const float4*, int, bool);
 template <class P> struct Fft4;
 template <> struct Fft4<P32> {
   template <class... A> static int strided(A... a) { return fft4_strided_p32(a...); }
@@ -345,7 +345,8 @@ static int x_pass(aim_ctx* c, const char* name, typename P::S* buf, XArgs a, con
   if (k != AIM_FFT_STOCKHAM) {
     XArgs4 x4{};
     x4.nx = a.nx; x4.Ly = a.rows_y; x4.Lz = a.rows_z; x4.G = a.G; x4.sG = a.sG; x4.hx = a.hx; x4.hy = a.hy;
-    const int rc = Fft4<P>::x(c, name, buf, x4, L, ghat, tw, k == AIM_FFT_FOURSTEP_SMALL ? 128 : 256);
+    const int rc = Fft4<P>::x(c, name, buf, x4, L, ghat, tw, k == AIM_FFT_FOURSTEP_SMALL ? 128 : 256,
+                              k == AIM_FFT_FOURSTEP_WARP);
     if (rc == 1) return AIM_OK;
     if (rc < 0) return -rc;
   }
