@@ -45,7 +45,7 @@ static void free_ctx(aim_ctx* c) {
   profile_free(c);
   cudaFree(c->base); cudaFree(c->near_ptr); cudaFree(c->near_col); cudaFree(c->pnode_ptr); cudaFree(c->pnode_m);
   cudaFree(c->diag); cudaFree(c->dinv64); cudaFree(c->d_verts); cudaFree(c->d_tris); cudaFree(c->rwg_tri);
-  cudaFree(c->rwg_free); cudaFree(c->rwg_len); cudaFree(c->tri_area); cudaFree(c->tri_nrm);
+  cudaFree(c->rwg_free); cudaFree(c->rwg_len); cudaFree(c->tri_area); cudaFree(c->tri_nrm); cudaFree(c->pgroups);
   delete c;
 }
 

@@ -155,6 +155,13 @@ struct aim_ctx {
   // problem
   int N = 0, M = 2, S = 27;  // S: stencil nodes per basis function ((M+1)^3, or (M+1)^2 on a planar grid)
   int planar = 0;            // grid reduced to the one z plane that holds every nonzero weight
+  // Projection over node groups: the projection writes only the listed
+  // 8-node groups (those with entries) into grid0, which was zeroed once, and
+  // the inverse z pass leaves Phi in grid2 so grid0 keeps its zeros (grids
+  // with z passes only)
+  int sparse_proj = 0;
+  int32_t* pgroups = nullptr;  // [ngroups] indices g of the groups [8g, 8g + 8) with entries
+  int64_t ngroups = 0;
   double alpha = 1.0;        // CFIE weight of the EFIE (1: EFIE)
   int kk0 = 0;               // that plane's offset in the stencil
   double k = 0, h = 0, radius = 0;
@@ -241,6 +248,8 @@ int convert_c128_to_c64(aim_ctx* c, const double2* in, float2* out, int64_t coun
 int convert_c64_to_c128(aim_ctx* c, const float2* in, double2* out, int64_t count);
 // fft.cu
 // grid0 (Q) -> grid0 (Phi) of each precision, G = 4 * nrhs grids
+// Phi's grid: grid2 for a context that projects over node groups, else grid0.
+template <class T> inline T* phi_grid(const aim_ctx* c, T* g0, T* g2) { return c->sparse_proj ? g2 : g0; }
 int fft_convolve_c64(aim_ctx* c, int G);
 int fft_convolve_c128(aim_ctx* c, int G);
 int fft_convolve_ff(aim_ctx* c, int G);

@@ -355,7 +355,7 @@ static int x_pass(aim_ctx* c, const char* name, typename P::S* buf, XArgs a, con
 
 template <class P>
 static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P::S* g2, const typename P::S* ghat,
-                    typename P::S* const* tw, int G) {
+                    typename P::S* const* tw, int G, typename P::S* phi) {
   const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
   const int Lx = c->L[0], Ly = c->L[1], Lz = c->L[2];
   const FftPlan* pd = c->plan_dev;
@@ -390,27 +390,27 @@ static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P
     a.sG_out = (long long)Lz * ny * nx; a.sA_out = (long long)ny * nx; a.sP_out = nx;
     AIM_TRY((strided_pass<P, true>(c, 3, "fft_y_inv", g2, gz, a, G, pd + 1, Ly, tw[1])));
   }
-  if (zpass) {  // z inverse: g1 -> g0 [G][nz][ny][nx]
+  if (zpass) {  // z inverse: g1 -> phi [G][nz][ny][nx] (g0, or g2 when grid0 keeps the projection's zeros)
     StridedArgs a{};
     a.n_in = Lz; a.n_out = nz; a.X = nx; a.A = ny;
     a.sG_in = (long long)Lz * ny * nx; a.sA_in = nx; a.sP_in = (long long)ny * nx;
     a.sG_out = (long long)nz * ny * nx; a.sA_out = nx; a.sP_out = (long long)ny * nx;
-    AIM_TRY((strided_pass<P, true>(c, 4, "fft_z_inv", g1, g0, a, G, pd + 2, Lz, tw[2])));
+    AIM_TRY((strided_pass<P, true>(c, 4, "fft_z_inv", g1, phi, a, G, pd + 2, Lz, tw[2])));
   }
   return AIM_OK;
 }
 
 int fft_convolve_c64(aim_ctx* c, int G) {
   PrecData<float>& p = c->p32;
-  return convolve<P32>(c, p.grid0, p.grid1, p.grid2, p.ghat, p.tw, G);
+  return convolve<P32>(c, p.grid0, p.grid1, p.grid2, p.ghat, p.tw, G, phi_grid(c, p.grid0, p.grid2));
 }
 int fft_convolve_c128(aim_ctx* c, int G) {
   PrecData<double>& p = c->p64;
-  return convolve<P64>(c, p.grid0, p.grid1, p.grid2, p.ghat, p.tw, G);
+  return convolve<P64>(c, p.grid0, p.grid1, p.grid2, p.ghat, p.tw, G, phi_grid(c, p.grid0, p.grid2));
 }
 int fft_convolve_ff(aim_ctx* c, int G) {
   FFData& p = c->pff;
-  return convolve<PFF>(c, p.grid0, p.grid1, p.grid2, p.ghat, p.tw, G);
+  return convolve<PFF>(c, p.grid0, p.grid1, p.grid2, p.ghat, p.tw, G, phi_grid(c, p.grid0, p.grid2));
 }
 
 // ------------------------------------------------------------------ Ghat
@@ -497,6 +497,6 @@ namespace aim {
 // Complex64 convolution on caller-provided pass buffers (used by the
 // product variant that allocates nothing; same kernels and launch shapes).
 int fft_convolve_c64_bufs(aim_ctx* c, int G, float2* g0, float2* g1, float2* g2) {
-  return convolve<P32>(c, g0, g1, g2, c->p32.ghat, c->p32.tw, G);
+  return convolve<P32>(c, g0, g1, g2, c->p32.ghat, c->p32.tw, G, g0);
 }
 }  // namespace aim

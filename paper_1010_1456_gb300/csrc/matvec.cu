@@ -61,45 +61,95 @@ __device__ __forceinline__ W4<double> load_w4(const double* p, int e) {
   return W4<double>{a.x, a.y, b.x, b.y};
 }
 
-// 4 lanes per grid node: the lanes take every fourth entry of the node's list
-// (adjacent lanes read adjacent entries) and combine with warp shuffles.
-template <class MD>
+// Warp tasks of the projection: task t is the 8 consecutive nodes of group
+// g = groups[t] (or g = t when every group is a task), lane slot s of the
+// warp's 8 takes node 8 g + s.  bounds() loads a node's entry range, empty for
+// a node past the grid or a task past the end.
+struct ProjTasks {
+  const int32_t* groups;
+  long long ntask, Nc;
+  int slot;
+  __device__ long long node(long long t) const { return 8LL * (groups ? (long long)groups[t] : t) + slot; }
+  __device__ void bounds(const int32_t* __restrict__ ptr, long long t, int* e0, int* e1) const {
+    *e0 = *e1 = 0;
+    if (t < ntask) {
+      const long long u = node(t);
+      if (u < Nc) {
+        *e0 = ptr[u];
+        *e1 = ptr[u + 1];
+      }
+    }
+  }
+};
+
+// One warp per task of 8 nodes, 4 lanes per node: the lanes take every
+// fourth entry of the node's list (adjacent lanes read adjacent entries) and
+// combine with warp shuffles.  Without a group list every group is a task
+// and a warp whose 8 nodes have no entries only writes their zeros; with
+// one, the unlisted groups are never written (they hold zeros from the
+// start).  The next task's list bounds are loaded while the current one is
+// summed, and the right-hand sides go in chunks of BC: an entry's weights
+// and column are loaded once per chunk and its BC gathers of x are
+// independent loads.
+template <class MD, int BC>
 __global__ void __launch_bounds__(256) proj_gather(const cplx<typename MD::R>* __restrict__ x, typename MD::S* __restrict__ Q,
                                                    const int32_t* __restrict__ ptr, const int32_t* __restrict__ mm,
-                                                   const typename MD::R* __restrict__ w, int N, long long Nc, int nrhs) {
+                                                   const typename MD::R* __restrict__ w, int N, long long Nc, int nrhs,
+                                                   const int32_t* __restrict__ groups, long long ntask) {
   using R = typename MD::R;
   using C = cplx<R>;
   const int lane = threadIdx.x & 3;
-  const long long stride = ((long long)gridDim.x * blockDim.x) >> 2;
-  for (long long u0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 2;; u0 += stride) {
-    // the warp leaves together, so every lane takes part in the shuffles below
+  const ProjTasks tasks{groups, ntask, Nc, (int)((threadIdx.x & 31) >> 2)};
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int pe0, pe1;
+  tasks.bounds(ptr, t, &pe0, &pe1);
+  // t is the same for the whole warp, so every lane takes part in the shuffles below
+  for (; t < ntask; t += nwarps) {
+    const long long u0 = tasks.node(t);
     const bool live = u0 < Nc;
-    if (!__any_sync(0xffffffffu, live)) break;
     const long long u = live ? u0 : Nc - 1;
-    const int e0 = ptr[u], e1 = ptr[u + 1];
-    for (int b = 0; b < nrhs; ++b) {
-      C a0 = cmake<C>(0, 0), a1 = a0, a2 = a0, a3 = a0;
-      const C* xb = x + (long long)b * N;
+    const int e0 = pe0, e1 = pe1;
+    tasks.bounds(ptr, t + nwarps, &pe0, &pe1);
+    if (__all_sync(0xffffffffu, e0 == e1)) {  // the warp's 8 nodes are empty: zeros, no reduction
+      if (live)
+        for (int b = 0; b < nrhs; ++b) Q[(long long)b * 4 * Nc + (long long)lane * Nc + u] = MD::put(cmake<C>(0, 0));
+      continue;
+    }
+    for (int b0 = 0; b0 < nrhs; b0 += BC) {
+      C a[BC][4];
+#pragma unroll
+      for (int q = 0; q < BC; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a[q][c] = cmake<C>(0, 0);
       for (int e = e0 + lane; e < e1; e += 4) {
         const W4<R> ww = load_w4(w, e);
-        const C xv = xb[mm[e]];
-        a0.x += ww.x * xv.x; a0.y += ww.x * xv.y;
-        a1.x += ww.y * xv.x; a1.y += ww.y * xv.y;
-        a2.x += ww.z * xv.x; a2.y += ww.z * xv.y;
-        a3.x += ww.w * xv.x; a3.y += ww.w * xv.y;
+        const C* xc = x + mm[e];
+        C xv[BC];
+#pragma unroll
+        for (int q = 0; q < BC; ++q) xv[q] = b0 + q < nrhs ? xc[(long long)(b0 + q) * N] : cmake<C>(0, 0);
+#pragma unroll
+        for (int q = 0; q < BC; ++q) {
+          a[q][0].x += ww.x * xv[q].x; a[q][0].y += ww.x * xv[q].y;
+          a[q][1].x += ww.y * xv[q].x; a[q][1].y += ww.y * xv[q].y;
+          a[q][2].x += ww.z * xv[q].x; a[q][2].y += ww.z * xv[q].y;
+          a[q][3].x += ww.w * xv[q].x; a[q][3].y += ww.w * xv[q].y;
+        }
       }
 #pragma unroll
-      for (int o = 1; o < 4; o <<= 1) {
-        a0.x += __shfl_xor_sync(0xffffffffu, a0.x, o, 4); a0.y += __shfl_xor_sync(0xffffffffu, a0.y, o, 4);
-        a1.x += __shfl_xor_sync(0xffffffffu, a1.x, o, 4); a1.y += __shfl_xor_sync(0xffffffffu, a1.y, o, 4);
-        a2.x += __shfl_xor_sync(0xffffffffu, a2.x, o, 4); a2.y += __shfl_xor_sync(0xffffffffu, a2.y, o, 4);
-        a3.x += __shfl_xor_sync(0xffffffffu, a3.x, o, 4); a3.y += __shfl_xor_sync(0xffffffffu, a3.y, o, 4);
-      }
-      if (live) {
-        typename MD::S* Qb = Q + (long long)b * 4 * Nc;
-        // lane c writes component c (one conversion per value)
-        const C val = lane == 0 ? a0 : lane == 1 ? a1 : lane == 2 ? a2 : a3;
-        Qb[(long long)lane * Nc + u] = MD::put(val);
+      for (int q = 0; q < BC; ++q) {
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            a[q][c].x += __shfl_xor_sync(0xffffffffu, a[q][c].x, o, 4);
+            a[q][c].y += __shfl_xor_sync(0xffffffffu, a[q][c].y, o, 4);
+          }
+        if (live && b0 + q < nrhs) {
+          // lane c writes component c (one conversion per value)
+          const C val = lane == 0 ? a[q][0] : lane == 1 ? a[q][1] : lane == 2 ? a[q][2] : a[q][3];
+          Q[(long long)(b0 + q) * 4 * Nc + (long long)lane * Nc + u] = MD::put(val);
+        }
       }
     }
   }
@@ -415,52 +465,77 @@ __global__ void k_w4_to_ff(const double* __restrict__ in, float4* __restrict__ o
   }
 }
 
-// Projection: 4 lanes per grid node, as proj_gather.
+// Projection with float-float arithmetic: the tasks, layout and order of
+// proj_gather (4 lanes per node, empty warps write zeros, next bounds
+// prefetched, right-hand sides in chunks of BC).
+template <int BC>
 __global__ void __launch_bounds__(256) proj_gather_ff(const float4* __restrict__ x, float4* __restrict__ Q,
                                                       const int32_t* __restrict__ ptr, const int32_t* __restrict__ mm,
-                                                      const float4* __restrict__ w, int N, long long Nc, int nrhs) {
+                                                      const float4* __restrict__ w, int N, long long Nc, int nrhs,
+                                                      const int32_t* __restrict__ groups, long long ntask) {
   const int lane = threadIdx.x & 3;
-  const long long stride = ((long long)gridDim.x * blockDim.x) >> 2;
-  for (long long u0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 2;; u0 += stride) {
+  const ProjTasks tasks{groups, ntask, Nc, (int)((threadIdx.x & 31) >> 2)};
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int pe0, pe1;
+  tasks.bounds(ptr, t, &pe0, &pe1);
+  for (; t < ntask; t += nwarps) {
+    const long long u0 = tasks.node(t);
     const bool live = u0 < Nc;
-    if (!__any_sync(0xffffffffu, live)) break;
     const long long u = live ? u0 : Nc - 1;
-    const int e0 = ptr[u], e1 = ptr[u + 1];
-    for (int b = 0; b < nrhs; ++b) {
-      ff a[4][2];
+    const int e0 = pe0, e1 = pe1;
+    tasks.bounds(ptr, t + nwarps, &pe0, &pe1);
+    if (__all_sync(0xffffffffu, e0 == e1)) {  // the warp's 8 nodes are empty: zeros, no reduction
+      if (live)
+        for (int b = 0; b < nrhs; ++b) Q[(long long)b * 4 * Nc + (long long)lane * Nc + u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    for (int b0 = 0; b0 < nrhs; b0 += BC) {
+      ff a[BC][4][2];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) a[c][0] = a[c][1] = ffv(0.f, 0.f);
-      const float4* xb = x + (long long)b * N;
+      for (int q = 0; q < BC; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a[q][c][0] = a[q][c][1] = ffv(0.f, 0.f);
       for (int e = e0 + lane; e < e1; e += 4) {
         const float4 wh = w[2 * e], wl = w[2 * e + 1];
-        const float4 xv = xb[mm[e]];
-        const ff xr = ffv(xv.x, xv.y), xi = ffv(xv.z, xv.w);
+        const float4* xc = x + mm[e];
+        float4 xv[BC];
+#pragma unroll
+        for (int q = 0; q < BC; ++q) xv[q] = b0 + q < nrhs ? xc[(long long)(b0 + q) * N] : make_float4(0.f, 0.f, 0.f, 0.f);
         const ff wc[4] = {ffv(wh.x, wl.x), ffv(wh.y, wl.y), ffv(wh.z, wl.z), ffv(wh.w, wl.w)};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          a[c][0] = ff_mad(wc[c], xr, a[c][0]);
-          a[c][1] = ff_mad(wc[c], xi, a[c][1]);
+        for (int q = 0; q < BC; ++q) {
+          const ff xr = ffv(xv[q].x, xv[q].y), xi = ffv(xv[q].z, xv[q].w);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            a[q][c][0] = ff_mad(wc[c], xr, a[q][c][0]);
+            a[q][c][1] = ff_mad(wc[c], xi, a[q][c][1]);
+          }
         }
       }
 #pragma unroll
-      for (int o = 1; o < 4; o <<= 1)
+      for (int q = 0; q < BC; ++q) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
+        for (int o = 1; o < 4; o <<= 1)
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const ff t = ffv(__shfl_xor_sync(0xffffffffu, a[c][q].hi, o, 4), __shfl_xor_sync(0xffffffffu, a[c][q].lo, o, 4));
-            a[c][q] = ff_add(a[c][q], t);
-          }
-      if (live) {
-        // lane c writes component c
-        ff re = a[0][0], im = a[0][1];
+          for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int c = 1; c < 4; ++c)
-          if (lane == c) {
-            re = a[c][0];
-            im = a[c][1];
-          }
-        Q[(long long)b * 4 * Nc + (long long)lane * Nc + u] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            for (int r = 0; r < 2; ++r) {
+              const ff t = ffv(__shfl_xor_sync(0xffffffffu, a[q][c][r].hi, o, 4),
+                               __shfl_xor_sync(0xffffffffu, a[q][c][r].lo, o, 4));
+              a[q][c][r] = ff_add(a[q][c][r], t);
+            }
+        if (live && b0 + q < nrhs) {
+          // lane c writes component c
+          ff re = a[q][0][0], im = a[q][0][1];
+#pragma unroll
+          for (int c = 1; c < 4; ++c)
+            if (lane == c) {
+              re = a[q][c][0];
+              im = a[q][c][1];
+            }
+          Q[(long long)(b0 + q) * 4 * Nc + (long long)lane * Nc + u] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
       }
     }
   }
@@ -537,6 +612,9 @@ __global__ void __launch_bounds__(256) interp_near_ff(const float4* __restrict__
   }
 }
 
+// Warp tasks of the projection: the listed groups, or every 8-node group.
+static long long proj_tasks(const aim_ctx* c, long long Nc) { return c->sparse_proj ? c->ngroups : (Nc + 7) / 8; }
+
 static int ensure_ff_arrays(aim_ctx* c) {
   FFData& p = c->pff;
   if (p.pnode_w) return AIM_OK;
@@ -574,10 +652,18 @@ static int run_product_ff(aim_ctx* c, const double2* x, double2* y, int nrhs) {
     AIM_TRY(launch_check(c, "x_to_ff"));
   }
   {
-    const int blocks = (int)std::min<long long>((4 * Nc + 255) / 256, 152LL * 16);
-    AIM_LAUNCH(c, "proj_gather",
-               (proj_gather_ff<<<blocks, 256, 0, c->stream>>>(p.xff, p.grid0, c->pnode_ptr, c->pnode_m, p.pnode_w, c->N,
-                                                             Nc, nrhs)));
+    const long long ntask = proj_tasks(c, Nc);
+    const int blocks = (int)std::min<long long>((ntask + 7) / 8, 152LL * 16);
+    const int32_t* groups = c->sparse_proj ? c->pgroups : nullptr;
+    const auto go = [&](auto bc) {
+      AIM_LAUNCH(c, "proj_gather",
+                 (proj_gather_ff<decltype(bc)::value><<<blocks, 256, 0, c->stream>>>(p.xff, p.grid0, c->pnode_ptr,
+                                                                                      c->pnode_m, p.pnode_w, c->N, Nc,
+                                                                                      nrhs, groups, ntask)));
+    };
+    if (nrhs == 1) go(std::integral_constant<int, 1>{});
+    else if (nrhs == 2) go(std::integral_constant<int, 2>{});
+    else go(std::integral_constant<int, 4>{});
     AIM_TRY(launch_check(c, "proj_gather"));
   }
   AIM_TRY(fft_convolve_ff(c, 4 * nrhs));
@@ -590,7 +676,7 @@ static int run_product_ff(aim_ctx* c, const double2* x, double2* y, int nrhs) {
     const float2 fmf = make_float2(fmh, (float)(fm - (double)fmh));
     const auto go = [&](auto mf) {
       AIM_LAUNCH(c, "interp_near",
-             (interp_near_ff<decltype(mf)::value><<<blocks, 256, 0, c->stream>>>(p.grid0, p.xff, y, p.lam, c->base, c->near_ptr,
+             (interp_near_ff<decltype(mf)::value><<<blocks, 256, 0, c->stream>>>(phi_grid(c, p.grid0, p.grid2), p.xff, y, p.lam, c->base, c->near_ptr,
                                                                 c->near_col, p.near_val, c->N, Nc, c->n[0], c->n[1],
                                                                 nrhs, fvec, frho, c->S, c->M + 1, p.lamM, fmf)));
     };
@@ -647,9 +733,16 @@ static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename 
       AIM_TRY(launch_check(c, "proj_gather"));
     }
   } else {
-    const int blocks = (int)std::min<long long>((4 * Nc + 255) / 256, 152LL * 16);
-    AIM_LAUNCH(c, "proj_gather",
-               proj_gather<MD><<<blocks, 256, 0, c->stream>>>(x, grid0, c->pnode_ptr, c->pnode_m, pw, c->N, Nc, nrhs));
+    const long long ntask = proj_tasks(c, Nc);
+    const int blocks = (int)std::min<long long>((ntask + 7) / 8, 152LL * 16);
+    const int32_t* groups = c->sparse_proj ? c->pgroups : nullptr;
+    const auto go = [&](auto bc) {
+      AIM_LAUNCH(c, "proj_gather", (proj_gather<MD, decltype(bc)::value><<<blocks, 256, 0, c->stream>>>(
+                                       x, grid0, c->pnode_ptr, c->pnode_m, pw, c->N, Nc, nrhs, groups, ntask)));
+    };
+    if (nrhs == 1) go(std::integral_constant<int, 1>{});
+    else if (nrhs == 2) go(std::integral_constant<int, 2>{});
+    else go(std::integral_constant<int, 4>{});
     AIM_TRY(launch_check(c, "proj_gather"));
   }
   AIM_TRY(convolve(c, 4 * nrhs));
@@ -703,6 +796,7 @@ int ensure_grids(aim_ctx* c, int precision) {
       AIM_CUDA_TRY(cudaMalloc(&p.grid0, sizeof(float2) * e0));
       AIM_CUDA_TRY(cudaMalloc(&p.grid1, sizeof(float2) * e1));
       AIM_CUDA_TRY(cudaMalloc(&p.grid2, sizeof(float2) * e2));
+      if (c->sparse_proj) AIM_CUDA_TRY(cudaMemsetAsync(p.grid0, 0, sizeof(float2) * e0, c->stream));
     }
   } else if (precision == AIM_C128_F64) {
     PrecData<double>& p = c->p64;
@@ -710,6 +804,7 @@ int ensure_grids(aim_ctx* c, int precision) {
       AIM_CUDA_TRY(cudaMalloc(&p.grid0, sizeof(double2) * e0));
       AIM_CUDA_TRY(cudaMalloc(&p.grid1, sizeof(double2) * e1));
       AIM_CUDA_TRY(cudaMalloc(&p.grid2, sizeof(double2) * e2));
+      if (c->sparse_proj) AIM_CUDA_TRY(cudaMemsetAsync(p.grid0, 0, sizeof(double2) * e0, c->stream));
     }
   } else {
     FFData& p = c->pff;
@@ -717,6 +812,7 @@ int ensure_grids(aim_ctx* c, int precision) {
       AIM_CUDA_TRY(cudaMalloc(&p.grid0, sizeof(float4) * e0));
       AIM_CUDA_TRY(cudaMalloc(&p.grid1, sizeof(float4) * e1));
       AIM_CUDA_TRY(cudaMalloc(&p.grid2, sizeof(float4) * e2));
+      if (c->sparse_proj) AIM_CUDA_TRY(cudaMemsetAsync(p.grid0, 0, sizeof(float4) * e0, c->stream));
     }
   }
   return AIM_OK;
@@ -742,10 +838,12 @@ int prepare_product(aim_ctx* c, int precision) {
 int matvec(aim_ctx* c, const void* x, void* y, int nrhs, int precision) {
   AIM_TRY(ensure_grids(c, precision));
   if (precision == AIM_C64)
-    return run_product<M32, M32>(c, (const float2*)x, (float2*)y, nrhs, c->p32.grid0, c->p32.grid0, c->p32.pnode_w,
+    return run_product<M32, M32>(c, (const float2*)x, (float2*)y, nrhs, c->p32.grid0,
+                                 phi_grid(c, c->p32.grid0, c->p32.grid2), c->p32.pnode_w,
                                  c->p32.lam, c->p32.near_val, fft_convolve_c64);
   if (precision == AIM_C128_F64)
-    return run_product<M64, M64>(c, (const double2*)x, (double2*)y, nrhs, c->p64.grid0, c->p64.grid0,
+    return run_product<M64, M64>(c, (const double2*)x, (double2*)y, nrhs, c->p64.grid0,
+                                 phi_grid(c, c->p64.grid0, c->p64.grid2),
                                  c->p64.pnode_w, c->p64.lam, c->p64.near_val, fft_convolve_c128);
   return run_product_ff(c, (const double2*)x, (double2*)y, nrhs);
 }
@@ -779,10 +877,17 @@ namespace aim {
 int matvec_c64_bufs(aim_ctx* c, const float2* x, float2* y, int nrhs, float2* g0, float2* g1, float2* g2) {
   const long long Nc = (long long)c->n[0] * c->n[1] * c->n[2];
   {
-    const int blocks = (int)std::min<long long>((Nc + 255) / 256, 152LL * 16);
-    AIM_LAUNCH(c, "proj_gather",
-               proj_gather<M32><<<blocks, 256, 0, c->stream>>>(x, g0, c->pnode_ptr, c->pnode_m, c->p32.pnode_w, c->N,
-                                                              Nc, nrhs));
+    // every group is a task here: the caller's g0 holds no zeros of ours
+    const long long ntask = (Nc + 7) / 8;
+    const int blocks = (int)std::min<long long>((ntask + 7) / 8, 152LL * 16);
+    const auto go = [&](auto bc) {
+      AIM_LAUNCH(c, "proj_gather", (proj_gather<M32, decltype(bc)::value><<<blocks, 256, 0, c->stream>>>(
+                                       x, g0, c->pnode_ptr, c->pnode_m, c->p32.pnode_w, c->N, Nc, nrhs, nullptr,
+                                       ntask)));
+    };
+    if (nrhs == 1) go(std::integral_constant<int, 1>{});
+    else if (nrhs == 2) go(std::integral_constant<int, 2>{});
+    else go(std::integral_constant<int, 4>{});
     AIM_TRY(launch_check(c, "proj_gather"));
   }
   AIM_TRY(fft_convolve_c64_bufs(c, 4 * nrhs, g0, g1, g2));

@@ -563,6 +563,17 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
   AIM_TRY(up(&c->near_col, c->h_near_col));
   AIM_TRY(up(&c->pnode_ptr, pptr));
   c->h_pnode_ptr = pptr;
+  // With z passes the projection writes only the 8-node groups that hold
+  // entries (most of the box around a closed surface holds none); the rest
+  // of grid0 is zeroed once when the grids are allocated.
+  c->sparse_proj = c->L[2] > 1;
+  if (c->sparse_proj) {
+    std::vector<int32_t> grp;
+    for (long long g = 0; 8 * g < Nc; ++g)
+      if (pptr[std::min(Nc, 8 * g + 8)] > pptr[8 * g]) grp.push_back((int32_t)g);
+    c->ngroups = (int64_t)grp.size();
+    if (!grp.empty()) AIM_TRY(up(&c->pgroups, grp));
+  }
   AIM_TRY(up(&c->pnode_m, pm));
   AIM_TRY(upload((void**)&c->p64.pnode_w, pw64.data(), pw64.size() * sizeof(double)));
   AIM_TRY(upload((void**)&c->p32.pnode_w, pw32.data(), pw32.size() * sizeof(float)));
