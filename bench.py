@@ -58,13 +58,15 @@ def mesh_for(kind, size):
 
 
 # ---------------------------------------------------------------- kernel models
-def kernel_models(N, n, L, nnz, nent, S, nrhs, e, touched=None):
+def kernel_models(N, n, L, nnz, nent, S, nrhs, e, touched=None, projected=None):
     """Algorithmic bytes and flops per launch of each product kernel.
 
     e = bytes per complex value, w = bytes per real weight.  FFT flops use
     the 5 L log2 L convention per length-L transform.  touched = grid nodes
-    that lie in some stencil (the interpolation reads only those; the
-    projection writes every node, zeros included); default all nodes.
+    that lie in some stencil (the interpolation reads only those); projected
+    = grid nodes the projection writes (the nodes of its 8-node groups with
+    entries when the grid keeps the zeros of the others, else every node);
+    both default to all nodes.
     """
     nx, ny, nz = n
     Lx, Ly, Lz = L
@@ -74,7 +76,8 @@ def kernel_models(N, n, L, nnz, nent, S, nrhs, e, touched=None):
     lg = np.log2
     oct_ = (Lx // 2 + 1) * (Ly // 2 + 1) * (Lz // 2 + 1)
     m = {}
-    m["proj_gather"] = (nent * (4 + 4 * w) + (Nc + 1) * 4 + nrhs * N * e + G * Nc * e, 16.0 * nent * nrhs)
+    npj = Nc if projected is None else projected
+    m["proj_gather"] = (nent * (4 + 4 * w) + (npj + 1) * 4 + nrhs * N * e + G * npj * e, 16.0 * nent * nrhs)
     m["fft_z_fwd"] = (G * (Nc + Lz * ny * nx) * e, G * nx * ny * 5.0 * Lz * lg(Lz))
     m["fft_y_fwd"] = (G * (Lz * ny * nx + Lz * Ly * nx) * e, G * nx * Lz * 5.0 * Ly * lg(Ly))
     m["fft_x_conv"] = (2 * G * Lz * Ly * nx * e + oct_ * e, G * Ly * Lz * (10.0 * Lx * lg(Lx) + 6.0 * Lx))
@@ -662,9 +665,14 @@ def run_ours(args, rank, world, local_rank):
     # roofline of the dominant kernel
     pptr = g.aim_export(ctx, g.AIM_EXPORT_PROJ_PTR)
     nent = int(pptr[-1])
-    touched = int(np.count_nonzero(np.diff(pptr)))
+    cnt = np.diff(pptr)
+    touched = int(np.count_nonzero(cnt))
+    # a grid with z passes is projected over its 8-node groups with entries
+    # (fewer than 16 RHS; the many-RHS projection writes every node)
+    groups = int(np.count_nonzero(np.add.reduceat(cnt, np.arange(0, len(cnt), 8))))
+    projected = 8 * groups if (L[2] > 1 and nrhs < 16) else None
     S = 9 if L[2] == 1 else 27  # stencil nodes (M = 2; a planar grid keeps one plane)
-    models = kernel_models(N, n, L, nnz, nent, S, nrhs, e, touched)
+    models = kernel_models(N, n, L, nnz, nent, S, nrhs, e, touched, projected)
     kernels = {k: {"launches": c, "avg_ms": ms / max(c, 1), "share": ms / max(sum(v[1] for v in prof.values()), 1e-30)}
                for k, (c, ms) in prof.items()}
     dom = max(kernels, key=lambda k: kernels[k]["share"])
