@@ -500,7 +500,7 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- our arm
-FFT_KERNEL_NAMES = {1: "stockham", 2: "fourstep", 3: "fourstep_small", 4: "fourstep_warp"}
+FFT_KERNEL_NAMES = {1: "stockham", 2: "fourstep", 3: "fourstep_small", 4: "fourstep_warp", 5: "fourstep_wide"}
 
 
 def fft_kernel_names(g, chosen, L):
@@ -572,7 +572,7 @@ def run_ours(args, rank, world, local_rank):
         chosen, tune_ms = g.aim_autotune(ctx, P, nrhs=nrhs, reps=3)
         tune = {"seconds": round(time.perf_counter() - t0, 2),
                 "kernels": fft_kernel_names(g, chosen, L),
-                "pass_ms": {p_: {FFT_KERNEL_NAMES[k]: round(float(tune_ms[i, k]), 4) for k in (1, 2, 3, 4)
+                "pass_ms": {p_: {FFT_KERNEL_NAMES[k]: round(float(tune_ms[i, k]), 4) for k in (1, 2, 3, 4, 5)
                                  if tune_ms[i, k] > 0} for i, p_ in enumerate(g.FFT_PASSES)}}
     else:
         chosen = g.aim_fft_config(ctx, P)

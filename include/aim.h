@@ -257,6 +257,9 @@ int aim_probe_fma_peak(int which, double* tflops);
  *   AIM_FFT_FOURSTEP_WARP   four-step x pass whose pencils go through the
  *                           three steps in groups of 1-8 warps, each group
  *                           with its own barrier (the x pass; elsewhere as
+ *                           AIM_FFT_FOURSTEP);
+ *   AIM_FFT_FOURSTEP_WIDE   four-step strided pass with twice the columns per
+ *                           block (the z and y passes; on the x pass as
  *                           AIM_FFT_FOURSTEP).
  * aim_fft_config sets (set != NULL, [5]) and/or reads (get != NULL, [5]) the
  * choices of one precision; get receives them with AUTO resolved by the rule.
@@ -266,9 +269,10 @@ enum {
   AIM_FFT_STOCKHAM = 1,
   AIM_FFT_FOURSTEP = 2,
   AIM_FFT_FOURSTEP_SMALL = 3,
-  AIM_FFT_FOURSTEP_WARP = 4
+  AIM_FFT_FOURSTEP_WARP = 4,
+  AIM_FFT_FOURSTEP_WIDE = 5
 };
-#define AIM_FFT_KERNELS 5 /* AIM_FFT_AUTO .. AIM_FFT_FOURSTEP_WARP */
+#define AIM_FFT_KERNELS 6 /* AIM_FFT_AUTO .. AIM_FFT_FOURSTEP_WIDE */
 #define AIM_FFT_PASSES 5
 int aim_fft_config(aim_ctx* ctx, int precision, const int32_t* set, int32_t* get);
 

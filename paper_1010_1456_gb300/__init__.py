@@ -304,8 +304,9 @@ def aim_probe_fma_peak(which=64):
     return float(t.value)
 
 
-AIM_FFT_AUTO, AIM_FFT_STOCKHAM, AIM_FFT_FOURSTEP, AIM_FFT_FOURSTEP_SMALL, AIM_FFT_FOURSTEP_WARP = 0, 1, 2, 3, 4
-AIM_FFT_KERNELS = 5
+(AIM_FFT_AUTO, AIM_FFT_STOCKHAM, AIM_FFT_FOURSTEP, AIM_FFT_FOURSTEP_SMALL, AIM_FFT_FOURSTEP_WARP,
+ AIM_FFT_FOURSTEP_WIDE) = range(6)
+AIM_FFT_KERNELS = 6
 FFT_PASSES = ("fft_z_fwd", "fft_y_fwd", "fft_x_conv", "fft_y_inv", "fft_z_inv")
 
 

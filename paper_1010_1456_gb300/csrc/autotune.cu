@@ -74,10 +74,12 @@ static int autotune(aim_ctx* c, int precision, int nrhs, int reps, int32_t* kern
     for (int i = 0; i < AIM_FFT_PASSES * AIM_FFT_KERNELS; ++i) ms_out[i] = -1.0;
   for (int pass = 0; pass < AIM_FFT_PASSES && rc == AIM_OK; ++pass) {
     if ((pass == 0 || pass == 4) && c->L[2] == 1) continue;  // a planar grid has no z passes
-    const int last = pass == 2 ? AIM_FFT_FOURSTEP_WARP : AIM_FFT_FOURSTEP;
     int best = AIM_FFT_AUTO;
     double best_ms = 0.0;
-    for (int k = AIM_FFT_STOCKHAM; k <= last && rc == AIM_OK; ++k) {
+    for (int k = AIM_FFT_STOCKHAM; k < AIM_FFT_KERNELS && rc == AIM_OK; ++k) {
+      // the x pass has the block-size and warp-group variants, the strided passes the wide one
+      const bool x_only = k == AIM_FFT_FOURSTEP_SMALL || k == AIM_FFT_FOURSTEP_WARP;
+      if (pass == 2 ? k == AIM_FFT_FOURSTEP_WIDE : x_only) continue;
       c->fft_kernel[pol][pass] = k;
       double ms = 0.0;
       rc = time_pass(c, pass, x, y, nrhs, precision, reps, &ms);
@@ -110,8 +112,8 @@ extern "C" int aim_fft_config(aim_ctx* ctx, int precision, const int32_t* set, i
   const int pol = fft_policy_of(precision);
   if (set) {
     for (int i = 0; i < AIM_FFT_PASSES; ++i)
-      if (set[i] < AIM_FFT_AUTO || set[i] > AIM_FFT_FOURSTEP_WARP) {
-        set_error("aim_fft_config: kernel choices are AIM_FFT_AUTO .. AIM_FFT_FOURSTEP_WARP");
+      if (set[i] < AIM_FFT_AUTO || set[i] >= AIM_FFT_KERNELS) {
+        set_error("aim_fft_config: kernel choices are AIM_FFT_AUTO .. AIM_FFT_FOURSTEP_WIDE");
         return AIM_EINVAL;
       }
     for (int i = 0; i < AIM_FFT_PASSES; ++i) ctx->fft_kernel[pol][i] = set[i];

@@ -176,7 +176,7 @@ struct aim_ctx {
   int64_t launches = 0;
   // FFT kernel per arithmetic policy (complex64, native FP64, float-float) and
   // pass (z fwd, y fwd, x, y inv, z inv): AIM_FFT_AUTO, AIM_FFT_STOCKHAM,
-  // AIM_FFT_FOURSTEP, AIM_FFT_FOURSTEP_SMALL or AIM_FFT_FOURSTEP_WARP (set by aim_fft_config and
+  // AIM_FFT_FOURSTEP, AIM_FFT_FOURSTEP_SMALL, AIM_FFT_FOURSTEP_WARP or AIM_FFT_FOURSTEP_WIDE (set by aim_fft_config and
   // aim_autotune).
   int32_t fft_kernel[3][AIM_FFT_PASSES] = {};
   aim::FftPlan plan[3];

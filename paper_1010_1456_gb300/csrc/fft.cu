@@ -164,11 +164,11 @@ using StridedArgs = StridedArgs4;
 // Four-step kernels per policy (fft4_p32.cu, fft4_p64.cu, fft4_pff.cu):
 // 1 launched, 0 no kernel for this length, < 0 minus an error code.
 int fft4_strided_p32(aim_ctx*, const char*, bool, const float2*, float2*, const StridedArgs4&, int, int,
-                     const float2*);
+                     const float2*, bool);
 int fft4_strided_p64(aim_ctx*, const char*, bool, const double2*, double2*, const StridedArgs4&, int, int,
-                     const double2*);
+                     const double2*, bool);
 int fft4_strided_pff(aim_ctx*, const char*, bool, const float4*, float4*, const StridedArgs4&, int, int,
-                     const float4*);
+                     const float4*, bool);
 int fft4_x_p32(aim_ctx*, const char*, float2*, const XArgs4&, int, const float2*, const float2*, int, bool);
 int fft4_x_p64(aim_ctx*, const char*, double2*, const XArgs4&, int, const double2*, const double2*, int, bool);
 int fft4_x_pff(aim_ctx*, const char*, float4*, const XArgs4&, int, const float4*, const float4*, int, bool);
@@ -330,8 +330,9 @@ template <class P> constexpr int policy_index() {
 template <class P, bool INV, class O = typename P::S>
 static int strided_pass(aim_ctx* c, int pass, const char* name, const typename P::S* in, O* out,
                         const StridedArgs& a, int G, const FftPlan* plan_dev, int L, const typename P::S* tw) {
-  if (fft_kernel_for(c, policy_index<P>(), pass) != AIM_FFT_STOCKHAM) {
-    const int rc = Fft4<P>::strided(c, name, INV, in, out, a, G, L, tw);
+  const int k = fft_kernel_for(c, policy_index<P>(), pass);
+  if (k != AIM_FFT_STOCKHAM) {
+    const int rc = Fft4<P>::strided(c, name, INV, in, out, a, G, L, tw, k == AIM_FFT_FOURSTEP_WIDE);
     if (rc == 1) return AIM_OK;
     if (rc < 0) return -rc;
   }

@@ -53,10 +53,13 @@ template <class S, class O> struct OutConv4 {
 
 // Columns per block of the strided kernels for length L: the policy's
 // preferred width, halved while one pencil set would need more than 48 KB of
-// shared memory (so long pencils still leave several blocks per SM).
-template <class P, int L> constexpr int strided_tx() {
-  int tx = P::kTX;
-  while (tx > 4 && (long long)L * tx * (long long)sizeof(typename P::S) > 48 * 1024) tx /= 2;
+// shared memory (so long pencils still leave several blocks per SM).  The
+// wide variant starts from twice that width with a 96 KB limit: longer
+// contiguous runs per pencil row, fewer blocks per SM.
+template <class P, int L, bool WIDE = false> constexpr int strided_tx() {
+  int tx = WIDE ? 2 * P::kTX : P::kTX;
+  const long long cap = (WIDE ? 96 : 48) * 1024;
+  while (tx > 4 && (long long)L * tx * (long long)sizeof(typename P::S) > cap) tx /= 2;
   return tx;
 }
 
@@ -69,12 +72,12 @@ constexpr int odd_row(int n) { return n + (n % 2 == 0 ? 1 : 0); }
 // straight from global memory into registers (samples >= n_in are zero and
 // never read); the only shared-memory round trip is the transpose between
 // the two steps.  Step B writes the first n_out outputs.
-template <class P, bool INV, int L1, int L2, class O>
+template <class P, bool INV, int L1, int L2, class O, bool WIDE = false>
 __global__ void __launch_bounds__(256) fft4_strided(const typename P::S* __restrict__ in, O* __restrict__ out,
                                                     StridedArgs4 a, const typename P::S* __restrict__ twL, int AY) {
   using S = typename P::S;
   using T = typename P::T;
-  constexpr int L = L1 * L2, TX = strided_tx<P, L>();
+  constexpr int L = L1 * L2, TX = strided_tx<P, L, WIDE>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* b = reinterpret_cast<S*>(smem_raw);  // [AY][L1][L2][TX]
   const int x0 = blockIdx.x * TX;

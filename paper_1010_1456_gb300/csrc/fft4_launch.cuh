@@ -12,23 +12,23 @@ constexpr int kNotHandled = -1;
 using Pol = AIM_FFT4_POLICY;
 using S = Pol::S;
 
-template <bool INV, int L1, int L2, class O>
+template <bool INV, int L1, int L2, class O, bool WIDE>
 int launch_strided4(aim_ctx* c, const char* name, const S* in, O* out, const StridedArgs4& a, int G, const S* tw) {
-  constexpr int L = L1 * L2, TX = strided_tx<Pol, L>();
+  constexpr int L = L1 * L2, TX = strided_tx<Pol, L, WIDE>();
   constexpr long long pencil_set = (long long)L * TX * sizeof(S);
   // other-axis indices per block: about 256 work units in the heavier step,
-  // one buffer of at most 48 KB
+  // one buffer of at most 48 KB (96 KB for the wide variant)
   int AY = std::max(1, 256 / (TX * std::min(L1, L2)));
-  AY = std::min<int>(AY, (int)std::max<long long>(1, (48 * 1024) / pencil_set));
+  AY = std::min<int>(AY, (int)std::max<long long>(1, ((WIDE ? 96 : 48) * 1024) / pencil_set));
   AY = std::min(AY, a.A);
   const int items = AY * TX * std::max(L1, L2);
   const int threads = std::min(256, (items + 31) / 32 * 32);
   const size_t sm = (size_t)AY * pencil_set;
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(fft4_strided<Pol, INV, L1, L2, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  static const cudaError_t attr = cudaFuncSetAttribute(fft4_strided<Pol, INV, L1, L2, O, WIDE>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   AIM_CUDA_TRY(attr);
   dim3 grid((a.X + TX - 1) / TX, (a.A + AY - 1) / AY, G);
-  AIM_LAUNCH(c, name, (fft4_strided<Pol, INV, L1, L2, O><<<grid, threads, sm, c->stream>>>(in, out, a, tw, AY)));
+  AIM_LAUNCH(c, name, (fft4_strided<Pol, INV, L1, L2, O, WIDE><<<grid, threads, sm, c->stream>>>(in, out, a, tw, AY)));
   return launch_check(c, name);
 }
 
@@ -102,13 +102,15 @@ int launch_x4(aim_ctx* c, const char* name, S* buf, XArgs4 a, const S* ghat, con
 
 // 1: launched; 0: no four-step kernel for this length; < 0: -error code.
 int AIM_FFT4_NAME(strided)(aim_ctx* c, const char* name, bool inv, const S* in, S* out, const StridedArgs4& a, int G,
-                           int L, const S* tw) {
+                           int L, const S* tw, bool wide) {
   int rc = AIM_OK;
   switch (L) {
-#define AIM_CASE(LL, A1, A2)                                         \
-  case LL:                                                           \
-    rc = inv ? launch_strided4<true, A1, A2, S>(c, name, in, out, a, G, tw)  \
-             : launch_strided4<false, A1, A2, S>(c, name, in, out, a, G, tw); \
+#define AIM_CASE(LL, A1, A2)                                                                      \
+  case LL:                                                                                        \
+    rc = wide ? (inv ? launch_strided4<true, A1, A2, S, true>(c, name, in, out, a, G, tw)         \
+                     : launch_strided4<false, A1, A2, S, true>(c, name, in, out, a, G, tw))       \
+              : (inv ? launch_strided4<true, A1, A2, S, false>(c, name, in, out, a, G, tw)        \
+                     : launch_strided4<false, A1, A2, S, false>(c, name, in, out, a, G, tw));     \
     return rc == AIM_OK ? 1 : -rc;
     AIM_FOURSTEP_LENGTHS(AIM_CASE)
 #undef AIM_CASE

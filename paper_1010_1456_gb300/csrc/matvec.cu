@@ -339,8 +339,28 @@ __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R
             }
           }
         }
-#pragma unroll 4
-        for (int e = r0; e < r1; ++e) {
+        // near entries in batches of EB: the batch's columns first, then its
+        // EB gathers of x, all in flight together
+        constexpr int EB = 4;
+        int e = r0;
+        for (; e + EB <= r1; e += EB) {
+          int col[EB];
+#pragma unroll
+          for (int i = 0; i < EB; ++i) col[i] = ncol[e + i];
+          Run<C, RL> xv[EB];
+#pragma unroll
+          for (int i = 0; i < EB; ++i) xv[i] = load_run<C, RL>(xT + (long long)col[i] * B + b);
+#pragma unroll
+          for (int i = 0; i < EB; ++i) {
+            const C v = nval[e + i];
+#pragma unroll
+            for (int q = 0; q < RL; ++q) {
+              an[q].x += v.x * xv[i].v[q].x - v.y * xv[i].v[q].y;
+              an[q].y += v.x * xv[i].v[q].y + v.y * xv[i].v[q].x;
+            }
+          }
+        }
+        for (; e < r1; ++e) {
           const C v = nval[e];
           const Run<C, RL> xv = load_run<C, RL>(xT + (long long)ncol[e] * B + b);
 #pragma unroll

@@ -192,7 +192,8 @@ def test_group_projection_across_batch_sizes():
         assert rel(y32, op.matvec(x.astype(np.complex64).astype(np.complex128))) <= 1e-5, nrhs
 
 
-FFT_CHOICES = [g.AIM_FFT_STOCKHAM, g.AIM_FFT_FOURSTEP, g.AIM_FFT_FOURSTEP_SMALL, g.AIM_FFT_FOURSTEP_WARP]
+FFT_CHOICES = [g.AIM_FFT_STOCKHAM, g.AIM_FFT_FOURSTEP, g.AIM_FFT_FOURSTEP_SMALL, g.AIM_FFT_FOURSTEP_WARP,
+               g.AIM_FFT_FOURSTEP_WIDE]
 
 
 @pytest.mark.parametrize("kernel", FFT_CHOICES)
@@ -229,8 +230,9 @@ def test_autotune_keeps_parity_and_profiler_state(sphere_small):
     assert g.aim_fft_config(ctx, g.AIM_C128) == kernels
     for p, k in enumerate(kernels):
         assert ms[p, k] > 0 and ms[p, k] == ms[p, ms[p] > 0].min()
-    # AUTO is never timed; the x-pass-only variants (small blocks, warp groups) only on the x pass
-    assert (ms[:, 0] == -1).all() and (ms[[0, 1, 3, 4]][:, 3:] == -1).all()
+    # AUTO is never timed; the x-pass-only variants (small blocks, warp groups)
+    # only on the x pass, the wide strided variant only on the others
+    assert (ms[:, 0] == -1).all() and (ms[[0, 1, 3, 4]][:, [3, 4]] == -1).all() and ms[2, 5] == -1
     y = g.aim_matvec(ctx, xt, precision=g.AIM_C128).cpu().numpy()
     assert rel(y, op.matvec(x)) <= 1e-12
     g.aim_fft_config(ctx, g.AIM_C128, [g.AIM_FFT_AUTO] * 5)
