@@ -297,8 +297,13 @@ def solve_section(g, ctx, kind, size, nrhs, P0, verts=None, tris=None):
     th, ph, w = g.rcs_direction_grid(nth)
     out = {}
     sig = {}
-    for name, P in (("plain_fp64", g.AIM_C128_F64), ("fp64_float_float_fft", g.AIM_C128),
-                    ("mixed_c64_fp64_refined", g.AIM_C64)):
+    runs = (("plain_fp64", g.AIM_C128_F64), ("fp64_float_float_fft", g.AIM_C128), ("mixed_c64_fp64_refined", g.AIM_C64))
+    if ctx.N * nrhs > 4_000_000:
+        # batches this large would keep the FP64 solves running for many minutes:
+        # only the mixed solve, its RCS compared with nothing
+        out["skipped"] = "plain_fp64 and fp64_float_float_fft: N x nrhs > 4e6"
+        runs = runs[2:]
+    for name, P in runs:
         g.aim_set_precision(ctx, P)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -326,9 +331,11 @@ def solve_section(g, ctx, kind, size, nrhs, P0, verts=None, tris=None):
                             "launches": int(sum(c for c, _ in prof.values())),
                             "top": {k: {"launches": c, "ms": round(ms, 3)} for k, (c, ms) in top}}
     g.aim_set_precision(ctx, P0)
-    out["err_thth_mixed_vs_plain"] = float(np.max(g.err_thth(sig["mixed_c64_fp64_refined"], sig["plain_fp64"], w)))
-    out["err_thth_float_float_vs_plain"] = float(np.max(g.err_thth(sig["fp64_float_float_fft"], sig["plain_fp64"], w)))
-    out["speedup_mixed_over_plain"] = out["plain_fp64"]["time_s"] / out["mixed_c64_fp64_refined"]["time_s"]
+    if "plain_fp64" in sig:
+        out["err_thth_mixed_vs_plain"] = float(np.max(g.err_thth(sig["mixed_c64_fp64_refined"], sig["plain_fp64"], w)))
+        out["err_thth_float_float_vs_plain"] = float(np.max(g.err_thth(sig["fp64_float_float_fft"], sig["plain_fp64"],
+                                                                       w)))
+        out["speedup_mixed_over_plain"] = out["plain_fp64"]["time_s"] / out["mixed_c64_fp64_refined"]["time_s"]
     out["rcs_directions"] = int(len(th))
     if kind == "sphere" and verts is not None:
         stream = torch.cuda.current_stream()
@@ -350,7 +357,8 @@ def solve_section(g, ctx, kind, size, nrhs, P0, verts=None, tris=None):
             "efie_iterations": out["mixed_c64_fp64_refined"]["iterations"], "restarts": info["restarts"],
             "max_rel_res": float(info["rel_res"].max()), "converged": bool(info["converged"].all()),
             "speedup_over_efie_mixed": out["mixed_c64_fp64_refined"]["time_s"] / t,
-            "err_thth_vs_efie_plain": float(np.max(g.err_thth(sc, sig["plain_fp64"], w)))}
+            "err_thth_vs_efie_plain": float(np.max(g.err_thth(sc, sig["plain_fp64"], w))) if "plain_fp64" in sig
+            else None}
     return out
 
 

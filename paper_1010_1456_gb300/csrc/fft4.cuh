@@ -31,17 +31,20 @@ struct StridedArgs4 {
 
 struct XArgs4 {
   int nx, Ly, Lz, G;
-  int RY;          // rows per block (its pencils: RY rows x G grids)
-  int GT, PPG;     // threads per pencil group (a multiple of 32), pencils per group at a time
+  int RY, TG;      // rows and grids per block (fft4_x); fft4_x_groups: all G grids of RY rows
+  int GT, PPG;     // fft4_x_groups: threads per pencil group (a multiple of 32), pencils per group at a time
   long long sG;    // grid stride (elements)
   int hx, hy;      // octant extents of Ghat (x, y)
 };
 
-// Barrier of one pencil group: the warp itself when the group is one warp,
-// else the named barrier 1 + grp over the group's GT threads (barrier 0 is
-// __syncthreads).  Also orders the group's shared-memory accesses.
+// Barrier of one pencil group: __syncthreads when the group is the whole
+// block, the warp itself when it is one warp, else the named barrier
+// 1 + grp over the group's GT threads.  Also orders the group's
+// shared-memory accesses.
 __device__ __forceinline__ void group_sync(int grp, int GT) {
-  if (GT == 32)
+  if (GT == (int)blockDim.x)
+    __syncthreads();
+  else if (GT == 32)
     __syncwarp();
   else
     asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(GT) : "memory");
@@ -127,13 +130,10 @@ __global__ void __launch_bounds__(256) fft4_strided(const typename P::S* __restr
 //   step B (thread k1):                row k1: DFT_L2, x Ghat, inverse DFT_L2, twiddle,
 //                                      written back over the same row;
 //   step C (thread n2, to global):     column n2: inverse DFT_L1, samples < nx written.
-// One [L1][odd L2] tile per pencil, two shared-memory round trips.  A block
-// owns RY rows (ky) x all G grids and keeps those rows of Ghat in shared
-// memory.  Its threads form groups of GT (one or more warps); a group takes
-// PPG pencils at a time through the three steps with its own tiles, and only
-// the group's own barrier separates the steps, so groups in different steps
-// overlap instead of waiting for the whole block (GT * PPG and the pencil
-// lengths are chosen by the launcher so that PPG * max(L1, L2) <= GT).
+// One [L1][odd L2] tile per pencil, two shared-memory round trips.  The block
+// handles RY rows (ky) x TG grids at a time with at most one work item per
+// thread in each step (the launcher sizes RY * TG * max(L1, L2) <= blockDim)
+// and keeps the RY rows of Ghat in shared memory.
 // Resident 256-thread blocks per SM the register allocation must allow:
 // three for complex64, two for the 16-byte policies.
 template <class P> constexpr int x_min_blocks() { return sizeof(typename P::S) <= 8 ? 3 : 2; }
@@ -142,6 +142,89 @@ template <class P, int L1, int L2>
 __global__ void __launch_bounds__(256, x_min_blocks<P>()) fft4_x(typename P::S* __restrict__ buf, XArgs4 a,
                                               const typename P::S* __restrict__ ghat,
                                               const typename P::S* __restrict__ twL) {
+  using S = typename P::S;
+  using T = typename P::T;
+  constexpr int L = L1 * L2;
+  constexpr int RA = odd_row(L2);
+  constexpr int PA = L1 * RA;  // per-pencil tile
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int RY = a.RY, TG = a.TG;
+  S* gr = reinterpret_cast<S*>(smem_raw);  // [RY][L]
+  S* tile = gr + RY * L;                    // [RY * TG][L1][RA]
+  const int ky0 = blockIdx.x * RY, kz = blockIdx.y;
+  const int nry = min(RY, a.Ly - ky0);
+  const int iz = min(kz, a.Lz - kz);
+  for (int e = threadIdx.x; e < nry * L; e += blockDim.x) {
+    const int r = e / L, p = e % L;
+    const int ky = ky0 + r;
+    const int iy = min(ky, a.Ly - ky);
+    gr[e] = ghat[((long long)iz * a.hy + iy) * a.hx + min(p, L - p)];
+  }
+  const long long row0 = ((long long)kz * a.Ly + ky0) * a.nx;
+  const int u = threadIdx.x;
+  for (int g0 = 0; g0 < a.G; g0 += TG) {
+    const int ng = min(TG, a.G - g0);
+    const int np = nry * ng;  // pencil pc = r * ng + gl
+    if (g0 > 0) __syncthreads();  // the previous group's step C has read its tiles
+    // step A: forward DFT_L1 of the zero-padded row, straight from global memory
+    if (u < np * L2) {
+      const int n2 = u % L2, pc = u / L2;
+      const int r = pc / ng, gl = pc - r * ng;
+      const S* src = buf + (long long)(g0 + gl) * a.sG + row0 + (long long)r * a.nx;
+      T v[L1];
+      static_for<0, L1>([&](auto n1) {
+        const int p = L2 * decltype(n1)::value + n2;
+        v[n1] = p < a.nx ? P::ld(src[p]) : P::zero();
+      });
+      RegDFT<P, L1, false>::run(v);
+      if (n2 > 0) static_for<1, L1>([&](auto k1) { v[k1] = P::mul(v[k1], P::ld(twL[n2 * decltype(k1)::value])); });
+      S* y = tile + pc * PA + n2;
+      static_for<0, L1>([&](auto k1) { y[decltype(k1)::value * RA] = P::st(v[k1]); });
+    }
+    __syncthreads();  // also orders Ghat's staging before the first step B
+    // step B: forward DFT_L2, product with Ghat, inverse DFT_L2, over one row
+    if (u < np * L1) {
+      const int k1 = u % L1, pc = u / L1;
+      const int r = pc / ng;
+      S* y = tile + pc * PA + k1 * RA;
+      T w[L2];
+      static_for<0, L2>([&](auto n2) { w[n2] = P::ld(y[decltype(n2)::value]); });
+      RegDFT<P, L2, false>::run(w);
+      const S* gg = gr + r * L + k1;
+      static_for<0, L2>([&](auto k2) { w[k2] = P::mul(w[k2], P::ld(gg[L1 * decltype(k2)::value])); });
+      RegDFT<P, L2, true>::run(w);
+      if (k1 > 0)
+        static_for<1, L2>([&](auto n2) { w[n2] = P::mul(w[n2], P::conj_if(P::ld(twL[k1 * decltype(n2)::value]), true)); });
+      static_for<0, L2>([&](auto n2) { y[decltype(n2)::value] = P::st(w[n2]); });
+    }
+    __syncthreads();
+    // step C: inverse DFT_L1 over one column, the first nx samples back to global memory
+    if (u < np * L2) {
+      const int n2 = u % L2, pc = u / L2;
+      const int r = pc / ng, gl = pc - r * ng;
+      const S* z = tile + pc * PA + n2;
+      T v[L1];
+      static_for<0, L1>([&](auto k1) { v[k1] = P::ld(z[decltype(k1)::value * RA]); });
+      RegDFT<P, L1, true>::run(v);
+      S* dst = buf + (long long)(g0 + gl) * a.sG + row0 + (long long)r * a.nx;
+      static_for<0, L1>([&](auto n1) {
+        const int p = n2 + L2 * decltype(n1)::value;
+        if (p < a.nx) dst[p] = P::st(v[n1]);
+      });
+    }
+  }
+}
+
+// The fused x pass in pencil groups: the same three steps and tiles as
+// fft4_x, but the block's threads form groups of GT (one or more warps).  A
+// group takes PPG pencils at a time (PPG * max(L1, L2) <= GT) through the
+// three steps with its own tiles, and only the group's own barrier separates
+// the steps, so groups in different steps overlap instead of waiting for the
+// whole block.  A block owns RY rows (ky) x all G grids.
+template <class P, int L1, int L2>
+__global__ void __launch_bounds__(256, x_min_blocks<P>()) fft4_x_groups(typename P::S* __restrict__ buf, XArgs4 a,
+                                                     const typename P::S* __restrict__ ghat,
+                                                     const typename P::S* __restrict__ twL) {
   using S = typename P::S;
   using T = typename P::T;
   constexpr int L = L1 * L2;
@@ -162,11 +245,14 @@ __global__ void __launch_bounds__(256, x_min_blocks<P>()) fft4_x(typename P::S* 
     const int iy = min(ky, a.Ly - ky);
     gr[e] = ghat[((long long)iz * a.hy + iy) * a.hx + min(p, L - p)];
   }
-  __syncthreads();  // the only block-wide barrier: Ghat rows staged
+  // Ghat rows staged: a block-wide group's first barrier (after step A)
+  // orders them before step B; smaller groups need a barrier of their own
+  if (GT != (int)blockDim.x) __syncthreads();
   const long long row0 = ((long long)kz * a.Ly + ky0) * a.nx;
   const int npen = nry * a.G;  // pencil q: row q / G, grid q % G
   // q0 is the same for every thread of a group, so the group meets its barriers together
   for (int q0 = grp * PPG; q0 < npen; q0 += ngroups * PPG) {
+    if (q0 != grp * PPG) group_sync(grp, GT);  // the previous step C has read the tiles
     // step A: forward DFT_L1 of the zero-padded row, straight from global memory
     if (u < PPG * L2) {
       const int n2 = u % L2, lp = u / L2, q = q0 + lp;
@@ -219,7 +305,6 @@ __global__ void __launch_bounds__(256, x_min_blocks<P>()) fft4_x(typename P::S* 
         });
       }
     }
-    group_sync(grp, GT);  // step C has read the tiles before the next step A writes them
   }
 }
 

@@ -32,18 +32,11 @@ int launch_strided4(aim_ctx* c, const char* name, const S* in, O* out, const Str
   return launch_check(c, name);
 }
 
-// Pencil groups for pencil steps of at most LM threads within `threads`
-// threads.  Block-wide (warp = false): one group of all the threads, as many
-// pencils as fit.  Warp groups: the smallest group (1, 2, 4 or 8 warps)
-// whose pencils keep at least 90 % of its lanes busy in the wider step, else
-// the busiest.
-inline void x_groups(int LM, int threads, bool warp, int* GT, int* PPG) {
-  if (!warp) {
-    *GT = threads;
-    *PPG = threads / LM;
-    if (*PPG < 1) *GT = 0;
-    return;
-  }
+// Pencil groups of fft4_x_groups for pencil steps of at most LM threads
+// within `threads` threads: the smallest group (1, 2, 4 or 8 warps) whose
+// pencils keep at least 90 % of its lanes busy in the wider step, else the
+// busiest.
+inline void x_groups(int LM, int threads, int* GT, int* PPG) {
   int best_gt = 0, best_ppg = 0;
   double best = -1.0;
   for (int w = 1; 32 * w <= threads; w *= 2) {
@@ -66,12 +59,12 @@ inline void x_groups(int LM, int threads, bool warp, int* GT, int* PPG) {
 }
 
 template <int L1, int L2>
-int launch_x4(aim_ctx* c, const char* name, S* buf, XArgs4 a, const S* ghat, const S* tw, int threads, bool warp) {
+int launch_x4_groups(aim_ctx* c, const char* name, S* buf, XArgs4 a, const S* ghat, const S* tw, int threads) {
   constexpr int L = L1 * L2;
   constexpr long long per_pencil = (long long)L1 * odd_row(L2);
   constexpr int LM = std::max(L1, L2);
   int GT = 0, PPG = 0;
-  x_groups(LM, threads, warp, &GT, &PPG);
+  x_groups(LM, threads, &GT, &PPG);
   if (GT == 0) return kNotHandled;  // a pencil wider than the block: the Stockham kernel
   // groups per block: the block's threads, fewer while the tiles and the
   // Ghat rows would not fit in 200 KB; rows per block: as many whole rows
@@ -92,10 +85,36 @@ int launch_x4(aim_ctx* c, const char* name, S* buf, XArgs4 a, const S* ghat, con
   a.GT = GT;
   a.PPG = PPG;
   static const cudaError_t attr =
+      cudaFuncSetAttribute(fft4_x_groups<Pol, L1, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  AIM_CUDA_TRY(attr);
+  dim3 grid((a.Ly + RY - 1) / RY, a.Lz);
+  AIM_LAUNCH(c, name, (fft4_x_groups<Pol, L1, L2><<<grid, ng * GT, sm, c->stream>>>(buf, a, ghat, tw)));
+  return launch_check(c, name);
+}
+
+template <int L1, int L2>
+int launch_x4(aim_ctx* c, const char* name, S* buf, XArgs4 a, const S* ghat, const S* tw, int threads, bool warp) {
+  if (warp) return launch_x4_groups<L1, L2>(c, name, buf, a, ghat, tw, threads);
+  constexpr int L = L1 * L2;
+  constexpr long long per_pencil = (long long)L1 * odd_row(L2);
+  constexpr int LM = std::max(L1, L2);
+  // pencils per block: one work item per thread in each step, shared memory
+  // within what one block may hold
+  const long long cap = (200 * 1024) / sizeof(S);
+  int np = std::max(1, threads / LM);
+  while (np > 1 && L + np * per_pencil > cap) --np;
+  const int TG = std::min(a.G, np);
+  const int RY = std::max(1, std::min(np / TG, a.Ly));
+  a.RY = RY;
+  a.TG = TG;
+  const size_t sm = (size_t)(RY * L + RY * TG * per_pencil) * sizeof(S);
+  if (sm > 227 * 1024 || RY * TG * LM > 256) return kNotHandled;  // leave it to the Stockham kernel
+  const int nthreads = (RY * TG * LM + 31) / 32 * 32;
+  static const cudaError_t attr =
       cudaFuncSetAttribute(fft4_x<Pol, L1, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   AIM_CUDA_TRY(attr);
   dim3 grid((a.Ly + RY - 1) / RY, a.Lz);
-  AIM_LAUNCH(c, name, (fft4_x<Pol, L1, L2><<<grid, ng * GT, sm, c->stream>>>(buf, a, ghat, tw)));
+  AIM_LAUNCH(c, name, (fft4_x<Pol, L1, L2><<<grid, nthreads, sm, c->stream>>>(buf, a, ghat, tw)));
   return launch_check(c, name);
 }
 }  // namespace
