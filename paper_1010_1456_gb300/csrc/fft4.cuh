@@ -75,9 +75,9 @@ constexpr int odd_row(int n) { return n + (n % 2 == 0 ? 1 : 0); }
 // straight from global memory into registers (samples >= n_in are zero and
 // never read); the only shared-memory round trip is the transpose between
 // the two steps.  Step B writes the first n_out outputs.
-template <class P, bool INV, int L1, int L2, class O, bool WIDE = false>
-__global__ void __launch_bounds__(256) fft4_strided(const typename P::S* __restrict__ in, O* __restrict__ out,
-                                                    StridedArgs4 a, const typename P::S* __restrict__ twL, int AY) {
+template <class P, bool INV, int L1, int L2, class O, bool WIDE>
+__device__ __forceinline__ void strided_body(const typename P::S* __restrict__ in, O* __restrict__ out,
+                                             const StridedArgs4 a, const typename P::S* __restrict__ twL, int AY) {
   using S = typename P::S;
   using T = typename P::T;
   constexpr int L = L1 * L2, TX = strided_tx<P, L, WIDE>();
@@ -120,6 +120,23 @@ __global__ void __launch_bounds__(256) fft4_strided(const typename P::S* __restr
   }
 }
 
+template <class P, bool INV, int L1, int L2, class O, bool WIDE = false>
+__global__ void __launch_bounds__(256) fft4_strided(const typename P::S* __restrict__ in, O* __restrict__ out,
+                                                    StridedArgs4 a, const typename P::S* __restrict__ twL, int AY) {
+  strided_body<P, INV, L1, L2, O, WIDE>(in, out, a, twL, AY);
+}
+// The same with four resident 256-thread blocks per SM required of the
+// register allocation: used for the complex64 length-648 pencils, which
+// otherwise take about 74 registers (the few values spilled at 64 cost less
+// than the lost warps).
+template <class P, bool INV, int L1, int L2, class O, bool WIDE = false>
+__global__ void __launch_bounds__(256, 4) fft4_strided_occ4(const typename P::S* __restrict__ in, O* __restrict__ out,
+                                                            StridedArgs4 a, const typename P::S* __restrict__ twL,
+                                                            int AY) {
+  strided_body<P, INV, L1, L2, O, WIDE>(in, out, a, twL, AY);
+}
+template <class P, int L> constexpr bool strided_occ4() { return sizeof(typename P::S) <= 8 && L >= 648; }
+
 // The fused x pass.  With k = k1 + L1 k2 and n = n2 + L2 n1,
 //   forward  X[k1 + L1 k2] = sum_n2 w_L2^(n2 k2) w_L^(n2 k1) sum_n1 x[L2 n1 + n2] w_L1^(n1 k1),
 //   inverse  y[n2 + L2 n1] = sum_k1 w_L1^(-k1 n1) w_L^(-k1 n2) sum_k2 X[k1 + L1 k2] w_L2^(-k2 n2).
@@ -134,12 +151,13 @@ __global__ void __launch_bounds__(256) fft4_strided(const typename P::S* __restr
 // handles RY rows (ky) x TG grids at a time with at most one work item per
 // thread in each step (the launcher sizes RY * TG * max(L1, L2) <= blockDim)
 // and keeps the RY rows of Ghat in shared memory.
-// Resident 256-thread blocks per SM the register allocation must allow:
-// three for complex64, two for the 16-byte policies.
-template <class P> constexpr int x_min_blocks() { return sizeof(typename P::S) <= 8 ? 3 : 2; }
+// Resident 256-thread blocks per SM the register allocation must allow: four
+// for complex64 (three for the longest compiled length, 648, which would
+// spill at four), two for the 16-byte policies.
+template <class P, int L> constexpr int x_min_blocks() { return sizeof(typename P::S) <= 8 ? (L >= 648 ? 3 : 4) : 2; }
 
 template <class P, int L1, int L2>
-__global__ void __launch_bounds__(256, x_min_blocks<P>()) fft4_x(typename P::S* __restrict__ buf, XArgs4 a,
+__global__ void __launch_bounds__(256, x_min_blocks<P, L1 * L2>()) fft4_x(typename P::S* __restrict__ buf, XArgs4 a,
                                               const typename P::S* __restrict__ ghat,
                                               const typename P::S* __restrict__ twL) {
   using S = typename P::S;
@@ -222,7 +240,7 @@ __global__ void __launch_bounds__(256, x_min_blocks<P>()) fft4_x(typename P::S* 
 // the steps, so groups in different steps overlap instead of waiting for the
 // whole block.  A block owns RY rows (ky) x all G grids.
 template <class P, int L1, int L2>
-__global__ void __launch_bounds__(256, x_min_blocks<P>()) fft4_x_groups(typename P::S* __restrict__ buf, XArgs4 a,
+__global__ void __launch_bounds__(256, x_min_blocks<P, L1 * L2>()) fft4_x_groups(typename P::S* __restrict__ buf, XArgs4 a,
                                                      const typename P::S* __restrict__ ghat,
                                                      const typename P::S* __restrict__ twL) {
   using S = typename P::S;

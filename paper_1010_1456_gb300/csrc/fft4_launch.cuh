@@ -24,11 +24,12 @@ int launch_strided4(aim_ctx* c, const char* name, const S* in, O* out, const Str
   const int items = AY * TX * std::max(L1, L2);
   const int threads = std::min(256, (items + 31) / 32 * 32);
   const size_t sm = (size_t)AY * pencil_set;
-  static const cudaError_t attr = cudaFuncSetAttribute(fft4_strided<Pol, INV, L1, L2, O, WIDE>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  auto kern = fft4_strided<Pol, INV, L1, L2, O, WIDE>;
+  if constexpr (strided_occ4<Pol, L>()) kern = fft4_strided_occ4<Pol, INV, L1, L2, O, WIDE>;
+  static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   AIM_CUDA_TRY(attr);
   dim3 grid((a.X + TX - 1) / TX, (a.A + AY - 1) / AY, G);
-  AIM_LAUNCH(c, name, (fft4_strided<Pol, INV, L1, L2, O, WIDE><<<grid, threads, sm, c->stream>>>(in, out, a, tw, AY)));
+  AIM_LAUNCH(c, name, (kern<<<grid, threads, sm, c->stream>>>(in, out, a, tw, AY)));
   return launch_check(c, name);
 }
 
