@@ -25,6 +25,19 @@ def test_kernel_models_scale_with_rhs_and_precision():
     assert m1["fft_x_conv"][1] == pytest.approx(4 * Ly * Lz * (10 * Lx * np.log2(Lx) + 6 * Lx))
 
 
+def test_projection_model_counts_the_projected_nodes():
+    """With a group list the projection writes only the nodes of its groups;
+    the interpolation reads only the touched nodes; both default to the grid."""
+    n, L = [10, 11, 12], [20, 24, 24]
+    Nc = 10 * 11 * 12
+    full = bench.kernel_models(1000, n, L, 80000, 27000, 27, 2, 8)
+    part = bench.kernel_models(1000, n, L, 80000, 27000, 27, 2, 8, touched=400, projected=320)
+    G, e = 8, 8
+    assert full["proj_gather"][0] - part["proj_gather"][0] == (Nc - 320) * (4 + G * e)
+    assert full["interp_near"][0] - part["interp_near"][0] == G * (Nc - 400) * e
+    assert part["proj_gather"][1] == full["proj_gather"][1]  # same arithmetic
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
