@@ -57,6 +57,7 @@ def test_error_strings_and_defaults(lib):
     o = _lib.aim_opts()
     lib.aim_default_opts(ctypes.byref(o))
     assert (o.precision, o.restart, o.max_rhs) == (_lib.AIM_C128, 50, 1)
+    assert (o.planar, o.cfie_alpha) == (1, 1.0)  # plane collapse on, plain EFIE
 
 
 def test_null_and_bad_arguments_are_rejected_without_a_device(lib):
@@ -72,6 +73,10 @@ def test_null_and_bad_arguments_are_rejected_without_a_device(lib):
     assert lib.aim_solve(None, None, None, 1, 1e-6, None) == _lib.AIM_EINVAL
     assert b"null" in lib.aim_last_error()
     assert lib.aim_probe_fma_peak(16, ctypes.byref(ctypes.c_double())) == _lib.AIM_EINVAL
+    get = (ctypes.c_int32 * 5)()
+    assert lib.aim_fft_config(None, _lib.AIM_C128, None, get) == _lib.AIM_EINVAL
+    assert lib.aim_autotune(None, _lib.AIM_C128, 1, 1, None, None) == _lib.AIM_EINVAL
+    assert lib.aim_export(None, _lib.AIM_EXPORT_WEIGHTS, None, 0) == _lib.AIM_EINVAL
 
 
 def test_setup_reports_missing_device(lib):
@@ -103,3 +108,6 @@ def test_footprint_is_host_only(lib):
     b8 = aim_footprint(v, t, 0.1, 2, 0.3, 8)
     assert 0 < b1 < b8
     assert aim_footprint(v, t, 0.1, 2, 0.3, 1, cfie_alpha=0.6) > b1
+    for bad in (0.0, -0.5, 1.5):  # CFIE weights outside (0, 1]
+        with pytest.raises(RuntimeError):
+            aim_footprint(v, t, 0.1, 2, 0.3, 1, cfie_alpha=bad)
