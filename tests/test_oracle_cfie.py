@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 import scipy.linalg
 
-from aim_inputs import icosphere_mesh, plate_mesh, planewave_minus_z_xpol
+from aim_inputs import icosphere_mesh, plate_mesh, planewave_minus_z_xpol, random_incidence
 from oracle import ETA0, aim, mfie, mie, rcs
 from oracle.efie import dense_Z
 from oracle.excitation import planewave_rhs
@@ -116,3 +116,25 @@ def test_cfie_sphere_rcs_near_mie_and_better_conditioned(small_sphere):
     assert rcs.err_thth(sc, ref, w) < 0.06
     assert rcs.err_thth(sc, se, w) < 0.05
     assert np.linalg.cond(ZC) < 0.5 * np.linalg.cond(ZES)
+
+
+def test_mfie_rhs_on_a_plate_reduces_to_efie_moments():
+    """On a flat plate with unit normal n, n x (khat x pol) = khat (n . pol) - pol (n . khat)
+    is a constant vector, so eta V^M = (n . pol) <f, khat e> - (n . khat) <f, pol e>: two
+    EFIE-type moments of the same phase (the EFIE right-hand side evaluated with khat and
+    with pol as the polarisation).  At normal incidence from above (khat = -z, pol = x,
+    n = +z) this is exactly V^E."""
+    v, t = plate_mesh(1.0, 6)
+    r = RWG(v, t)
+    nz = mfie.tri_normals(r.verts, r.tris)
+    assert np.allclose(np.abs(nz[:, 2]), 1.0)
+    n = nz[0]
+    assert np.all(nz == n)  # one orientation over the plate
+    kh, po = random_incidence(3, seed=11)
+    VM = ETA0 * mfie.planewave_rhs_mfie(r, K0, kh, po)
+    ref = (po @ n)[:, None] * planewave_rhs(r, K0, kh, kh) - (kh @ n)[:, None] * planewave_rhs(r, K0, kh, po)
+    assert np.linalg.norm(VM - ref) <= 1e-13 * np.linalg.norm(ref)
+    kz, px = np.array([[0.0, 0.0, -1.0]]), np.array([[1.0, 0.0, 0.0]])
+    VMn = ETA0 * mfie.planewave_rhs_mfie(r, K0, kz, px)
+    VEn = planewave_rhs(r, K0, kz, px)
+    assert np.linalg.norm(VMn - n[2] * VEn) <= 1e-13 * np.linalg.norm(VEn)
