@@ -1,5 +1,6 @@
 """Pins for the oracle's quadrature, meshes and RWG functions (CPU only)."""
 
+import os
 from math import factorial
 
 import numpy as np
@@ -108,3 +109,32 @@ def test_rwg_order_and_halves():
         assert r.free_p[m] not in r.edge[m] and r.free_m[m] not in r.edge[m]
         assert t[r.tri_p[m], r.slot_p[m]] == r.free_p[m]
         assert t[r.tri_m[m], r.slot_m[m]] == r.free_m[m]
+
+
+def _table1():
+    rows = []
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_plates.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            rows.append([int(v) for v in line.split()])
+    return rows
+
+
+@pytest.mark.parametrize("L", [1, 2, 4, 8, 16, 32])
+def test_plate_unknowns_match_table1(L):
+    """Table 1's plates are square meshes of 10 L_P x 10 L_P squares (lambda/10 edges),
+    each split by one diagonal: the oracle's RWG count (interior edges) gives the
+    printed N for every plate it can build here.  The printed 76 840 of the 16 lambda
+    row reads as 76 480 (two digits transposed): 2 n (n - 1) + n^2 with n = 160,
+    the count every other row also follows.  The grid's third extent is M + 1 = 4
+    nodes for the paper's M = 3 on a plate lying in one node plane."""
+    row = {r[0]: r for r in _table1()}[L]
+    v, t = plate_mesh(float(L), 10 * L)
+    r = RWG(v, t)
+    printed = 76480 if L == 16 else row[1]
+    assert r.N == printed
+    if L <= 4:
+        from oracle import aim
+
+        anc = aim.anchors(r.centre, 0.1, 3)
+        assert anc[:, 2].max() + 3 - anc[:, 2].min() + 1 == row[4]
