@@ -43,7 +43,7 @@ def test_mfie_reduces_to_half_gram_on_a_plate():
     assert np.abs(ZM.real - 0.5 * G).max() <= 1e-14 * np.abs(G).max()
 
 
-@pytest.mark.parametrize("M", [2, 3])
+@pytest.mark.parametrize("M", [2, 3, 4, 5])
 def test_mfie_weights_reproduce_the_curl_moments(small_sphere, M):
     """sum_u W^c_m(u) q(u) = int f_m . (n x (grad q x e_c)) dS for every monomial q of
     per-axis degree <= M (local coordinates), right side from a 10-point rule."""
