@@ -89,3 +89,18 @@ def test_mom_sphere_rcs_matches_mie():
     # a mirrored pattern (wrong travel direction) is far off
     ref_wrong = mie.sigma_thth_minus_z(R, np.pi - th, ph)
     assert rcs.err_thth(s, ref_wrong, w) > 5 * e
+
+
+def test_planewave_rhs_closed_form_at_normal_incidence():
+    """On the z = 0 plate a wave travelling -z has unit phase everywhere, so
+    V_m = pol . int f_m dS, and for an RWG function int f_m dS = (l_m / 3)(p_- - p_+)
+    with p_+- the free vertices of its two triangles (the centroid of each
+    triangle lies a third of the way from the free vertex to the edge)."""
+    v, t = plate_mesh(1.0, 5)
+    r = RWG(v, t)
+    closed = (r.length / 3.0)[:, None] * (r.verts[r.free_m] - r.verts[r.free_p])
+    kz = np.array([[0.0, 0.0, -1.0], [0.0, 0.0, -1.0]])
+    pols = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    V = planewave_rhs(r, K0, kz, pols)
+    assert np.abs(V.imag).max() <= 1e-15 * np.abs(V).max()
+    assert np.abs(V.real - (closed @ pols.T).T).max() <= 1e-14 * np.abs(closed).max()
