@@ -176,6 +176,48 @@ def convolve_direct(Q, h, k):
     return (q @ Gm.T).reshape(Q.shape)
 
 
+def convolve_direct_at(Q, nodes, h, k, chunk=1 << 22):
+    """Phi(u) = sum_v G_h(u - v) Q(v) at listed nodes u only, by direct summation.
+
+    Q: [..., nz, ny, nx] complex; nodes: [T, 3] integer (x, y, z) grid indices.
+    The sum runs over every node v where some leading slice of Q is nonzero
+    (the others add nothing), in chunks of about ``chunk`` (u, v) pairs.
+    G_h(D) depends on D only through the integer |D|^2, so it is tabulated
+    once over 0 .. max |D|^2 with the arithmetic of ``grid_kernel`` (same
+    values, bit for bit) and looked up per pair.  Returns [..., T].  This is
+    the definition of the grid convolution restricted to a few output nodes:
+    it serves products of very large grids checked on sampled rows, where the
+    padded FFT of ``convolve_fft`` would hold tens of GB of host memory.
+    """
+    lead = Q.shape[:-3]
+    nz, ny, nx = Q.shape[-3:]
+    q = Q.reshape((-1, nz * ny * nx))
+    src = np.nonzero(np.any(q != 0, axis=0))[0]
+    sx = src % nx
+    sy = (src // nx) % ny
+    sz = src // (nx * ny)
+    spts = np.stack([sx, sy, sz], axis=1)
+    qs = q[:, src]  # [B, nsrc]
+    nodes = np.asarray(nodes, dtype=np.int64).reshape(-1, 3)
+    ext = np.maximum(np.abs(nodes).max(axis=0) if len(nodes) else 0, [nx, ny, nz]) + np.array([nx, ny, nz])
+    d2max = int((ext.astype(np.int64) ** 2).sum())
+    r = h * np.sqrt(np.arange(d2max + 1, dtype=np.float64))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tab = np.exp(-1j * k * r) / (4.0 * np.pi * r)
+    tab[0] = 0.0  # G_h(0) = 0
+    out = np.zeros((q.shape[0], len(nodes)), dtype=np.complex128)
+    step = max(1, chunk // max(len(nodes), 1))
+    nd = nodes.astype(np.int32)
+    sp = spts.astype(np.int32)
+    for s0 in range(0, len(src), step):
+        d2 = np.zeros((len(nodes), min(step, len(src) - s0)), dtype=np.int32)
+        for ax in range(3):  # |u - v|^2 summed axis by axis: [T, chunk]
+            dd = nd[:, ax, None] - sp[None, s0 : s0 + step, ax]
+            d2 += dd * dd
+        out += qs[:, s0 : s0 + step] @ tab[d2].T
+    return out.reshape(lead + (len(nodes),))
+
+
 def near_pairs(centres, radius):
     """All (m, n) with |c_m - c_n| <= radius, row-major sorted, self included."""
     from scipy.spatial import cKDTree
@@ -240,7 +282,7 @@ class AIMOperator:
             from .mfie import mfie_weights
 
             self.W = mfie_weights(rwg, h, M, self.anc)
-        self.Ghat = scipy.fft.fftn(green_grid(self.n, self.L, h, k), workers=-1)
+        self._Ghat = None  # transformed on first use (convolve), see Ghat
         rows, cols = near_pairs(rwg.centre, self.radius)
         if near_rows is not None:  # restrict the correction to some rows
             keep = np.isin(rows, near_rows)
@@ -248,6 +290,13 @@ class AIMOperator:
         self.near_rows, self.near_cols = rows, cols
         self.near_vals = self._near_values(rows, cols)
         self.Znear = scipy.sparse.csr_matrix((self.near_vals, (rows, cols)), shape=(self.N, self.N))
+
+    @property
+    def Ghat(self):
+        """fftn of the circulant-embedded G_h on the padded grid (computed once, on first use)."""
+        if self._Ghat is None:
+            self._Ghat = scipy.fft.fftn(green_grid(self.n, self.L, self.h, self.k), workers=-1)
+        return self._Ghat
 
     def _near_values(self, rows, cols):
         zmn = mom_entries(self.rwg, rows, cols, self.k)
@@ -264,42 +313,48 @@ class AIMOperator:
         return self.alpha * ze + (1.0 - self.alpha) * ETA0 * zm
 
     # --- the four steps of one product -----------------------------------
-    def project(self, x):
-        """Q_c(u) = sum_m Lambda^c_m(u - a_m) x_m on the n-grid: [B, 4, nz, ny, nx]."""
+    def project(self, x, comps=(0, 1, 2, 3)):
+        """Q_c(u) = sum_m Lambda^c_m(u - a_m) x_m on the n-grid: [B, len(comps), nz, ny, nx]
+        for the components c in ``comps`` (0, 1, 2: x, y, z current; 3: charge)."""
         x = np.atleast_2d(x)
         B = x.shape[0]
         nx, ny, nz = self.n
-        Q = np.zeros((B, 4, nz * ny * nx), dtype=np.complex128)
+        Q = np.zeros((B, len(comps), nz * ny * nx), dtype=np.complex128)
         off = stencil_offsets(self.M)
         node = self.loc[:, None, :] + off[None, :, :]  # [N, S, 3]
         flat = (node[..., 2] * ny + node[..., 1]) * nx + node[..., 0]
         for b in range(B):
-            for c in range(4):
-                np.add.at(Q[b, c], flat.ravel(), (self.lam[:, c, :] * x[b][:, None]).ravel())
-        return Q.reshape(B, 4, nz, ny, nx)
+            for ci, c in enumerate(comps):
+                np.add.at(Q[b, ci], flat.ravel(), (self.lam[:, c, :] * x[b][:, None]).ravel())
+        return Q.reshape(B, len(comps), nz, ny, nx)
 
     def convolve(self, Q):
         return convolve_fft(Q, self.Ghat, self.n, self.L)
 
-    def interpolate(self, Phi):
-        """y_m = j k eta [sum_{x,y,z} <Lambda^c_m, Phi_c> - k^-2 <Lambda^rho_m, Phi_rho>]."""
+    def interpolate(self, Phi, comps=(0, 1, 2, 3)):
+        """y_m = j k eta [sum_{x,y,z} <Lambda^c_m, Phi_c> - k^-2 <Lambda^rho_m, Phi_rho>].
+
+        Phi: [B, len(comps), nz, ny, nx], the potentials of the components in
+        ``comps``; the sum runs over those components only (all four give the
+        product's grid part)."""
         B = Phi.shape[0]
         nx, ny, nz = self.n
         off = stencil_offsets(self.M)
         node = self.loc[:, None, :] + off[None, :, :]
         flat = (node[..., 2] * ny + node[..., 1]) * nx + node[..., 0]
-        P = Phi.reshape(B, 4, -1)
+        P = Phi.reshape(B, len(comps), -1)
         fac = np.array([1.0, 1.0, 1.0, -1.0 / (self.k * self.k)])
         y = np.zeros((B, self.N), dtype=np.complex128)
-        for c in range(4):
-            y += fac[c] * np.einsum("ms,bms->bm", self.lam[:, c, :], P[:, c][:, flat])
+        for ci, c in enumerate(comps):
+            y += fac[c] * np.einsum("ms,bms->bm", self.lam[:, c, :], P[:, ci][:, flat])
         y = (1j * self.k * ETA0) * y
         if self.alpha == 1.0:
             return y
         # MFIE: -<f_m, n x curl A> with the differentiated interpolation weights
         ym = np.zeros((B, self.N), dtype=np.complex128)
-        for c in range(3):
-            ym -= np.einsum("ms,bms->bm", self.W[:, c, :], P[:, c][:, flat])
+        for ci, c in enumerate(comps):
+            if c < 3:
+                ym -= np.einsum("ms,bms->bm", self.W[:, c, :], P[:, ci][:, flat])
         return self.alpha * y + (1.0 - self.alpha) * ETA0 * ym
 
     def matvec(self, x):
@@ -307,6 +362,34 @@ class AIMOperator:
         x = np.atleast_2d(np.asarray(x, dtype=np.complex128))
         y = self.interpolate(self.convolve(self.project(x)))
         y += (self.Znear @ x.T).T
+        return y
+
+    def matvec_rows(self, x, rows):
+        """Rows ``rows`` of one product, with the grid convolution summed directly
+        at the stencil nodes of those rows (``convolve_direct_at``) instead of the
+        padded FFT: the same four steps (projection of every basis function,
+        convolution, interpolation, near correction) evaluated only where the
+        listed rows read them.  The near correction must cover these rows
+        (``near_rows`` at construction includes them, or is None)."""
+        x = np.atleast_2d(np.asarray(x, dtype=np.complex128))
+        rows = np.asarray(rows, dtype=np.int64)
+        Q = self.project(x)  # [B, 4, nz, ny, nx]
+        off = stencil_offsets(self.M)
+        node = self.loc[rows][:, None, :] + off[None, :, :]  # [R, S, 3]
+        uniq, inv = np.unique(node.reshape(-1, 3), axis=0, return_inverse=True)
+        phi_u = convolve_direct_at(Q, uniq, self.h, self.k)  # [B, 4, U]
+        P = phi_u[..., inv.ravel()].reshape(x.shape[0], 4, len(rows), len(off))  # [B, 4, R, S]
+        fac = np.array([1.0, 1.0, 1.0, -1.0 / (self.k * self.k)])
+        y = np.zeros((x.shape[0], len(rows)), dtype=np.complex128)
+        for c in range(4):
+            y += fac[c] * np.einsum("rs,brs->br", self.lam[rows, c, :], P[:, c])
+        y = (1j * self.k * ETA0) * y
+        if self.alpha != 1.0:
+            ym = np.zeros_like(y)
+            for c in range(3):
+                ym -= np.einsum("rs,brs->br", self.W[rows, c, :], P[:, c])
+            y = self.alpha * y + (1.0 - self.alpha) * ETA0 * ym
+        y += (self.Znear[rows] @ x.T).T
         return y
 
     def far_matvec(self, x):

@@ -200,3 +200,52 @@ def test_error_vs_dense_decreases_with_near_radius(ball):
         errs.append(np.linalg.norm(op.matvec(x)[0] - ref) / np.linalg.norm(ref))
     assert errs[0] < 2e-2
     assert errs[0] > errs[1] > errs[2]
+
+
+def test_direct_sum_at_nodes_equals_full_direct_sum():
+    """convolve_direct_at (sources restricted to the nonzero nodes, outputs to
+    listed nodes, chunked) against the all-pairs brute-force sum at every node,
+    with a Q that is zero on some nodes of every slice."""
+    rng = np.random.default_rng(5)
+    Q = rng.standard_normal((2, 3, 5, 4)) + 1j * rng.standard_normal((2, 3, 5, 4))
+    Q[:, :, 1, :] = 0.0
+    Q[..., 0, 2, 3] = 0.0
+    ref = aim.convolve_direct(Q, H, K0)  # [2, 3, 5, 4]
+    nz, ny, nx = Q.shape[-3:]
+    Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    nodes = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    for chunk in (7, 1 << 20):  # many chunks and one
+        got = aim.convolve_direct_at(Q, nodes, H, K0, chunk=chunk)
+        assert np.abs(got - ref.reshape(2, -1)).max() <= 1e-13 * np.abs(ref).max()
+    # a few nodes in arbitrary order
+    pick = np.array([5, 0, 59, 17])
+    got = aim.convolve_direct_at(Q, nodes[pick], H, K0)
+    assert np.abs(got - ref.reshape(2, -1)[:, pick]).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.6])
+def test_matvec_rows_equals_full_product_rows(ball, alpha):
+    """The row-sampled product (direct sum at the rows' stencil nodes) equals
+    the FFT product's rows; near list restricted to the rows, EFIE and CFIE."""
+    rows = np.array([0, 3, 17, ball.N - 1])
+    full = aim.AIMOperator(ball, K0, H, 2, alpha=alpha)
+    part = aim.AIMOperator(ball, K0, H, 2, near_rows=rows, alpha=alpha)
+    x = random_complex((2, ball.N), 6)
+    ref = full.matvec(x)[:, rows]
+    got = part.matvec_rows(x, rows)
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+    assert part._Ghat is None  # the sampled product never builds the padded spectrum
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.6])
+def test_product_by_components_sums_to_the_product(ball, alpha):
+    """Projection, convolution and interpolation run one component at a time
+    (comps=[c]) add up to the grid part of the product."""
+    op = aim.AIMOperator(ball, K0, H, 2, alpha=alpha)
+    x = random_complex((2, ball.N), 8)
+    ref = op.far_matvec(x)
+    tot = np.zeros_like(ref)
+    for c in range(4):
+        tot += op.interpolate(op.convolve(op.project(x, comps=[c])), comps=[c])
+    assert np.linalg.norm(tot - ref) <= 1e-14 * np.linalg.norm(ref)
+    assert np.array_equal(op.project(x, comps=[2])[:, 0], op.project(x)[:, 2])
