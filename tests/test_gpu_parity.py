@@ -389,3 +389,49 @@ def test_plate_off_node_plane_keeps_three_dimensions():
     x = random_complex((1, ctx.N), 55)
     y = g.aim_matvec(ctx, torch.from_numpy(x).cuda()).cpu().numpy()
     assert rel(y, op.matvec(x)) <= 1e-12
+
+
+@pytest.mark.slow
+def test_full_size_sphere_16_lambda_sampled_rows():
+    """16 lambda sphere (N = 908,280, grid 323^3 padded 648^3), the benchmark's
+    workload: the complex64 product of 8 right-hand sides in the benchmark's
+    launch configuration (FFT kernels autotuned), and with each FFT kernel
+    forced on every pass (length-648 four-step pencils, the four-block
+    strided kernel, the wide strided variant, the warp-group and small-block
+    x passes, Stockham); then, on a one-RHS context, the FP64-accurate
+    (float-float) and native FP64 products.  Sampled rows against the
+    oracle's rows computed by direct summation of the grid convolution at
+    their stencil nodes (its padded FFT would hold about 50 GB of host
+    memory)."""
+    R = 16.0
+    v, t = icosphere_mesh(R, icosphere_frequency(R))
+    rwg = RWG(v, t)
+    assert rwg.N == 908280
+    rows = np.sort(np.random.default_rng(7).choice(rwg.N, 32, replace=False))
+    # inputs exactly representable in complex64, so one oracle evaluation serves every precision
+    x = random_complex((8, rwg.N), 81).astype(np.complex64)
+    op = oaim.AIMOperator(rwg, K0, H, 2, near_rows=rows)
+    ref = op.matvec_rows(x.astype(np.complex128), rows)  # [8, 32]
+
+    ctx = g.aim_setup(v, t, K0, H, M=2, near_radius=3 * H, max_rhs=8, precision=g.AIM_C64)
+    n, L, _ = g.aim_grid_info(ctx)
+    assert n == [323, 323, 323] and L == [648, 648, 648]
+    xt = torch.from_numpy(x).cuda()
+    for kernel in FFT_CHOICES:
+        g.aim_fft_config(ctx, g.AIM_C64, [kernel] * 5)
+        y = g.aim_matvec(ctx, xt, precision=g.AIM_C64).cpu().numpy()[:, rows]
+        assert rel(y, ref) <= 1e-5, (kernel, rel(y, ref))
+    g.aim_fft_config(ctx, g.AIM_C64, [g.AIM_FFT_AUTO] * 5)
+    g.aim_autotune(ctx, g.AIM_C64, nrhs=8, reps=1)
+    y = g.aim_matvec(ctx, xt, precision=g.AIM_C64).cpu().numpy()[:, rows]
+    assert rel(y, ref) <= 1e-5
+    ctx.close()
+    del xt
+    torch.cuda.empty_cache()
+
+    ctx = g.aim_setup(v, t, K0, H, M=2, near_radius=3 * H, max_rhs=1, precision=g.AIM_C128)
+    x1 = torch.from_numpy(x[:1].astype(np.complex128)).cuda()
+    for prec in WIDE:
+        y = g.aim_matvec(ctx, x1, precision=prec).cpu().numpy()[:, rows]
+        assert rel(y, ref[:1]) <= 1e-12, (prec, rel(y, ref[:1]))
+    ctx.close()
