@@ -10,16 +10,20 @@
 //
 // The array (kNoallocScratchBytes = 64 MiB) is part of the library's device
 // image: every GPU that loads the library holds it until the process exits.
-// Its device address is looked up once per device with cudaGetSymbolAddress,
-// on the first call made with that device current (the host-side name of the
-// array is only a stand-in and must never be passed to a kernel); with lazy
-// module loading the driver maps the array during that first lookup.  All calls
-// share the array and it keeps the last call's contents; every kernel of the
-// product writes every grid element it later reads, so nothing has to start
-// at zero.  Calls whose work overlaps on the GPU (different streams, or
-// different contexts at the same time) race on the array; callers must order
-// them.
-#include <mutex>
+// The host-side name of the array is only a stand-in and must never be passed
+// to a kernel; its device address is looked up with cudaGetSymbolAddress in
+// every call, with the context's device current.  The address belongs to
+// the CUDA context it was looked up in, so it is never cached: a caller that
+// makes another context current, or a call after cudaDeviceReset, gets the
+// address of the array in the context that is current now.  With lazy module
+// loading the driver maps the array during the first lookup in a context
+// (the set-up of that device); later lookups are host-side and allocate
+// nothing.  All calls share the array and it keeps the last call's
+// contents; every kernel of the product writes every grid element it later
+// reads, so nothing has to start at zero.  Calls whose work overlaps on the
+// GPU (different streams, or different contexts at the same time) race on
+// the array; callers must order them.
+#include <string>
 
 #include "common.h"
 
@@ -28,29 +32,23 @@ namespace aim {
 constexpr size_t kNoallocScratchBytes = 64ull << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device.
-static int noalloc_scratch(void** out) {
-  int dev = 0;
-  AIM_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("aim_matvec_c64_noalloc: device ordinal out of range");
+// Device address of the scratch array in the current context, which must be
+// the context of device `dev`.
+static int noalloc_scratch(int dev, void** out) {
+  int cur = -1;
+  AIM_CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != dev) {
+    set_error("aim_matvec_c64_noalloc: the context was built on device " + std::to_string(dev) +
+              " but device " + std::to_string(cur) + " is current; make the context's device current first");
     return AIM_EINVAL;
   }
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error(std::string("aim_matvec_c64_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
-      return AIM_ECUDA;
-    }
-    g_noalloc_addr[dev] = p;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    set_error(std::string("aim_matvec_c64_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+    return AIM_ECUDA;
   }
-  *out = g_noalloc_addr[dev];
+  *out = p;
   return AIM_OK;
 }
 
@@ -81,7 +79,7 @@ extern "C" int aim_matvec_c64_noalloc(aim_ctx* ctx, const void* x_dev, void* y_d
     return AIM_EINVAL;
   }
   void* base = nullptr;
-  AIM_TRY(noalloc_scratch(&base));
+  AIM_TRY(noalloc_scratch(ctx->device, &base));
   unsigned char* s = static_cast<unsigned char*>(base);
   float2* g0 = reinterpret_cast<float2*>(s);
   float2* g1 = reinterpret_cast<float2*>(s + b0);
