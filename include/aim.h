@@ -54,9 +54,13 @@ enum {
  * round them once where a lower precision is used.
  *   AIM_C64      complex64 vectors; FP32 weights, spectrum, near entries,
  *                grids and accumulation (the mixed-precision inner product).
- *   AIM_C128     complex128 vectors; projection, interpolation and near SpMV
- *                in FP64, FFT passes in float-float arithmetic (pairs of
- *                FP32 numbers, about 48 significant bits) on the FP32 pipes.
+ *   AIM_C128     complex128 vectors (FP64 in and out); every step in between
+ *                -- projection, FFT passes, spectral product, interpolation
+ *                and near SpMV, with their weights, spectrum, near entries,
+ *                grids and accumulations -- in float-float arithmetic (pairs
+ *                of FP32 numbers, about 48 significant bits) on the FP32
+ *                pipes: FP64-accurate (1e-12 against an FP64 reference), not
+ *                native FP64.
  *   AIM_C128_F64 complex128 vectors; every step in native FP64 (the plain
  *                FP64 path; on GB300 its FFT is bound by the FP64 pipe).
  */
@@ -188,6 +192,34 @@ int aim_solve(aim_ctx* ctx, const void* V_dev, void* X_dev, int nrhs, double tol
 int aim_rcs(aim_ctx* ctx, const void* X_dev, int nrhs, int ndir, const double* theta,
             const double* phi, double* sig_tt, double* sig_pp);
 
+/*
+ * Direction quadrature of the error measure of eq. (1) (the paper does not
+ * state its quadrature): Gauss-Legendre nodes in cos(theta) (n_theta of
+ * them, theta descending from pi) times n_phi uniform midpoint nodes in phi;
+ * weight = Gauss weight * 2 pi / n_phi (the weights sum to 4 pi).  theta,
+ * phi, weight: host [n_theta * n_phi], theta-major.  Host only; needs no GPU.
+ */
+int aim_rcs_grid(int n_theta, int n_phi, double* theta, double* phi, double* weight);
+
+/*
+ * Eq. (1): err[b] = sqrt( sum_d w_d (sigma[b][d] - ref[b][d])^2 / sum_d w_d ref[b][d]^2 ),
+ * the relative RMS difference of two bistatic RCS patterns over the sphere of
+ * directions.  sigma, ref: host [nrhs][ndir]; weight [ndir]; err [nrhs].
+ * AIM_EINVAL if a reference pattern is zero.  Host only.
+ */
+int aim_err_thth(int nrhs, int ndir, const double* sigma, const double* ref, const double* weight, double* err);
+
+/*
+ * Reference RCS of a PEC sphere (paper Section 2.2: the sphere results of
+ * Table 2 are measured against the analytic Mie series): bistatic sigma_thth
+ * in m^2 (units of the length unit squared) of a sphere of radius `radius`
+ * centred at the origin, lit by an x-polarised plane wave of unit amplitude
+ * travelling along -z, at the directions (theta[d], phi[d]); wavenumber k in
+ * the inverse length unit.  Series cut at n = ceil(ka + 4 (ka)^(1/3) + 10).
+ * sigma: host [ndir].  Host only.
+ */
+int aim_mie_sigma_thth(double radius, double k, int ndir, const double* theta, const double* phi, double* sigma);
+
 /* Bytes of device memory a context for this mesh would hold (estimate, +-10 %);
  * cfie_alpha as in aim_opts (1: EFIE; < 1 adds the MFIE arrays). */
 int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int max_rhs, double cfie_alpha,
@@ -304,14 +336,15 @@ int aim_autotune(aim_ctx* ctx, int precision, int nrhs, int reps, int32_t* kerne
  * library (held by every GPU that loads the library until the process
  * exits); a product needs 8 * 4 * nrhs * (nx*ny*nz + Lz*ny*nx + Lz*Ly*nx)
  * bytes (each part rounded up to 256), and larger requests return
- * AIM_EINVAL with the size in aim_last_error().  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; with lazy module loading the driver maps the array at
- * that moment, so the device's free memory drops by 64 MiB on the first call
- * and stays there until exit.  Make that first call before any stream
- * capture.  All
- * calls share the array: calls whose work overlaps on the GPU race and must
- * be ordered by the caller.  The context itself is built by aim_setup.
+ * AIM_EINVAL with the size in aim_last_error().  The context's device must
+ * be current (AIM_EINVAL otherwise).  Every call looks up the array's device
+ * address (cudaGetSymbolAddress) in the current context; with lazy module
+ * loading the driver maps the array at the first lookup in a context (the
+ * set-up of that device), so the device's free memory drops by 64 MiB on the
+ * first call and stays there until exit.  Make that first call before any
+ * stream capture.  All calls share the array: calls whose work overlaps on
+ * the GPU race and must be ordered by the caller.  The 64 MiB are not part of
+ * aim_footprint's estimate.  The context itself is built by aim_setup.
  */
 int aim_matvec_c64_noalloc(aim_ctx* ctx, const void* x_dev, void* y_dev, int nrhs);
 

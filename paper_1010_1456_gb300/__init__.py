@@ -332,20 +332,41 @@ def aim_autotune(ctx, precision=AIM_C128, nrhs=1, reps=3):
     return [int(v) for v in k], np.array(list(ms)).reshape(5, AIM_FFT_KERNELS)
 
 
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
 def rcs_direction_grid(n_theta, n_phi=None):
-    """Directions and weights for eq. (1): Gauss-Legendre nodes in cos(theta),
-    uniform phi.  Returns (theta, phi, weight) flattened theta-major."""
+    """(theta, phi, weight) of the eq. (1) quadrature (aim_rcs_grid): Gauss-Legendre
+    in cos(theta) times uniform phi, flattened theta-major."""
     n_phi = 2 * n_theta if n_phi is None else n_phi
-    mu, wmu = np.polynomial.legendre.leggauss(n_theta)
-    th = np.arccos(mu)
-    ph = (np.arange(n_phi) + 0.5) * (2.0 * np.pi / n_phi)
-    T, P = np.meshgrid(th, ph, indexing="ij")
-    return T.ravel(), P.ravel(), np.repeat(wmu, n_phi) * (2.0 * np.pi / n_phi)
+    nd = int(n_theta) * int(n_phi)
+    th, ph, w = np.empty(nd), np.empty(nd), np.empty(nd)
+    dp = C.POINTER(C.c_double)
+    check(load().aim_rcs_grid(int(n_theta), int(n_phi), th.ctypes.data_as(dp), ph.ctypes.data_as(dp),
+                              w.ctypes.data_as(dp)), "aim_rcs_grid")
+    return th, ph, w
 
 
 def err_thth(sigma, sigma_ref, weight):
-    """Paper eq. (1): relative RMS difference of two bistatic RCS patterns over the sphere."""
-    sigma, sigma_ref = np.asarray(sigma), np.asarray(sigma_ref)
-    num = (np.abs(sigma - sigma_ref) ** 2 * weight).sum(axis=-1)
-    den = (np.abs(sigma_ref) ** 2 * weight).sum(axis=-1)
-    return np.sqrt(num / den)
+    """Eq. (1) (aim_err_thth): relative RMS difference of bistatic RCS patterns
+    [nrhs, ndir] (or [ndir]) against a reference of the same shape."""
+    s = _f64(np.atleast_2d(sigma))
+    r = _f64(np.broadcast_to(np.atleast_2d(sigma_ref), s.shape))
+    w = _f64(weight)
+    out = np.empty(s.shape[0])
+    dp = C.POINTER(C.c_double)
+    check(load().aim_err_thth(s.shape[0], s.shape[1], s.ctypes.data_as(dp), r.ctypes.data_as(dp),
+                              w.ctypes.data_as(dp), out.ctypes.data_as(dp)), "aim_err_thth")
+    return out if np.ndim(sigma) > 1 else out[0]
+
+
+def mie_sigma_thth(radius, theta, phi, k=2.0 * np.pi):
+    """Mie-series sigma_thth of a PEC sphere lit by an x-polarised wave travelling -z
+    (aim_mie_sigma_thth), at directions theta, phi (flattened)."""
+    th, ph = _f64(np.ravel(theta)), _f64(np.ravel(phi))
+    out = np.empty(len(th))
+    dp = C.POINTER(C.c_double)
+    check(load().aim_mie_sigma_thth(float(radius), float(k), len(th), th.ctypes.data_as(dp), ph.ctypes.data_as(dp),
+                                    out.ctypes.data_as(dp)), "aim_mie_sigma_thth")
+    return out

@@ -60,6 +60,12 @@ SIGNATURES = {
     "aim_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.POINTER(aim_solve_info)]),
     "aim_rcs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                           C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "aim_rcs_grid": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                               C.POINTER(C.c_double)]),
+    "aim_err_thth": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                               C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "aim_mie_sigma_thth": (C.c_int, [C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "aim_footprint": (C.c_int, [C.POINTER(aim_mesh), C.c_double, C.c_int, C.c_double, C.c_int, C.c_double,
                                 C.POINTER(C.c_size_t)]),
     "aim_export": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),

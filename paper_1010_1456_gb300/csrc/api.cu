@@ -261,6 +261,30 @@ int aim_rcs(aim_ctx* ctx, const void* X_dev, int nrhs, int ndir, const double* t
   return rcs(ctx, (const double2*)X_dev, nrhs, ndir, theta, phi, sig_tt, sig_pp);
 }
 
+int aim_rcs_grid(int n_theta, int n_phi, double* theta, double* phi, double* weight) {
+  if (n_theta < 1 || n_phi < 1 || n_theta > 100000 || !theta || !phi || !weight) {
+    set_error("aim_rcs_grid: need 1 <= n_theta <= 100000, n_phi >= 1 and non-null outputs");
+    return AIM_EINVAL;
+  }
+  return rcs_grid(n_theta, n_phi, theta, phi, weight);
+}
+
+int aim_err_thth(int nrhs, int ndir, const double* sigma, const double* ref, const double* weight, double* err) {
+  if (nrhs < 1 || ndir < 1 || !sigma || !ref || !weight || !err) {
+    set_error("aim_err_thth: bad arguments");
+    return AIM_EINVAL;
+  }
+  return err_thth(nrhs, ndir, sigma, ref, weight, err);
+}
+
+int aim_mie_sigma_thth(double radius, double k, int ndir, const double* theta, const double* phi, double* sigma) {
+  if (!(radius > 0.0) || !(k > 0.0) || !(k * radius <= 1e4) || ndir < 1 || !theta || !phi || !sigma) {
+    set_error("aim_mie_sigma_thth: need radius > 0, k > 0, k radius <= 1e4, ndir >= 1, non-null arrays");
+    return AIM_EINVAL;
+  }
+  return mie_sigma_thth(radius, k, ndir, theta, phi, sigma);
+}
+
 int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int max_rhs, double cfie_alpha,
                   size_t* bytes) {
   if (!mesh || !bytes || !(h > 0.0) || M < 1 || M > 5 || max_rhs < 1 || !(cfie_alpha > 0.0 && cfie_alpha <= 1.0)) {

@@ -300,6 +300,10 @@ void free_krylov(aim_ctx* c);
 int rhs_planewave(aim_ctx* c, int nrhs, const double* khat, const double* pol, double2* V);
 int rcs(aim_ctx* c, const double2* X, int nrhs, int ndir, const double* theta, const double* phi,
         double* sig_tt, double* sig_pp);
+// rcs_ref.cu (host only)
+int rcs_grid(int n_theta, int n_phi, double* theta, double* phi, double* weight);
+int err_thth(int nrhs, int ndir, const double* sig, const double* ref, const double* w, double* err);
+int mie_sigma_thth(double radius, double k, int ndir, const double* theta, const double* phi, double* sigma);
 // probe.cu
 int probe_fma(int which, double* tflops);
 }  // namespace aim
