@@ -1,13 +1,19 @@
 #!/usr/bin/env python3
-"""Benchmark of the AIM matrix-vector product on synthetic PEC scatterers.
+"""Benchmark of the AIM matrix-vector product and solve on synthetic PEC scatterers.
 
-Default workload: the 4 lambda PEC sphere of the paper's sphere family
-(Section 2.1; geodesic icosphere at mean edge <= lambda/9, N = 58,080 RWG
-unknowns, grid 83^3 zero-padded to 180^3, h = lambda/10, 27-point stencils,
-near radius 3h), one right-hand side, plain complex128 (FP64) product.  A
-step is one full AIM product (projection, five FFT passes, interpolation and
-near correction).  Inputs are resident in HBM; the working set of a product
-(~1.4 GB) exceeds L2 and L2 is also flushed between steps.
+Default workload: the 16 lambda PEC sphere of the paper's sphere family
+(Section 2.1, Table 2; geodesic icosphere at mean edge <= lambda/9,
+N = 908,280 RWG unknowns, grid 323^3 zero-padded to 648^3, h = lambda/10,
+27-point stencils, near radius 3h) with 8 right-hand sides: the largest
+configuration that fits one GPU.  A step is one complex64 AIM product of the
+8 vectors (projection, five FFT passes, interpolation and near correction)
+through the C ABI; the inputs are resident in HBM, the product's working set
+(~60 GB of grids) exceeds L2 and L2 is also flushed between steps.  Beside
+the product the line reports the plain single-RHS FP64 products, the mixed
+(complex64 Arnoldi, FP64-accurate refinement) and plain FP64-accurate CFIE
+solves (alpha = 0.6) of the paper's excitation with err_thth (eq. 1) of
+both against the Mie series, a short serving stream (p50/p99), the
+end-to-end rate through host buffers and the oracle timed on the host.
 
   python bench.py [--gpus N --steps K --warmup W] [--workload NAME] [--impl ours|reference]
 
@@ -46,7 +52,7 @@ WORKLOADS = {
     "pec-sphere-r16lambda-c64-8rhs": ("sphere", 16.0, 8, "c64"),
 }
 PRECISION = {"c128": 2, "f64": 3, "c64": 1}  # AIM_C128, AIM_C128_F64, AIM_C64
-DEFAULT = "pec-sphere-r4lambda-fp64-1rhs"
+DEFAULT = "pec-sphere-r16lambda-c64-8rhs"
 
 
 def mesh_for(kind, size):
@@ -235,53 +241,79 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle timing
-def oracle_matvec_rate(verts, tris, nrhs, budget_s=20.0, sample_rows=192, seed=0):
-    """Oracle products per second on this host, as the oracle stands.
+class OracleSample:
+    """The oracle's AIM product, as it stands, timed on this host in bounded pieces.
 
     The oracle's near-zone setup for all rows of a large problem takes far
-    longer than a bench run, so the near matrix is built for a seeded sample
-    of rows; one product is timed as the full grid part (projection, FFT
-    convolution, interpolation of every row) plus the near SpMV of the sampled
-    rows scaled by N / rows.
+    longer than a bench run, so its near matrix is built for a seeded sample
+    of rows.  One timed piece is a quarter of one right-hand side's product:
+    the projection, padded FFT convolution and interpolation of one grid
+    component (x, y, z current or charge, in turn), plus a quarter of the
+    near SpMV (the sampled rows' time scaled by N / rows).  Four pieces make
+    one product, so products/s = 0.25 x pieces / time.
     """
-    from aim_inputs import random_complex
-    from oracle import aim as oaim
-    from oracle.rwg import RWG
 
-    rwg = RWG(verts, tris)
-    rng = np.random.default_rng(seed)
-    rows = np.sort(rng.choice(rwg.N, min(sample_rows, rwg.N), replace=False))
-    op = oaim.AIMOperator(rwg, K0, H, 2, near_rows=rows)
-    x = random_complex((nrhs, rwg.N), seed + 1)
-    reps, t_far, t_near = 0, 0.0, 0.0
-    t_start = time.perf_counter()
-    while reps < 1 or (time.perf_counter() - t_start < budget_s and reps < 50):
+    def __init__(self, verts, tris, sample_rows=192, seed=0):
+        from oracle import aim as oaim
+        from oracle.rwg import RWG
+
         t0 = time.perf_counter()
-        op.far_matvec(x)
+        rwg = RWG(verts, tris)
+        rng = np.random.default_rng(seed)
+        self.rows = np.sort(rng.choice(rwg.N, min(sample_rows, rwg.N), replace=False))
+        self.op = oaim.AIMOperator(rwg, K0, H, 2, near_rows=self.rows)
+        _ = self.op.Ghat  # the padded spectrum, built once outside the timed pieces
+        self.N = rwg.N
+        self.setup_s = time.perf_counter() - t0
+        self.t = []
+        self.comp = 0
+
+    def piece(self, x):
+        """Time one quarter product of x [1, N]; returns its seconds."""
+        op, c = self.op, self.comp
+        self.comp = (self.comp + 1) % 4
+        t0 = time.perf_counter()
+        op.interpolate(op.convolve(op.project(x, comps=[c])), comps=[c])
         t1 = time.perf_counter()
-        (op.Znear @ x.T)
+        op.Znear @ x[0]
         t2 = time.perf_counter()
-        t_far += t1 - t0
-        t_near += t2 - t1
-        reps += 1
-    per = (t_far + t_near * (rwg.N / len(rows))) / reps
-    return {
-        "value": nrhs / per,
-        "unit": "matvec/s",
-        "cores": os.cpu_count(),
-        "kind": "oracle",
-        "sample": f"{reps} oracle products (NumPy/SciPy FP64, scipy.fft workers={os.cpu_count()}); full grid part, "
-                  f"near SpMV of {len(rows)} seeded rows scaled by N/{len(rows)}",
-    }
+        dt = (t1 - t0) + 0.25 * (t2 - t1) * (self.N / len(self.rows))
+        self.t.append(dt)
+        return dt
+
+    def result(self, warm=0):
+        t = self.t[warm:]
+        return {
+            "value": 0.25 * len(t) / sum(t),
+            "unit": "matvec/s",
+            "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{len(t)} timed quarter products of one RHS (NumPy/SciPy FP64, scipy.fft workers="
+                      f"{os.cpu_count()}): projection, padded FFT convolution and interpolation of one grid "
+                      f"component in turn, plus a quarter of the near SpMV timed on {len(self.rows)} seeded rows "
+                      f"and scaled by N/{len(self.rows)}; 4 pieces = 1 product; oracle setup "
+                      f"{self.setup_s:.0f} s outside the timing",
+        }
+
+
+def oracle_matvec_rate(verts, tris, budget_s=20.0, seed=0):
+    """cpu_baseline: the oracle sample timed for about budget_s seconds (one warm-up piece)."""
+    from aim_inputs import random_complex
+
+    o = OracleSample(verts, tris, seed=seed)
+    x = random_complex((1, o.N), seed + 1)
+    o.piece(x)
+    t_start = time.perf_counter()
+    while len(o.t) < 2 or (time.perf_counter() - t_start < budget_s and len(o.t) < 200):
+        o.piece(x)
+    return o.result(warm=1)
 
 
 # ---------------------------------------------------------------- solves
-def solve_section(g, ctx, kind, size, nrhs, P0, verts=None, tris=None):
-    """Plain (complex128) and mixed (complex64 + FP64 refinement) solves of
-    the workload's excitation, tol 1e-6; err_thth of the mixed RCS against
-    the plain RCS by eq. (1).  For a sphere (closed) also the mixed CFIE
-    solve (alpha = 0.6, Section 2.2) on its own context: set-up time,
-    iterations, and its RCS against the plain EFIE one."""
+def solve_section(g, ctx, kind, size, nrhs, P0):
+    """EFIE solves of an open scatterer (plate): plain native FP64, FP64-accurate
+    and mixed (complex64 + FP64 refinement), tol 1e-6; err_thth of the mixed
+    and FP64-accurate RCS against the plain RCS by eq. (1)."""
     import torch
 
     from aim_inputs import planewave_minus_z_xpol, random_incidence
@@ -337,29 +369,110 @@ def solve_section(g, ctx, kind, size, nrhs, P0, verts=None, tris=None):
                                                                        w)))
         out["speedup_mixed_over_plain"] = out["plain_fp64"]["time_s"] / out["mixed_c64_fp64_refined"]["time_s"]
     out["rcs_directions"] = int(len(th))
-    if kind == "sphere" and verts is not None:
-        stream = torch.cuda.current_stream()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        cc = g.aim_setup(verts, tris, K0, H, M=2, near_radius=3 * H, max_rhs=nrhs, precision=g.AIM_C64,
-                         stream=stream.cuda_stream, cfie_alpha=0.6)
-        setup_s = time.perf_counter() - t0
-        Vc = g.aim_rhs_planewave(cc, kh, po)
-        g.aim_solve(cc, Vc, 1e-6, raise_on_noconv=False)  # first solve: one-time conversions, graph capture
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Xc, info = g.aim_solve(cc, Vc, 1e-6, raise_on_noconv=False)
-        t = time.perf_counter() - t0
-        sc = g.aim_rcs(cc, Xc, th, ph)[0]
-        g.aim_destroy(cc)
-        out["cfie_mixed_alpha0.6"] = {
-            "setup_s": setup_s, "time_s": t, "solves_per_s": 1.0 / t, "iterations": info["iterations"],
-            "efie_iterations": out["mixed_c64_fp64_refined"]["iterations"], "restarts": info["restarts"],
-            "max_rel_res": float(info["rel_res"].max()), "converged": bool(info["converged"].all()),
-            "speedup_over_efie_mixed": out["mixed_c64_fp64_refined"]["time_s"] / t,
-            "err_thth_vs_efie_plain": float(np.max(g.err_thth(sc, sig["plain_fp64"], w))) if "plain_fp64" in sig
-            else None}
     return out
+
+
+def solve_section_sphere(g, verts, tris, radius, nrhs, stream):
+    """CFIE (alpha = 0.6, the paper's formulation for closed bodies, Section 2.2)
+    solves of the sphere, tol 1e-6 on the true residual:
+
+    * mixed: the whole batch in one solve, complex64 Arnoldi products with
+      FP64-accurate (float-float) true residuals at every restart;
+    * plain: the -z pair (x and y polarisation) one right-hand side at a
+      time, every product FP64-accurate (the plain single-RHS FP64 path).
+
+    Right-hand sides: 8 or more -> the four travel directions -z, -x, -y,
+    -(1,1,1)/sqrt3 with theta/phi polarisation (the first two are the -z
+    pair, x and y polarised); 1 -> the x-polarised wave travelling -z.
+    err_thth (eq. 1) of both against the Mie series on the -z pair; first
+    solves (one-time allocations and graph capture included)."""
+    import torch
+
+    from aim_inputs import planewave_minus_z_xpol, sphere_four_directions
+
+    if nrhs >= 8:
+        kh, po = sphere_four_directions()
+        kh, po = kh[:nrhs], po[:nrhs]
+        nrhs = len(kh)
+    else:
+        kh, po = planewave_minus_z_xpol(1)
+        nrhs = 1
+    npair = min(2, nrhs)
+    t0 = time.perf_counter()
+    ctx = g.aim_setup(verts, tris, K0, H, M=2, near_radius=3 * H, max_rhs=nrhs, precision=g.AIM_C64,
+                      stream=stream.cuda_stream, cfie_alpha=0.6)
+    setup_s = time.perf_counter() - t0
+    V = g.aim_rhs_planewave(ctx, kh, po)
+    out = {"formulation": "CFIE alpha = 0.6", "setup_s": setup_s, "nrhs_mixed": nrhs, "tol": 1e-6,
+           "rhs": "four directions -z, -x, -y, -(1,1,1)/sqrt3 x (theta, phi) polarisation" if nrhs >= 8
+           else "x-polarised wave travelling -z"}
+    # mixed: the whole batch
+    g.aim_set_precision(ctx, g.AIM_C64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Xm, info = g.aim_solve(ctx, V, 1e-6, raise_on_noconv=False)
+    tm = time.perf_counter() - t0
+    out["mixed_c64_fp64_refined"] = {"time_s": tm, "solves_per_s": nrhs / tm, "iterations": info["iterations"],
+                                     "restarts": info["restarts"], "max_rel_res": float(info["rel_res"].max()),
+                                     "converged": bool(info["converged"].all())}
+    # plain: one right-hand side at a time, FP64-accurate products
+    g.aim_set_precision(ctx, g.AIM_C128)
+    Xp = torch.empty((npair, ctx.N), dtype=torch.complex128, device=V.device)
+    tp, its, res, conv = 0.0, [], [], []
+    for b in range(npair):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xb, ib = g.aim_solve(ctx, V[b : b + 1].contiguous(), 1e-6, raise_on_noconv=False)
+        tp += time.perf_counter() - t0
+        Xp[b] = Xb[0]
+        its.append(ib["iterations"])
+        res.append(float(ib["rel_res"].max()))
+        conv.append(bool(ib["converged"].all()))
+    out["plain_fp64_accurate_single_rhs"] = {"time_s": tp, "solves": npair, "solves_per_s": npair / tp,
+                                             "iterations": its, "max_rel_res": max(res), "converged": all(conv)}
+    out["speedup_mixed_over_plain_solves_per_s"] = (nrhs / tm) / (npair / tp)
+    # RCS and eq. (1) against the Mie series on the -z pair
+    ka = K0 * radius
+    nth = max(64, 4 * int(np.ceil(ka)))
+    th, ph, w = g.rcs_direction_grid(nth)
+    t0 = time.perf_counter()
+    sm = g.aim_rcs(ctx, Xm[:npair].contiguous(), th, ph)[0]
+    sp = g.aim_rcs(ctx, Xp, th, ph)[0]
+    out["rcs_seconds"] = time.perf_counter() - t0
+    mie = [g.mie_sigma_thth(radius, th, ph), g.mie_sigma_thth(radius, th, ph - np.pi / 2)][:npair]
+    em = [float(g.err_thth(sm[b], mie[b], w)) for b in range(npair)]
+    ep = [float(g.err_thth(sp[b], mie[b], w)) for b in range(npair)]
+    out["rcs_directions"] = int(len(th))
+    out["err_thth_vs_mie"] = {"mixed": em, "plain": ep, "pols": ["x", "y"][:npair]}
+    out["err_thth_mixed_vs_plain"] = [float(g.err_thth(sm[b], sp[b], w)) for b in range(npair)]
+    out["equal_accuracy"] = bool(all(a <= b + 1e-3 for a, b in zip(em, ep)))
+    g.aim_destroy(ctx)
+    del V, Xm, Xp
+    torch.cuda.empty_cache()
+    return out
+
+
+def serve_summary(requests=24, slots=4):
+    """The small serving stream (plates 1-4 lambda EFIE, spheres 0.5-1 lambda CFIE,
+    1-16 RHS): capacity closed-loop, then Poisson arrivals (seed 1) at 0.7 x capacity."""
+    from paper_1010_1456_gb300 import serve
+
+    plates, spheres = SERVE_SIZES["small"]
+    cap_reqs = serve.make_stream(requests, rate=1.0, seed=2, plate_sides=plates, sphere_radii=spheres,
+                                 max_rhs=16, sphere_cfie_alpha=0.6)
+    res, span = serve.Server(slots=slots).run(cap_reqs, realtime=False)
+    cap = serve.summarize(res, span)
+    rate = 0.7 * cap["solves_per_s"]
+    reqs = serve.make_stream(requests, rate=rate, seed=1, plate_sides=plates, sphere_radii=spheres, max_rhs=16,
+                             sphere_cfie_alpha=0.6)
+    srv = serve.Server(slots=slots)
+    res, span = srv.run(reqs, realtime=True)
+    summ = serve.summarize(res, span)
+    return {"stream": f"plates {plates} lambda (EFIE), spheres {spheres} lambda (CFIE alpha 0.6), 1..16 RHS, "
+                      f"{requests} requests, Poisson seed 1 at 0.7 x capacity, {slots} slots",
+            "solves_per_s": summ["solves_per_s"], "p50_s": summ["p50_s"], "p99_s": summ["p99_s"],
+            "capacity_solves_per_s": cap["solves_per_s"], "failed": summ["failed"],
+            "max_rel_res": summ["max_rel_res"], "peak_concurrent": srv.peak_busy}
 
 
 # ---------------------------------------------------------------- serving
@@ -480,11 +593,21 @@ def run_sweep(args):
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
+    """The oracle on this host's cores for the same workload: every step is one
+    bounded piece (a quarter of one right-hand side's product, OracleSample)."""
     if rank != 0:
         return 0
+    from aim_inputs import random_complex
+
     kind, size, nrhs, prec = WORKLOADS[args.workload]
     verts, tris = mesh_for(kind, size)
-    base = oracle_matvec_rate(verts, tris, nrhs, budget_s=max(5.0, 4.0 * args.steps))
+    o = OracleSample(verts, tris)
+    x = random_complex((1, o.N), 1)
+    for _ in range(args.warmup):
+        o.piece(x)
+    for _ in range(args.steps):
+        o.piece(x)
+    base = o.result(warm=args.warmup)
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -493,13 +616,14 @@ def run_reference(args, rank, world):
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": 1e3 / base["value"],
+        "ms_per_step": float(np.mean(o.t[args.warmup:]) * 1e3),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "nrhs": nrhs},
+        "config": {"workload": args.workload, "nrhs": nrhs,
+                   "step": "a quarter of one right-hand side's product (one grid component) on the host"},
         "cpu_baseline": base,
         "e2e": {"value": base["value"], "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -550,10 +674,48 @@ def cufft_comparison(torch, dev, stream, L, nrhs, wide, kernels, flush, reps=5, 
             "cufft_ms": tot / reps, "ours_fft_ms": ours, "speedup_ours": (tot / reps) / ours if ours else None}
 
 
+def time_products(g, torch, ctx, x, y, P, steps, stream, flush):
+    """Mean ms of `steps` products (CUDA events on the context stream, L2 flushed between them)."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        g.aim_matvec(ctx, x, y, precision=P)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
+def plain_single_rhs_products(g, torch, verts, tris, xh, stream, flush, autotune, steps=10):
+    """The plain single-RHS FP64 path: FP64-accurate (float-float) and native
+    FP64 products of one vector on a one-RHS context."""
+    dev = flush.device
+    ctx1 = g.aim_setup(verts, tris, K0, H, M=2, near_radius=3 * H, max_rhs=1, precision=g.AIM_C128,
+                       stream=stream.cuda_stream)
+    x1 = torch.from_numpy(xh[:1].astype(np.complex128)).to(dev)
+    y1 = torch.empty_like(x1)
+    out = {}
+    for name, VP, what in (("fp64_accurate", g.AIM_C128, "float-float arithmetic end to end (FP64-accurate)"),
+                           ("native_fp64", g.AIM_C128_F64, "native FP64 arithmetic end to end")):
+        if autotune:
+            g.aim_autotune(ctx1, VP, nrhs=1, reps=2)
+        for _ in range(3):
+            g.aim_matvec(ctx1, x1, y1, precision=VP)
+        torch.cuda.synchronize()
+        ms = time_products(g, torch, ctx1, x1, y1, VP, steps if VP == g.AIM_C128 else max(3, steps // 3), stream,
+                           flush)
+        out[name] = {"what": what, "matvec_per_s": 1e3 / ms, "ms_per_product": ms}
+    ctx1.close()
+    del x1, y1
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
     import paper_1010_1456_gb300 as g
+    from aim_inputs import random_complex
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -569,7 +731,6 @@ def run_ours(args, rank, world, local_rank):
     setup_s = time.perf_counter() - t0
     n, L, nnz = g.aim_grid_info(ctx)
     N = ctx.N
-    from aim_inputs import random_complex
 
     xh = random_complex((nrhs, N), 1000 + rank).astype(np.complex128 if wide else np.complex64)
     x = torch.from_numpy(xh).to(dev)
@@ -580,7 +741,7 @@ def run_ours(args, rank, world, local_rank):
         chosen, tune_ms = g.aim_autotune(ctx, P, nrhs=nrhs, reps=3)
         tune = {"seconds": round(time.perf_counter() - t0, 2),
                 "kernels": fft_kernel_names(g, chosen, L),
-                "pass_ms": {p_: {FFT_KERNEL_NAMES[k]: round(float(tune_ms[i, k]), 4) for k in (1, 2, 3, 4, 5)
+                "pass_ms": {p_: {FFT_KERNEL_NAMES[k]: round(float(tune_ms[i, k]), 4) for k in FFT_KERNEL_NAMES
                                  if tune_ms[i, k] > 0} for i, p_ in enumerate(g.FFT_PASSES)}}
     else:
         chosen = g.aim_fft_config(ctx, P)
@@ -610,62 +771,8 @@ def run_ours(args, rank, world, local_rank):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms, value = aggregate(sum(step_ms), args.steps, nrhs, world, dev)
 
-    variants = {}
-    for vname, vprec in (("f64", "native FP64 product"), ("c128", "float-float FFT product"), ("c64", "complex64 product")):
-        if vname == prec or not args.variants:
-            continue
-        # the variant's three grid buffers must fit next to what the context holds
-        ve = 8 if vname == "c64" else 16
-        need = ve * 4 * nrhs * (n[0] * n[1] * n[2] + L[2] * n[1] * n[0] + L[2] * L[1] * n[0])
-        if need > 0.8 * torch.cuda.mem_get_info(dev)[0]:
-            variants[vname] = {"what": vprec, "skipped": f"its grids ({need / 1e9:.0f} GB) do not fit in free memory"}
-            continue
-        VP = PRECISION[vname]
-        xv = torch.from_numpy(xh.astype(np.complex64 if vname == "c64" else np.complex128)).to(dev)
-        yv = torch.empty_like(xv)
-        if args.autotune:
-            g.aim_autotune(ctx, VP, nrhs=nrhs, reps=3)
-        for _ in range(3):
-            g.aim_matvec(ctx, xv, yv, precision=VP)
-        torch.cuda.synchronize()
-        vsteps = max(10, args.steps // 4)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(vsteps)]
-        for i in range(vsteps):
-            flush.zero_()
-            evs[i][0].record(stream)
-            g.aim_matvec(ctx, xv, yv, precision=VP)
-            evs[i][1].record(stream)
-        torch.cuda.synchronize()
-        vms = sum(a.elapsed_time(b) for a, b in evs) / vsteps
-        variants[vname] = {"what": vprec, "matvec_per_s": nrhs * 1e3 / vms, "ms_per_step": vms, "steps": vsteps}
-        del xv, yv
-    if args.variants and L[2] == 1:
-        # the same product on the full three-dimensional grid (no plane collapse)
-        ctx3 = g.aim_setup(verts, tris, K0, H, M=2, near_radius=3 * H, max_rhs=nrhs, precision=P,
-                           stream=stream.cuda_stream, planar=False)
-        if args.autotune:
-            g.aim_autotune(ctx3, P, nrhs=nrhs, reps=3)
-        for _ in range(3):
-            g.aim_matvec(ctx3, x, y, precision=P)
-        torch.cuda.synchronize()
-        vsteps = max(10, args.steps // 4)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(vsteps)]
-        for i in range(vsteps):
-            flush.zero_()
-            evs[i][0].record(stream)
-            g.aim_matvec(ctx3, x, y, precision=P)
-            evs[i][1].record(stream)
-        torch.cuda.synchronize()
-        vms = sum(a.elapsed_time(b) for a, b in evs) / vsteps
-        n3, L3, _ = g.aim_grid_info(ctx3)
-        variants["grid_3d"] = {"what": f"same product on the full grid {n3} padded {L3} (no plane collapse)",
-                               "matvec_per_s": nrhs * 1e3 / vms, "ms_per_step": vms, "steps": vsteps}
-        ctx3.close()
-        del ctx3
-    solve = solve_section(g, ctx, kind, size, nrhs, P, verts, tris) if args.solve else None
-
     # end to end through the host-buffer entry point (copies inside the timed region)
-    e2e_steps = max(3, args.steps)
+    e2e_steps = max(3, min(args.steps, 10))
     xp = torch.from_numpy(xh).pin_memory()  # pinned host buffers: the copies run at full link speed
     yp = torch.empty_like(xp).pin_memory()
     g.aim_matvec_host(ctx, xp, precision=P, out=yp)
@@ -674,9 +781,10 @@ def run_ours(args, rank, world, local_rank):
         g.aim_matvec_host(ctx, xp, precision=P, out=yp)
     e2e_s = time.perf_counter() - t0
     e2e = {"value": world * e2e_steps * nrhs / e2e_s, "unit": "matvec/s", "host_buffers": "pinned",
-           "h2d_bytes_per_step": int(xh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
+           "h2d_bytes_per_step": int(xh.nbytes), "d2h_bytes_per_step": int(xh.nbytes), "steps": e2e_steps}
+    del xp, yp
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: the method's algorithmic bytes per launch (pass model)
     pptr = g.aim_export(ctx, g.AIM_EXPORT_PROJ_PTR)
     nent = int(pptr[-1])
     cnt = np.diff(pptr)
@@ -687,8 +795,8 @@ def run_ours(args, rank, world, local_rank):
     projected = 8 * groups if (L[2] > 1 and nrhs < 16) else None
     S = 9 if L[2] == 1 else 27  # stencil nodes (M = 2; a planar grid keeps one plane)
     models = kernel_models(N, n, L, nnz, nent, S, nrhs, e, touched, projected)
-    kernels = {k: {"launches": c, "avg_ms": ms / max(c, 1), "share": ms / max(sum(v[1] for v in prof.values()), 1e-30)}
-               for k, (c, ms) in prof.items()}
+    tot_ms = max(sum(v[1] for v in prof.values()), 1e-30)
+    kernels = {k: {"launches": c, "avg_ms": ms / max(c, 1), "share": ms / tot_ms} for k, (c, ms) in prof.items()}
     dom = max(kernels, key=lambda k: kernels[k]["share"])
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -696,43 +804,70 @@ def run_ours(args, rank, world, local_rank):
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
     alu64 = g.aim_probe_fma_peak(64)
     alu32 = g.aim_probe_fma_peak(32)
-    alu = alu64 if prec == "f64" else alu32
-    bytes_, flops = models.get(dom, (None, None))
-    avg_s = kernels[dom]["avg_ms"] * 1e-3
-    ff32 = ff_fft_flops(dom, n, L, nrhs) if prec == "c128" else None
-    if ff32 is not None:
-        # float-float pass: bound by the FP32 pipes that carry the emulated FP64 arithmetic
-        roof = {"bound": "alu", "achieved": ff32 / avg_s / 1e12, "peak": alu32, "unit": "TFLOP/s",
-                "peak_source": "FP32 FMA probe (aim_probe_fma_peak), this run",
-                "achieved_counts": "FP32 flops of the float-float butterflies (bench.ff_fft_flops model)",
-                "fp64_equivalent_tflops": flops / avg_s / 1e12, "native_fp64_peak": alu64}
-        roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["kernel"] = dom
-        roof["algorithmic_bytes"] = bytes_
-        roof["algorithmic_flops"] = ff32
-        roof["traffic"] = ncu_traffic(args.workload, dom)
-    elif bytes_ is not None:
-        intensity = flops / bytes_
-        ridge = alu * 1e12 / (hbm * 1e9)
-        if intensity > ridge:
-            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": alu, "unit": "TFLOP/s",
-                    "peak_source": f"FP{'64' if prec == 'f64' else '32'} FMA probe (aim_probe_fma_peak), this run"}
-        else:
-            roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
-                    "peak_source": hbm_src}
-        roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["kernel"] = dom
-        roof["algorithmic_bytes"] = bytes_
-        roof["algorithmic_flops"] = flops
-        roof["traffic"] = ncu_traffic(args.workload, dom)
-    else:
-        roof = None
     for k, v in kernels.items():
         if k in models:
             b, f = models[k]
-            s = v["avg_ms"] * 1e-3
-            v["GB/s"] = b / s / 1e9
-            v["TFLOP/s"] = f / s / 1e12
+            s_ = v["avg_ms"] * 1e-3
+            v["GB/s"] = b / s_ / 1e9
+            v["hbm_frac"] = b / s_ / 1e9 / hbm
+            v["TFLOP/s"] = f / s_ / 1e12
+    roof = None
+    if dom in models:
+        bytes_, flops = models[dom]
+        avg_s = kernels[dom]["avg_ms"] * 1e-3
+        roof = {"bound": "hbm", "kernel": dom, "achieved": bytes_ / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": bytes_ / avg_s / 1e9 / hbm, "peak_source": hbm_src, "traffic": ncu_traffic(args.workload, dom),
+                "algorithmic_bytes": bytes_, "avg_launch_ms": kernels[dom]["avg_ms"],
+                "bytes_model": "pass model: G = 4 x nrhs grids; x pass reads and writes G Lz Ly nx complex values "
+                               "plus the Ghat octant; strided passes read n_in and write n_out samples per pencil"}
+        if prec == "c128":
+            ff32 = ff_fft_flops(dom, n, L, nrhs)
+            if ff32 is not None:
+                roof["fp32_issue"] = {"achieved_tflops": ff32 / avg_s / 1e12, "peak_tflops": alu32,
+                                      "frac": ff32 / avg_s / 1e12 / alu32,
+                                      "counts": "FP32 flops of the float-float butterflies (ff_fft_flops)"}
+        else:
+            roof["fp32_issue"] = {"achieved_tflops": flops / avg_s / 1e12, "peak_tflops": alu32 if prec == "c64"
+                                  else alu64, "frac": flops / avg_s / 1e12 / (alu32 if prec == "c64" else alu64),
+                                  "counts": "5 L log2 L flops per length-L transform (+ the spectral product)"}
+        roof["all_kernels_hbm_frac"] = sum(models[k][0] for k in kernels if k in models) / (
+            sum(kernels[k]["avg_ms"] for k in kernels if k in models) * 1e-3) / 1e9 / hbm
+
+    variants = None
+    if args.variants:
+        if nrhs > 1:
+            variants = plain_single_rhs_products(g, torch, verts, tris, xh, stream, flush, args.autotune)
+        else:
+            variants = {}
+            for vname, VP in (("native_fp64", g.AIM_C128_F64), ("fp64_accurate", g.AIM_C128), ("c64", g.AIM_C64)):
+                if VP == P:
+                    continue
+                xv = torch.from_numpy(xh.astype(np.complex64 if VP == g.AIM_C64 else np.complex128)).to(dev)
+                yv = torch.empty_like(xv)
+                if args.autotune:
+                    g.aim_autotune(ctx, VP, nrhs=nrhs, reps=3)
+                for _ in range(3):
+                    g.aim_matvec(ctx, xv, yv, precision=VP)
+                torch.cuda.synchronize()
+                ms = time_products(g, torch, ctx, xv, yv, VP, max(10, args.steps // 4), stream, flush)
+                variants[vname] = {"matvec_per_s": nrhs * 1e3 / ms, "ms_per_product": ms}
+                del xv, yv
+    cufft = cufft_comparison(torch, dev, stream, L, nrhs, wide, kernels, flush) if args.cufft else None
+    ctx.close()
+    del ctx, x, y
+    torch.cuda.empty_cache()
+
+    solve = None
+    if args.solve:
+        if kind == "sphere":
+            solve = solve_section_sphere(g, verts, tris, size, nrhs, stream)
+        else:
+            c2 = g.aim_setup(verts, tris, K0, H, M=2, near_radius=3 * H, max_rhs=nrhs, precision=P,
+                             stream=stream.cuda_stream)
+            solve = solve_section(g, c2, kind, size, nrhs, P)
+            c2.close()
+            torch.cuda.empty_cache()
+    serving = serve_summary() if args.serve_extra else None
 
     line = {
         "metric": METRIC,
@@ -745,35 +880,32 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"f64": "f64", "c128": "f64 (FFT passes: f32 float-float pairs)", "c64": "f32"}[prec],
-        "variants": variants,
+        "dtype": {"f64": "f64", "c128": "f64 in and out, float-float (f32 pairs) throughout", "c64": "c64 (f32)"}[prec],
         "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "grid": n, "padded": L, "nnz_near": nnz, "nrhs": nrhs,
-                   "M": 2, "h_lambda": H, "near_radius_h": 3, "l2": "flushed between steps (256 MB write)",
+                   "formulation": "EFIE", "M": 2, "h_lambda": H, "near_radius_h": 3,
+                   "l2": "inputs (60 GB of grids at the 16 lambda sphere) exceed L2; also flushed between steps "
+                         "(256 MB write)",
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
                    "fft_kernels": fft_kernel_names(g, chosen, L)},
-        "autotune": tune,
-        "cufft_comparison": cufft_comparison(torch, dev, stream, L, nrhs, wide, kernels, flush) if args.cufft else None,
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),
-        "kernels": kernels,
+        "plain_fp64_single_rhs": variants if nrhs > 1 else None,
+        "variants": variants if nrhs == 1 else None,
         "solve": solve,
+        "serving": serving,
+        "autotune": tune,
+        "cufft_comparison": cufft,
+        "kernels": kernels,
         "fp64_fma_tflops": alu64,
         "fp32_fma_tflops": alu32,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        if float(np.prod(L)) * 16 * 4 * nrhs > 16e9:
-            # the oracle holds its four padded complex128 grids per RHS in host memory
-            line["cpu_baseline"] = {"value": None, "unit": "matvec/s", "kind": "oracle", "cores": os.cpu_count(),
-                                    "sample": "not run: the oracle's padded FP64 grids "
-                                              f"({float(np.prod(L)) * 64 * nrhs / 1e9:.0f} GB) exceed the host budget"}
-        else:
-            line["cpu_baseline"] = oracle_matvec_rate(verts, tris, nrhs, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = oracle_matvec_rate(verts, tris, budget_s=args.cpu_budget)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     return 0
 
 
@@ -788,8 +920,9 @@ def main():
     ap.add_argument("--solve", type=int, default=1, help="1: also time plain and mixed solves")
     ap.add_argument("--variants", type=int, default=1, help="1: also time the other product precisions")
     ap.add_argument("--autotune", type=int, default=1, help="1: autotune the FFT kernels before timing")
-    ap.add_argument("--cufft", type=int, default=1, help="1: also time the unpruned cuFFT convolution")
+    ap.add_argument("--cufft", type=int, default=1, help="1: also time the unpruned cuFFT convolution (grids <= 8 GB)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--serve-extra", type=int, default=1, help="1: add the small serving stream's p50/p99")
     ap.add_argument("--serve", action="store_true", help="run the serving stream instead of the product benchmark")
     ap.add_argument("--sweep", action="store_true", help="matvec time against N over plates and spheres")
     ap.add_argument("--sweep-max", type=float, default=0.0, help="largest size (lambda) in the sweep; 0: all")

@@ -73,3 +73,21 @@ def test_replica_aggregation_takes_the_slowest_rank():
 def test_single_rank_aggregation_is_local():
     total, value = bench.aggregate(200.0, steps=20, nrhs=1, world=1)
     assert total == 200.0 and value == pytest.approx(100.0)
+
+
+def test_oracle_sample_pieces_make_up_products():
+    """The oracle's bounded timing sample: pieces cycle through the four grid
+    components, and four pieces count as one product."""
+    from aim_inputs import plate_mesh, random_complex
+
+    v, t = plate_mesh(1.0, 9)
+    o = bench.OracleSample(v, t, sample_rows=16)
+    x = random_complex((1, o.N), 3)
+    comps = []
+    for _ in range(5):
+        comps.append(o.comp)
+        o.piece(x)
+    assert comps == [0, 1, 2, 3, 0]
+    r = o.result(warm=1)
+    assert r["value"] == pytest.approx(0.25 * 4 / sum(o.t[1:]))
+    assert r["kind"] == "oracle" and r["cores"] == os.cpu_count() and r["unit"] == "matvec/s"
