@@ -82,7 +82,8 @@ template <typename R> struct PrecData {
   R* pnode_w = nullptr;           // [nent][4] projection weights, node-ordered
   cplx<R>* ghat = nullptr;        // octant [Lz/2+1][Ly/2+1][Lx/2+1], scaled by 1/(LxLyLz)
   cplx<R>* near_val = nullptr;    // [nnz]
-  cplx<R>* tw[3] = {nullptr, nullptr, nullptr};  // forward twiddles exp(-2 pi i t / L_d)
+  cplx<R>* tw[3] = {nullptr, nullptr, nullptr};  // forward twiddles exp(-2 pi i t / L_d), t < L_d, then the
+                                                 // four-step factors as [L1][L2] and [L2][L1] (3 L_d entries)
   cplx<R>* grid0 = nullptr;       // [B][4][nz][ny][nx]  Q, then Phi
   cplx<R>* grid1 = nullptr;       // [B][4][Lz][ny][nx]
   cplx<R>* grid2 = nullptr;       // [B][4][Lz][Ly][nx]
@@ -250,6 +251,9 @@ int convert_c64_to_c128(aim_ctx* c, const float2* in, double2* out, int64_t coun
 // grid0 (Q) -> grid0 (Phi) of each precision, G = 4 * nrhs grids
 // Phi's grid: grid2 for a context that projects over node groups, else grid0.
 template <class T> inline T* phi_grid(const aim_ctx* c, T* g0, T* g2) { return c->sparse_proj ? g2 : g0; }
+// The four-step split L = L1 * L2 of a padded length that has four-step
+// kernels (false for the Stockham-only lengths).
+bool fourstep_split(int L, int* L1, int* L2);
 int fft_convolve_c64(aim_ctx* c, int G);
 int fft_convolve_c128(aim_ctx* c, int G);
 int fft_convolve_ff(aim_ctx* c, int G);

@@ -315,6 +315,16 @@ static int launch_x(aim_ctx* c, const char* name, typename P::S* buf, XArgs a, c
   return launch_check(c, name);
 }
 
+bool fourstep_split(int L, int* L1, int* L2) {
+  switch (L) {
+#define AIM_CASE(LL, A1, A2) \
+  case LL: *L1 = A1; *L2 = A2; return true;
+    AIM_FOURSTEP_LENGTHS(AIM_CASE)
+#undef AIM_CASE
+    default: return false;
+  }
+}
+
 int fft_policy_of(int precision) { return precision == AIM_C64 ? 0 : precision == AIM_C128_F64 ? 1 : 2; }
 
 int fft_kernel_for(const aim_ctx* c, int pol, int pass) {

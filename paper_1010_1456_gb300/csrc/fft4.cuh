@@ -11,6 +11,13 @@
 // index arithmetic inside the register DFTs is resolved at compile time.  These kernels serve the padded lengths in
 // kFourStepLengths; other lengths use the Stockham kernels of fft.cu.
 //
+// Twiddles: twL holds w_L^t for t < L (the Stockham kernels' table), then
+// the same factors w_L^(k1 n2) laid out twice for the four-step kernels: as
+// [k1][n2] at twL + L (step A: the lanes of a warp take consecutive n2) and
+// as [n2][k1] at twL + 2L (the x pass's step B: consecutive k1), so each
+// warp-wide twiddle load touches one or two cache lines instead of one line
+// per lane.
+//
 // fft4_strided: the z and y passes (pencil along a strided axis, TX
 // consecutive x columns per block, as in fft.cu).
 // fft4_x: the fused x pass: forward transform of the nx zero-padded samples
@@ -99,7 +106,7 @@ __device__ __forceinline__ void strided_body(const typename P::S* __restrict__ i
     });
     RegDFT<P, L1, INV>::run(v);
     if (n2 > 0)
-      static_for<1, L1>([&](auto k1) { v[k1] = P::mul(v[k1], P::conj_if(P::ld(twL[n2 * decltype(k1)::value]), INV)); });
+      static_for<1, L1>([&](auto k1) { v[k1] = P::mul(v[k1], P::conj_if(P::ld(twL[L + decltype(k1)::value * L2 + n2]), INV)); });
     S* y = b + t * L * TX;
     static_for<0, L1>([&](auto k1) { y[(decltype(k1)::value * L2 + n2) * TX + c] = P::st(v[k1]); });
   }
@@ -195,7 +202,7 @@ __global__ void __launch_bounds__(256, x_min_blocks<P, L1 * L2>()) fft4_x(typena
         v[n1] = p < a.nx ? P::ld(src[p]) : P::zero();
       });
       RegDFT<P, L1, false>::run(v);
-      if (n2 > 0) static_for<1, L1>([&](auto k1) { v[k1] = P::mul(v[k1], P::ld(twL[n2 * decltype(k1)::value])); });
+      if (n2 > 0) static_for<1, L1>([&](auto k1) { v[k1] = P::mul(v[k1], P::ld(twL[L + decltype(k1)::value * L2 + n2])); });
       S* y = tile + pc * PA + n2;
       static_for<0, L1>([&](auto k1) { y[decltype(k1)::value * RA] = P::st(v[k1]); });
     }
@@ -212,7 +219,7 @@ __global__ void __launch_bounds__(256, x_min_blocks<P, L1 * L2>()) fft4_x(typena
       static_for<0, L2>([&](auto k2) { w[k2] = P::mul(w[k2], P::ld(gg[L1 * decltype(k2)::value])); });
       RegDFT<P, L2, true>::run(w);
       if (k1 > 0)
-        static_for<1, L2>([&](auto n2) { w[n2] = P::mul(w[n2], P::conj_if(P::ld(twL[k1 * decltype(n2)::value]), true)); });
+        static_for<1, L2>([&](auto n2) { w[n2] = P::mul(w[n2], P::conj_if(P::ld(twL[2 * L + decltype(n2)::value * L1 + k1]), true)); });
       static_for<0, L2>([&](auto n2) { y[decltype(n2)::value] = P::st(w[n2]); });
     }
     __syncthreads();
@@ -283,7 +290,7 @@ __global__ void __launch_bounds__(256, x_min_blocks<P, L1 * L2>()) fft4_x_groups
           v[n1] = p < a.nx ? P::ld(src[p]) : P::zero();
         });
         RegDFT<P, L1, false>::run(v);
-        if (n2 > 0) static_for<1, L1>([&](auto k1) { v[k1] = P::mul(v[k1], P::ld(twL[n2 * decltype(k1)::value])); });
+        if (n2 > 0) static_for<1, L1>([&](auto k1) { v[k1] = P::mul(v[k1], P::ld(twL[L + decltype(k1)::value * L2 + n2])); });
         S* y = tile + lp * PA + n2;
         static_for<0, L1>([&](auto k1) { y[decltype(k1)::value * RA] = P::st(v[k1]); });
       }
@@ -302,7 +309,7 @@ __global__ void __launch_bounds__(256, x_min_blocks<P, L1 * L2>()) fft4_x_groups
         static_for<0, L2>([&](auto k2) { w[k2] = P::mul(w[k2], P::ld(gg[L1 * decltype(k2)::value])); });
         RegDFT<P, L2, true>::run(w);
         if (k1 > 0)
-          static_for<1, L2>([&](auto n2) { w[n2] = P::mul(w[n2], P::conj_if(P::ld(twL[k1 * decltype(n2)::value]), true)); });
+          static_for<1, L2>([&](auto n2) { w[n2] = P::mul(w[n2], P::conj_if(P::ld(twL[2 * L + decltype(n2)::value * L1 + k1]), true)); });
         static_for<0, L2>([&](auto n2) { y[decltype(n2)::value] = P::st(w[n2]); });
       }
     }

@@ -625,20 +625,30 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
       set_error("aim_setup: padded length is not 2,3,5-smooth");
       return AIM_EINVAL;
     }
+    // w^t for t < L, then (four-step lengths) w^(k1 n2) as [k1][n2] and as [n2][k1]
     const int L = c->L[d];
-    std::vector<double> t64(2 * (size_t)L);
-    std::vector<float> t32(2 * (size_t)L), tff(4 * (size_t)L);
-    for (int t = 0; t < L; ++t) {
-      const double ang = (2.0 * kPi * t) / L;
-      t64[2 * t] = std::cos(ang);
-      t64[2 * t + 1] = -std::sin(ang);
+    int L1 = 0, L2 = 0;
+    const bool four = fourstep_split(L, &L1, &L2);
+    std::vector<double> t64(6 * (size_t)L, 0.0);
+    std::vector<float> t32(6 * (size_t)L, 0.f), tff(12 * (size_t)L, 0.f);
+    const auto put = [&](size_t slot, long long t) {
+      const double ang = (2.0 * kPi * (double)(t % L)) / L;
+      t64[2 * slot] = std::cos(ang);
+      t64[2 * slot + 1] = -std::sin(ang);
       for (int q = 0; q < 2; ++q) {
-        const float hi = (float)t64[2 * t + q];
-        t32[2 * t + q] = hi;
-        tff[4 * t + 2 * q] = hi;
-        tff[4 * t + 2 * q + 1] = (float)(t64[2 * t + q] - (double)hi);
+        const float hi = (float)t64[2 * slot + q];
+        t32[2 * slot + q] = hi;
+        tff[4 * slot + 2 * q] = hi;
+        tff[4 * slot + 2 * q + 1] = (float)(t64[2 * slot + q] - (double)hi);
       }
-    }
+    };
+    for (int t = 0; t < L; ++t) put(t, t);
+    if (four)
+      for (int k1 = 0; k1 < L1; ++k1)
+        for (int n2 = 0; n2 < L2; ++n2) {
+          put((size_t)L + (size_t)k1 * L2 + n2, (long long)k1 * n2);
+          put(2 * (size_t)L + (size_t)n2 * L1 + k1, (long long)k1 * n2);
+        }
     AIM_TRY(upload((void**)&c->p64.tw[d], t64.data(), t64.size() * sizeof(double)));
     AIM_TRY(upload((void**)&c->p32.tw[d], t32.data(), t32.size() * sizeof(float)));
     AIM_TRY(upload((void**)&c->pff.tw[d], tff.data(), tff.size() * sizeof(float)));
