@@ -95,6 +95,12 @@ typedef struct {
                       closed surface with outward-oriented triangles (vertex order (r0, r1, r2)
                       with (r1 - r0) x (r2 - r0) pointing out); aim_setup returns AIM_EINVAL for an
                       open mesh.  Products, right-hand sides and solves then use the CFIE. */
+  size_t mem_budget; /* 0 (default): no limit.  Otherwise the most device memory, in bytes, the
+                      context may plan to hold: aim_setup returns AIM_ENOMEM, before it allocates
+                      anything, when aim_footprint's estimate for this mesh, max_rhs, cfie_alpha
+                      and precision exceeds it; a later product in a precision whose grids that
+                      estimate does not include (see aim_footprint) returns AIM_ENOMEM when its
+                      grids would take the planned total above the budget. */
 } aim_opts;
 
 /* Per-solve report. rel_res and iters are caller arrays of length nrhs. */
@@ -120,7 +126,9 @@ void aim_default_opts(aim_opts* opts);
  *   setting is M = 3, its reference solutions go to M = 5), near_radius >= 0.
  *   Synchronises.
  * Returns AIM_EINVAL for a non-manifold or degenerate mesh, a mesh without
- * interior edges, or a grid whose padded size exceeds 2^31 points.
+ * interior edges, vertex coordinates that are NaN or infinite, or a grid
+ * whose padded size exceeds 2^31 points; AIM_ENOMEM when opts.mem_budget is
+ * set and the footprint estimate exceeds it.
  */
 int aim_setup(const aim_mesh* mesh, double k, double h, int M, double near_radius,
               const aim_opts* opts, aim_ctx** out);
@@ -144,6 +152,7 @@ int aim_grid_info(const aim_ctx* ctx, int32_t n[3], int32_t L[3], int64_t* nnz_n
  * (paper Section 2.1 excitation), collapsed Gauss-Legendre 4x4 rule per
  * triangle; with CFIE, alpha V_m + (1 - alpha) int f_m . (n x (khat x pol))
  * exp(-j k khat . r) dS.  khat, pol: host [nrhs][3].  V_dev: device c128 [nrhs][N].
+ * AIM_EINVAL if khat or pol holds NaN or an infinity.
  */
 int aim_rhs_planewave(aim_ctx* ctx, int nrhs, const double* khat, const double* pol, void* V_dev);
 
@@ -178,7 +187,9 @@ int aim_matvec_host(aim_ctx* ctx, const void* x_host, void* y_host, int nrhs, in
  * around a complex64 inner solve.  Stops when every right-hand
  * side has ||V - Z~ X|| / ||V|| <= tol (true residual) or after opts.maxit
  * steps (AIM_ENOCONV).  V_dev, X_dev: device c128 [nrhs][N]; X is
- * overwritten (initial guess 0).  info may be NULL.  Synchronises.
+ * overwritten (initial guess 0).  info may be NULL.  Synchronises.  A
+ * right-hand side holding NaN or an infinity is rejected with AIM_EINVAL
+ * before any iteration (its norm, computed first, is not finite).
  */
 int aim_solve(aim_ctx* ctx, const void* V_dev, void* X_dev, int nrhs, double tol, aim_solve_info* info);
 
@@ -220,10 +231,16 @@ int aim_err_thth(int nrhs, int ndir, const double* sigma, const double* ref, con
  */
 int aim_mie_sigma_thth(double radius, double k, int ndir, const double* theta, const double* phi, double* sigma);
 
-/* Bytes of device memory a context for this mesh would hold (estimate, +-10 %);
- * cfie_alpha as in aim_opts (1: EFIE; < 1 adds the MFIE arrays). */
+/* Bytes of device memory a context for this mesh would hold (estimate, +-10 %)
+ * once it has solved with the solver precision `precision` (as aim_opts):
+ * AIM_C64 counts the complex64 grids and the float-float grids of the
+ * FP64-accurate refinement, AIM_C128 the float-float grids, AIM_C128_F64 the
+ * native FP64 grids; cfie_alpha as in aim_opts (1: EFIE; < 1 adds the MFIE
+ * arrays).  Not included: the fixed 64 MiB array of aim_matvec_c64_noalloc.
+ * Host only.  AIM_EINVAL for a bad argument or a mesh with non-finite vertex
+ * coordinates. */
 int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int max_rhs, double cfie_alpha,
-                  size_t* bytes);
+                  int precision, size_t* bytes);
 
 /*
  * Copy internal setup arrays to host memory for inspection and testing.

@@ -93,7 +93,7 @@ def aim_default_opts():
 
 
 def aim_setup(verts, tris, k, h, M=2, near_radius=None, precision=AIM_C128, restart=50, maxit=3000,
-              check_every=5, max_rhs=1, stream=None, planar=True, verbose=False, cfie_alpha=1.0):
+              check_every=5, max_rhs=1, stream=None, planar=True, verbose=False, cfie_alpha=1.0, mem_budget=0):
     """Build a context (host FP64 setup + device spectrum); see aim_setup in aim.h."""
     lib = load()
     mesh, keep = _mesh(verts, tris)
@@ -107,6 +107,7 @@ def aim_setup(verts, tris, k, h, M=2, near_radius=None, precision=AIM_C128, rest
     o.planar = 1 if planar else 0
     o.verbose = 1 if verbose else 0
     o.cfie_alpha = float(cfie_alpha)
+    o.mem_budget = int(mem_budget)
     h_ = C.c_void_p()
     r = 3.0 * h if near_radius is None else float(near_radius)
     check(lib.aim_setup(C.byref(mesh), float(k), float(h), int(M), r, C.byref(o), C.byref(h_)), "aim_setup")
@@ -242,12 +243,13 @@ def aim_rcs(ctx, X, theta, phi):
     return stt, spp
 
 
-def aim_footprint(verts, tris, h, M=2, near_radius=None, max_rhs=1, cfie_alpha=1.0):
+def aim_footprint(verts, tris, h, M=2, near_radius=None, max_rhs=1, cfie_alpha=1.0, precision=AIM_C128):
+    """Estimated device bytes of a context that has solved with solver precision ``precision``."""
     mesh, keep = _mesh(verts, tris)
     b = C.c_size_t()
     r = 3.0 * h if near_radius is None else float(near_radius)
-    check(load().aim_footprint(C.byref(mesh), float(h), int(M), r, int(max_rhs), float(cfie_alpha), C.byref(b)),
-          "aim_footprint")
+    check(load().aim_footprint(C.byref(mesh), float(h), int(M), r, int(max_rhs), float(cfie_alpha), int(precision),
+                               C.byref(b)), "aim_footprint")
     return int(b.value)
 
 

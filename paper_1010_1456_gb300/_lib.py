@@ -31,6 +31,7 @@ class aim_opts(C.Structure):
         ("stream", C.c_void_p),
         ("planar", C.c_int),
         ("cfie_alpha", C.c_double),
+        ("mem_budget", C.c_size_t),
     ]
 
 
@@ -67,7 +68,7 @@ SIGNATURES = {
     "aim_mie_sigma_thth": (C.c_int, [C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double),
                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "aim_footprint": (C.c_int, [C.POINTER(aim_mesh), C.c_double, C.c_int, C.c_double, C.c_int, C.c_double,
-                                C.POINTER(C.c_size_t)]),
+                                C.c_int, C.POINTER(C.c_size_t)]),
     "aim_export": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
     "aim_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "aim_profile": (C.c_int, [C.c_void_p, C.c_int]),

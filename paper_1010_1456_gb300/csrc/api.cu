@@ -68,6 +68,90 @@ static int check_device() {
   return AIM_OK;
 }
 
+static bool mesh_finite(const aim_mesh* mesh) {
+  for (long long i = 0; i < 3LL * mesh->nv; ++i)
+    if (!std::isfinite(mesh->verts[i])) return false;
+  return true;
+}
+
+// Device bytes of a context for this mesh once it has solved in `precision`
+// (see aim_footprint in aim.h).
+int footprint_estimate(const aim_mesh* mesh, double h, int M, double near_radius, int max_rhs, double alpha,
+                       int precision, size_t* bytes) {
+  (void)near_radius;
+  if (mesh->nv < 1 || mesh->nt < 1 || !mesh->verts || !mesh->tris) {
+    set_error("aim_footprint: empty mesh");
+    return AIM_EINVAL;
+  }
+  if (!mesh_finite(mesh)) {
+    set_error("aim_footprint: a vertex coordinate is NaN or infinite");
+    return AIM_EINVAL;
+  }
+  // grid box from the vertices' bounding box, basis count from the edge count
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < mesh->nv; ++i)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], mesh->verts[3 * i + d]);
+      hi[d] = std::max(hi[d], mesh->verts[3 * i + d]);
+    }
+  long long n[3], L[3];
+  for (int d = 0; d < 3; ++d) {
+    n[d] = (long long)std::floor(hi[d] / h) - (long long)std::floor(lo[d] / h) + M + 1;
+    long long m = 2 * n[d] - 1, x;
+    for (L[d] = m;; ++L[d]) {
+      x = L[d];
+      for (int p : {2, 3, 5})
+        while (x % p == 0) x /= p;
+      if (x == 1) break;
+    }
+  }
+  const long long N = (long long)(1.5 * mesh->nt);  // interior edges of a closed surface
+  const long long S = (long long)(M + 1) * (M + 1) * (M + 1);
+  const long long nnz = N * 100LL;  // generous near-row length
+  const long long nc = n[0] * n[1] * n[2];
+  const double cells = (double)max_rhs * 4 * (nc + L[2] * n[1] * n[0] + L[2] * L[1] * n[0]);
+  double b = 0;
+  b += (double)N * 4 * S * (8 + 4) * 2;                               // weights f64/f32 + node lists
+  b += (double)nnz * (16 + 8 + 4);                                     // near values + columns
+  b += (double)(L[0] / 2 + 1) * (L[1] / 2 + 1) * (L[2] / 2 + 1) * 24; // spectra
+  b += (double)L[0] * L[1] * L[2] * 32;                                // setup transform scratch
+  // pass grids of the precisions a solve in `precision` allocates
+  b += cells * (precision == AIM_C64 ? 8 + 16 : 16);
+  b += (double)max_rhs * N * (16 * 53 + 48);                           // Krylov basis (m = 50) and vectors
+  if (precision != AIM_C128_F64)
+    b += (double)N * 4 * S * 8 * 2 + (double)nnz * 16;                 // float-float weights and near values
+  if (max_rhs >= kRhsLanesMin) b += (double)max_rhs * (4.0 * nc + N) * 16;  // RHS-minor copies of Phi and x
+  b += (double)mesh->nt * 60 * (144 + 12) + (double)nnz * 56;          // near-fill scratch at setup (peak)
+  if (alpha < 1.0)  // MFIE weights in three precisions, MFIE pair blocks and halves at setup
+    b += (double)N * 3 * S * (8 + 4 + 8) + (double)mesh->nt * 60 * 144 + (double)nnz * 32;
+  *bytes = (size_t)b;
+  return AIM_OK;
+}
+
+// Grid bytes a product in `precision` allocates on first use, and whether
+// the setup's estimate (solver precision opts.precision) already counts them.
+size_t grid_bytes(const aim_ctx* c, int precision) {
+  const double cells = (double)c->max_rhs * 4 *
+                       ((double)c->n[0] * c->n[1] * c->n[2] + (double)c->L[2] * c->n[1] * c->n[0] +
+                        (double)c->L[2] * c->L[1] * c->n[0]);
+  return (size_t)(cells * (precision == AIM_C64 ? 8 : 16));
+}
+
+int budget_grids(aim_ctx* c, int precision) {
+  if (c->opts.mem_budget == 0) return AIM_OK;
+  const int sp = c->opts.precision;
+  const bool planned = precision == sp || (sp == AIM_C64 && precision == AIM_C128);
+  if (planned) return AIM_OK;
+  const size_t need = grid_bytes(c, precision);
+  if (c->planned_bytes + need > c->opts.mem_budget) {
+    set_error("product grids of " + std::to_string(need) + " bytes would take the planned total above mem_budget (" +
+              std::to_string(c->opts.mem_budget) + " bytes)");
+    return AIM_ENOMEM;
+  }
+  c->planned_bytes += need;
+  return AIM_OK;
+}
+
 }  // namespace aim
 
 using namespace aim;
@@ -128,6 +212,23 @@ int aim_setup(const aim_mesh* mesh, double k, double h, int M, double near_radiu
     set_error("aim_setup: restart in 1..200, max_rhs in 1..256, maxit >= 1, check_every >= 1");
     return AIM_EINVAL;
   }
+  if (!mesh || mesh->nv < 1 || mesh->nt < 1 || !mesh->verts || !mesh->tris) {
+    set_error("aim_setup: empty mesh");
+    return AIM_EINVAL;
+  }
+  if (!mesh_finite(mesh)) {
+    set_error("aim_setup: a vertex coordinate is NaN or infinite");
+    return AIM_EINVAL;
+  }
+  size_t planned = 0;
+  if (o.mem_budget > 0) {
+    AIM_TRY(footprint_estimate(mesh, h, M, near_radius, o.max_rhs, o.cfie_alpha, o.precision, &planned));
+    if (planned > o.mem_budget) {
+      set_error("aim_setup: footprint estimate " + std::to_string(planned) + " bytes exceeds mem_budget " +
+                std::to_string(o.mem_budget));
+      return AIM_ENOMEM;
+    }
+  }
   AIM_TRY(check_device());
   aim_ctx* c = new (std::nothrow) aim_ctx();
   if (!c) return AIM_ENOMEM;
@@ -138,6 +239,7 @@ int aim_setup(const aim_mesh* mesh, double k, double h, int M, double near_radiu
   c->opts = o;
   c->max_rhs = o.max_rhs;
   c->stream = (cudaStream_t)o.stream;
+  c->planned_bytes = planned;
   cudaGetDevice(&c->device);
   int rc = AIM_OK;
   try {
@@ -205,6 +307,11 @@ int aim_rhs_planewave(aim_ctx* ctx, int nrhs, const double* khat, const double* 
     set_error("aim_rhs_planewave: bad arguments");
     return AIM_EINVAL;
   }
+  for (int i = 0; i < 3 * nrhs; ++i)
+    if (!std::isfinite(khat[i]) || !std::isfinite(pol[i])) {
+      set_error("aim_rhs_planewave: khat or pol holds NaN or an infinity");
+      return AIM_EINVAL;
+    }
   return rhs_planewave(ctx, nrhs, khat, pol, (double2*)V_dev);
 }
 
@@ -258,6 +365,11 @@ int aim_rcs(aim_ctx* ctx, const void* X_dev, int nrhs, int ndir, const double* t
     set_error("aim_rcs: bad arguments");
     return AIM_EINVAL;
   }
+  for (int d = 0; d < ndir; ++d)
+    if (!std::isfinite(theta[d]) || !std::isfinite(phi[d])) {
+      set_error("aim_rcs: a direction angle is NaN or infinite");
+      return AIM_EINVAL;
+    }
   return rcs(ctx, (const double2*)X_dev, nrhs, ndir, theta, phi, sig_tt, sig_pp);
 }
 
@@ -286,47 +398,13 @@ int aim_mie_sigma_thth(double radius, double k, int ndir, const double* theta, c
 }
 
 int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int max_rhs, double cfie_alpha,
-                  size_t* bytes) {
-  if (!mesh || !bytes || !(h > 0.0) || M < 1 || M > 5 || max_rhs < 1 || !(cfie_alpha > 0.0 && cfie_alpha <= 1.0)) {
+                  int precision, size_t* bytes) {
+  if (!mesh || !bytes || !(h > 0.0) || M < 1 || M > 5 || max_rhs < 1 || !(cfie_alpha > 0.0 && cfie_alpha <= 1.0) ||
+      (precision != AIM_C64 && precision != AIM_C128 && precision != AIM_C128_F64)) {
     set_error("aim_footprint: bad arguments");
     return AIM_EINVAL;
   }
-  // grid box from the vertices' bounding box, basis count from the edge count
-  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-  for (int i = 0; i < mesh->nv; ++i)
-    for (int d = 0; d < 3; ++d) {
-      lo[d] = std::min(lo[d], mesh->verts[3 * i + d]);
-      hi[d] = std::max(hi[d], mesh->verts[3 * i + d]);
-    }
-  long long n[3], L[3];
-  for (int d = 0; d < 3; ++d) {
-    n[d] = (long long)std::floor(hi[d] / h) - (long long)std::floor(lo[d] / h) + M + 1;
-    long long m = 2 * n[d] - 1, x;
-    for (L[d] = m;; ++L[d]) {
-      x = L[d];
-      for (int p : {2, 3, 5})
-        while (x % p == 0) x /= p;
-      if (x == 1) break;
-    }
-  }
-  const long long N = (long long)(1.5 * mesh->nt);  // interior edges of a closed surface
-  const long long S = (long long)(M + 1) * (M + 1) * (M + 1);
-  const long long nnz = N * 100LL;  // generous near-row length
-  const long long nc = n[0] * n[1] * n[2];
-  double b = 0;
-  b += (double)N * 4 * S * (8 + 4) * 2;                               // weights f64/f32 + node lists
-  b += (double)nnz * (16 + 8 + 4);                                     // near values + columns
-  b += (double)(L[0] / 2 + 1) * (L[1] / 2 + 1) * (L[2] / 2 + 1) * 24; // spectra
-  b += (double)L[0] * L[1] * L[2] * 32;                                // setup transform scratch
-  b += (double)max_rhs * 4 * (nc + L[2] * n[1] * n[0] + L[2] * L[1] * n[0]) * 24;  // grids, both precisions
-  b += (double)max_rhs * N * (16 * 53 + 48);                           // Krylov basis (m = 50) and vectors
-  b += (double)N * 4 * S * 8 * 2 + (double)nnz * 16;                   // float-float weights and near values
-  if (max_rhs >= kRhsLanesMin) b += (double)max_rhs * (4.0 * nc + N) * 16;  // RHS-minor copies of Phi and x
-  b += (double)mesh->nt * 60 * (144 + 12) + (double)nnz * 56;          // near-fill scratch at setup (peak)
-  if (cfie_alpha < 1.0)  // MFIE weights in three precisions, MFIE pair blocks and halves at setup
-    b += (double)N * 3 * S * (8 + 4 + 8) + (double)mesh->nt * 60 * 144 + (double)nnz * 32;
-  *bytes = (size_t)b;
-  return AIM_OK;
+  return footprint_estimate(mesh, h, M, near_radius, max_rhs, cfie_alpha, precision, bytes);
 }
 
 int aim_export(aim_ctx* c, int what, void* dst, size_t bytes) {

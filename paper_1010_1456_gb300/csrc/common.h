@@ -174,6 +174,7 @@ struct aim_ctx {
   aim_opts opts;
   cudaStream_t stream = nullptr;
   int device = 0;
+  size_t planned_bytes = 0;  // aim_footprint estimate at setup plus grids added beyond it (mem_budget)
   int64_t launches = 0;
   // FFT kernel per arithmetic policy (complex64, native FP64, float-float) and
   // pass (z fwd, y fwd, x, y inv, z inv): AIM_FFT_AUTO, AIM_FFT_STOCKHAM,
@@ -292,6 +293,12 @@ struct NearFillArgs {
 // Writes the near values [nnz] (c128) and the MoM diagonal [N] (c128).
 int near_fill_device(aim_ctx* c, const NearFillArgs& a, double* val_out, double* diag_out);
 int alloc_krylov(aim_ctx* c);
+// api.cu: footprint estimate (aim_footprint), and the mem_budget check of the
+// grids of a product precision the setup's estimate did not count.
+int footprint_estimate(const aim_mesh* mesh, double h, int M, double near_radius, int max_rhs, double alpha,
+                       int precision, size_t* bytes);
+size_t grid_bytes(const aim_ctx* c, int precision);
+int budget_grids(aim_ctx* c, int precision);
 // Allocates everything a product of this precision allocates lazily, so a
 // product can be captured into a CUDA graph.
 int prepare_product(aim_ctx* c, int precision);

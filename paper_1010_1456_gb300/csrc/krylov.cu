@@ -503,11 +503,16 @@ int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_so
   AIM_TRY(s.norms(V, N, k.bnorm));
   AIM_CUDA_TRY(cudaMemcpyAsync(bn.data(), k.bnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->stream));
   AIM_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  for (int b = 0; b < nrhs; ++b)
+  for (int b = 0; b < nrhs; ++b) {
+    if (!std::isfinite(bn[b])) {  // the norm pass sees every NaN and infinity of V
+      set_error("aim_solve: right-hand side " + std::to_string(b) + " holds NaN or an infinity");
+      return AIM_EINVAL;
+    }
     if (bn[b] == 0.0) {
       act[b] = 0;
       rel[b] = 0.0;
     }
+  }
   int iters = 0, restarts = 0;
   bool first = true, stepped = false;
   for (;;) {

@@ -813,6 +813,7 @@ int ensure_grids(aim_ctx* c, int precision) {
   if (precision == AIM_C64) {
     PrecData<float>& p = c->p32;
     if (!p.grid0) {
+      AIM_TRY(budget_grids(c, precision));
       AIM_CUDA_TRY(cudaMalloc(&p.grid0, sizeof(float2) * e0));
       AIM_CUDA_TRY(cudaMalloc(&p.grid1, sizeof(float2) * e1));
       AIM_CUDA_TRY(cudaMalloc(&p.grid2, sizeof(float2) * e2));
@@ -821,6 +822,7 @@ int ensure_grids(aim_ctx* c, int precision) {
   } else if (precision == AIM_C128_F64) {
     PrecData<double>& p = c->p64;
     if (!p.grid0) {
+      AIM_TRY(budget_grids(c, precision));
       AIM_CUDA_TRY(cudaMalloc(&p.grid0, sizeof(double2) * e0));
       AIM_CUDA_TRY(cudaMalloc(&p.grid1, sizeof(double2) * e1));
       AIM_CUDA_TRY(cudaMalloc(&p.grid2, sizeof(double2) * e2));
@@ -829,6 +831,7 @@ int ensure_grids(aim_ctx* c, int precision) {
   } else {
     FFData& p = c->pff;
     if (!p.grid0) {
+      AIM_TRY(budget_grids(c, precision));
       AIM_CUDA_TRY(cudaMalloc(&p.grid0, sizeof(float4) * e0));
       AIM_CUDA_TRY(cudaMalloc(&p.grid1, sizeof(float4) * e1));
       AIM_CUDA_TRY(cudaMalloc(&p.grid2, sizeof(float4) * e2));

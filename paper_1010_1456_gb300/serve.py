@@ -154,7 +154,8 @@ class Server:
                           error=repr(e))
 
     def _footprint(self, req):
-        return aim_footprint(req.verts, req.tris, req.h, req.M, req.near_radius, len(req.khat), req.cfie_alpha)
+        return aim_footprint(req.verts, req.tris, req.h, req.M, req.near_radius, len(req.khat), req.cfie_alpha,
+                             self.precision)
 
     # -------------------------------------------------------------- driver
     def run(self, requests, realtime=True):

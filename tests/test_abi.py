@@ -100,7 +100,7 @@ def test_setup_reports_missing_device(lib):
 
 
 def test_footprint_is_host_only(lib):
-    from paper_1010_1456_gb300 import aim_footprint
+    from paper_1010_1456_gb300 import _lib, aim_footprint
     from aim_inputs import icosphere_mesh
 
     v, t = icosphere_mesh(1.0, 8)
@@ -111,3 +111,34 @@ def test_footprint_is_host_only(lib):
     for bad in (0.0, -0.5, 1.5):  # CFIE weights outside (0, 1]
         with pytest.raises(RuntimeError):
             aim_footprint(v, t, 0.1, 2, 0.3, 1, cfie_alpha=bad)
+    # the complex64 solver also holds the float-float refinement grids; native FP64 holds no float-float arrays
+    c64 = aim_footprint(v, t, 0.1, 2, 0.3, 4, precision=_lib.AIM_C64)
+    c128 = aim_footprint(v, t, 0.1, 2, 0.3, 4, precision=_lib.AIM_C128)
+    f64 = aim_footprint(v, t, 0.1, 2, 0.3, 4, precision=_lib.AIM_C128_F64)
+    assert c64 > c128 > f64 > 0
+    with pytest.raises(RuntimeError):
+        aim_footprint(v, t, 0.1, 2, 0.3, 1, precision=7)
+
+
+def test_non_finite_vertices_and_budget_are_rejected_on_the_host(lib):
+    """NaN or infinite coordinates, and a footprint above opts.mem_budget, fail
+    before any device work (so also without a GPU)."""
+    import numpy as np
+
+    import paper_1010_1456_gb300 as g
+    from aim_inputs import plate_mesh
+    from paper_1010_1456_gb300 import _lib
+
+    v, t = plate_mesh(1.0, 9)
+    for bad in (np.nan, np.inf):
+        vb = v.copy()
+        vb[3, 1] = bad
+        with pytest.raises(g.AIMError) as e:
+            g.aim_setup(vb, t, 6.28, 0.1, stream=0)
+        assert e.value.code == _lib.AIM_EINVAL
+        with pytest.raises(g.AIMError):
+            g.aim_footprint(vb, t, 0.1)
+    with pytest.raises(g.AIMError) as e:
+        g.aim_setup(v, t, 6.28, 0.1, mem_budget=1000, stream=0)
+    assert e.value.code == _lib.AIM_ENOMEM
+    assert b"mem_budget" in lib.aim_last_error()

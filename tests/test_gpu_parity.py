@@ -435,3 +435,40 @@ def test_full_size_sphere_16_lambda_sampled_rows():
         y = g.aim_matvec(ctx, x1, precision=prec).cpu().numpy()[:, rows]
         assert rel(y, ref[:1]) <= 1e-12, (prec, rel(y, ref[:1]))
     ctx.close()
+
+
+def test_mem_budget_and_non_finite_inputs():
+    """opts.mem_budget: a context whose budget is exactly its footprint estimate
+    (solver precision AIM_C128) runs FP64-accurate products, but a native-FP64
+    product, whose grids the estimate does not count, is refused with
+    AIM_ENOMEM and the context stays usable.  NaN or infinite plane-wave
+    directions, right-hand sides and RCS angles are rejected with AIM_EINVAL."""
+    from paper_1010_1456_gb300 import _lib
+
+    v, t = plate_mesh(1.0, 9)
+    est = g.aim_footprint(v, t, H, 2, 3 * H, 1, precision=g.AIM_C128)
+    ctx, op = make(v, t)
+    x = torch.from_numpy(random_complex((1, ctx.N), 91)).cuda()
+    ref = op.matvec(x.cpu().numpy())
+    ctx.close()
+    ctx = g.aim_setup(v, t, K0, H, max_rhs=1, precision=g.AIM_C128, mem_budget=est)
+    assert rel(g.aim_matvec(ctx, x, precision=g.AIM_C128).cpu().numpy(), ref) <= 1e-12
+    with pytest.raises(g.AIMError) as e:
+        g.aim_matvec(ctx, x, precision=g.AIM_C128_F64)
+    assert e.value.code == _lib.AIM_ENOMEM
+    assert rel(g.aim_matvec(ctx, x, precision=g.AIM_C128).cpu().numpy(), ref) <= 1e-12
+    kh, po = planewave_minus_z_xpol()
+    for bad in (np.nan, np.inf):
+        kb = kh.copy()
+        kb[0, 2] = bad
+        with pytest.raises(g.AIMError) as e:
+            g.aim_rhs_planewave(ctx, kb, po)
+        assert e.value.code == _lib.AIM_EINVAL
+    V = g.aim_rhs_planewave(ctx, kh, po)
+    V[0, 5] = complex(np.nan, 0.0)
+    with pytest.raises(g.AIMError) as e:
+        g.aim_solve(ctx, V, 1e-6)
+    assert e.value.code == _lib.AIM_EINVAL
+    with pytest.raises(g.AIMError):
+        g.aim_rcs(ctx, V, np.array([0.1, np.nan]), np.array([0.0, 0.0]))
+    ctx.close()
