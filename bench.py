@@ -460,19 +460,24 @@ def serve_summary(requests=24, slots=4):
     plates, spheres = SERVE_SIZES["small"]
     cap_reqs = serve.make_stream(requests, rate=1.0, seed=2, plate_sides=plates, sphere_radii=spheres,
                                  max_rhs=16, sphere_cfie_alpha=0.6)
-    res, span = serve.Server(slots=slots).run(cap_reqs, realtime=False)
+    cap_srv = serve.Server(slots=slots)
+    res, span = cap_srv.run(cap_reqs, realtime=False)
+    cap_srv.close()
     cap = serve.summarize(res, span)
     rate = 0.7 * cap["solves_per_s"]
     reqs = serve.make_stream(requests, rate=rate, seed=1, plate_sides=plates, sphere_radii=spheres, max_rhs=16,
                              sphere_cfie_alpha=0.6)
     srv = serve.Server(slots=slots)
     res, span = srv.run(reqs, realtime=True)
+    srv.close()
     summ = serve.summarize(res, span)
     return {"stream": f"plates {plates} lambda (EFIE), spheres {spheres} lambda (CFIE alpha 0.6), 1..16 RHS, "
                       f"{requests} requests, Poisson seed 1 at 0.7 x capacity, {slots} slots",
             "solves_per_s": summ["solves_per_s"], "p50_s": summ["p50_s"], "p99_s": summ["p99_s"],
             "capacity_solves_per_s": cap["solves_per_s"], "failed": summ["failed"],
-            "max_rel_res": summ["max_rel_res"], "peak_concurrent": srv.peak_busy}
+            "max_rel_res": summ["max_rel_res"], "peak_concurrent": srv.peak_busy,
+            "contexts_built": summ["setups"], "mean_requests_per_solve": summ["mean_batch"],
+            "batching": "resident contexts per scatterer; queued same-scatterer requests merged into one solve"}
 
 
 # ---------------------------------------------------------------- serving
@@ -493,17 +498,19 @@ def run_serve(args):
     plates, spheres = SERVE_SIZES[args.serve_sizes]
     cap_reqs = serve.make_stream(args.requests, rate=1.0, seed=2, plate_sides=plates, sphere_radii=spheres,
                                  max_rhs=args.serve_max_rhs, sphere_cfie_alpha=args.serve_cfie)
-    srv = serve.Server(slots=args.slots)
+    srv = serve.Server(slots=args.slots, cache=bool(args.serve_cache))
     res, span = srv.run(cap_reqs, realtime=False)
+    srv.close()
     cap = serve.summarize(res, span)
     rate = 0.7 * cap["solves_per_s"]
     reqs = serve.make_stream(args.requests, rate=rate, seed=1, plate_sides=plates, sphere_radii=spheres,
                              max_rhs=args.serve_max_rhs, sphere_cfie_alpha=args.serve_cfie)
-    srv = serve.Server(slots=args.slots)
+    srv = serve.Server(slots=args.slots, cache=bool(args.serve_cache))
     t0 = time.perf_counter()
     with ClockSampler(0) as clk:
         res, span = srv.run(reqs, realtime=True)
     wall = time.perf_counter() - t0
+    srv.close()
     summ = serve.summarize(res, span)
     line = {
         "metric": "served solves/s (p50/p99 latency), complex64 AIM with FP64 refinement, tol 1e-6",
@@ -524,6 +531,9 @@ def run_serve(args):
         "failed": summ["failed"],
         "max_rel_res": summ["max_rel_res"],
         "peak_concurrent": srv.peak_busy,
+        "contexts_built": summ["setups"],
+        "mean_requests_per_solve": summ["mean_batch"],
+        "resident_contexts": bool(args.serve_cache),
         "wall_s": wall,
         "clocks": clk.summary(),
     }
@@ -930,6 +940,8 @@ def main():
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-max-rhs", type=int, default=16)
+    ap.add_argument("--serve-cache", type=int, default=1,
+                    help="1: resident contexts and merged same-scatterer solves; 0: one context per request")
     ap.add_argument("--serve-cfie", type=float, default=0.6,
                     help="alpha of the CFIE the spheres of the serving stream are solved with (1: EFIE)")
     args = ap.parse_args()

@@ -11,12 +11,25 @@ requests run concurrently: their setup (host), spectra, products and Krylov
 steps interleave on the device.  The library calls release the GIL, so the
 threads overlap.
 
+Two batching levels sit on top (``cache=True``, the default):
+
+* resident contexts: a context built for a scatterer (mesh, k, h, M, near
+  radius, CFIE alpha, tolerance) stays on the device after its solve, so a
+  later request for the same scatterer skips the setup; idle contexts are
+  evicted least recently used when the memory budget needs room;
+* merged solves: when a slot takes a request, every pending request for the
+  same scatterer joins it (up to ``merge_rhs`` right-hand sides in total) and
+  the group is solved as one multi-RHS solve, so each product, FFT pass and
+  Krylov step is one launch for all of them.  Each right-hand side keeps its
+  own Arnoldi process in the batched GMRES, so a request's result is the one
+  it would get alone.
+
 The request/response path is the library's C ABI only; no step of a solve
 runs in Python.
 """
 
 import dataclasses
-import queue
+import hashlib
 import threading
 import time
 
@@ -27,6 +40,7 @@ from . import (
     aim_footprint,
     aim_rcs,
     aim_rhs_planewave,
+    aim_set_stream,
     aim_setup,
     aim_solve,
 )
@@ -62,14 +76,27 @@ class Result:
     footprint: int
     sigma: np.ndarray = None
     error: str = None
+    batch: int = 1  # requests solved together in this request's solve
+    setup: bool = True  # a context was built for this result (the first request of a batch that found none)
 
     @property
     def latency(self):
         return self.finished - self.arrival
 
 
+def scatterer_key(req):
+    """Requests with equal keys share one operator: same mesh, wavenumber, grid
+    step, stencil order, near radius, CFIE weight and tolerance."""
+    h = hashlib.sha1()
+    h.update(np.ascontiguousarray(req.verts, dtype=np.float64).tobytes())
+    h.update(np.ascontiguousarray(req.tris, dtype=np.int32).tobytes())
+    return (h.hexdigest(), float(req.k), float(req.h), int(req.M), float(req.near_radius), float(req.cfie_alpha),
+            float(req.tol))
+
+
 class Server:
-    def __init__(self, slots=4, mem_budget=None, device=0, precision=AIM_C64, max_skip=8):
+    def __init__(self, slots=4, mem_budget=None, device=0, precision=AIM_C64, max_skip=8, cache=True,
+                 merge_rhs=16):
         import torch
 
         self.torch = torch
@@ -84,21 +111,64 @@ class Server:
         self.slots = slots
         self.precision = precision
         self.max_skip = max_skip
-        self.claimed = 0
+        self.cache = cache
+        self.merge_rhs = int(merge_rhs)
+        self.claimed = 0  # footprints of running uncached requests and of every resident context
         self.lock = threading.Condition()
-        self.pending = []  # admitted-not-yet requests, arrival order
+        self.pending = []  # admitted-not-yet requests, arrival order: (req, footprint, key)
         self.results = {}
         self.busy = 0
         self.stop = False
         self.t0 = None
+        # resident contexts: key -> {"ctx", "fp", "busy", "used"}
+        self.contexts = {}
+        self.setups = 0
+        self.batches = []  # sizes of the solves run
 
     # -------------------------------------------------------------- admission
+    def _evict_idle(self, need):
+        """Free idle resident contexts, least recently used first, until `need` bytes fit (under the lock)."""
+        for key, ent in sorted(self.contexts.items(), key=lambda kv: kv[1]["used"]):
+            if self.claimed + need <= self.budget:
+                break
+            if ent["busy"]:
+                continue
+            ent["ctx"].close()
+            self.claimed -= ent["fp"]
+            del self.contexts[key]
+
     def _admissible(self):
-        """Pop the first pending request that fits (under the lock)."""
-        for i, (req, fp) in enumerate(self.pending[: self.max_skip]):
-            if self.claimed + fp <= self.budget or (self.busy == 0 and self.claimed == 0):
+        """Pop the first pending request that can run now, with the pending requests
+        that merge into its solve (under the lock).  Returns (batch, claim) or None;
+        claim is the footprint charged for the batch's duration (0 when it reuses a
+        resident context, whose footprint stays claimed while it is resident)."""
+        for i, (req, fp, key) in enumerate(self.pending[: self.max_skip]):
+            ent = self.contexts.get(key) if self.cache else None
+            if ent is not None and ent["busy"]:
+                continue  # its context is solving: this request waits for it (or merges into the next solve)
+            need = 0 if ent is not None else fp
+            if self.cache and need and self.claimed + need > self.budget:
+                self._evict_idle(need)
+            if need == 0 or self.claimed + need <= self.budget or (self.busy == 0 and self.claimed == 0):
                 self.pending.pop(i)
-                return req, fp
+                batch = [req]
+                if self.cache:
+                    tot = len(req.khat)
+                    j = 0
+                    while j < len(self.pending):
+                        r2, _fp2, k2 = self.pending[j]
+                        if k2 == key and tot + len(r2.khat) <= self.merge_rhs:
+                            batch.append(r2)
+                            tot += len(r2.khat)
+                            self.pending.pop(j)
+                        else:
+                            j += 1
+                    if ent is None:  # the context this solve builds stays resident
+                        self.contexts[key] = {"ctx": None, "fp": fp, "busy": True, "used": time.perf_counter()}
+                    else:
+                        ent["busy"] = True
+                        ent["used"] = time.perf_counter()
+                return batch, need
         return None
 
     def _make_stream(self):
@@ -115,22 +185,40 @@ class Server:
                         return
                     got = self._admissible() if self.pending else None
                     if got is not None:
-                        req, fp = got
-                        self.claimed += fp
+                        batch, claim = got
+                        self.claimed += claim
                         self.busy += 1
                         self.peak_claimed = max(self.peak_claimed, self.claimed)
                         self.peak_busy = max(self.peak_busy, self.busy)
+                        self.batches.append(len(batch))
                         break
                     self.lock.wait(0.05)
             admitted = time.perf_counter() - self.t0
-            res = self._run(req, fp, stream, admitted)
+            res = self._solve_batch(batch, claim, stream, admitted)
             with self.lock:
-                self.claimed -= fp
+                if not self.cache:
+                    self.claimed -= claim
+                else:
+                    key = scatterer_key(batch[0])
+                    ent = self.contexts.get(key)
+                    if ent is not None:
+                        ent["busy"] = False
+                        ent["used"] = time.perf_counter()
+                        if ent["ctx"] is None:  # its setup failed: nothing resident
+                            self.claimed -= ent["fp"]
+                            del self.contexts[key]
                 self.busy -= 1
-                self.results[req.rid] = res
+                for r in res:
+                    self.results[r.rid] = r
                 self.lock.notify_all()
 
+    def _solve_batch(self, batch, claim, stream, admitted):
+        if not self.cache:
+            return [self._run(req, self._footprint(req), stream, admitted) for req in batch]
+        return self._run_merged(batch, stream, admitted)
+
     def _run(self, req, fp, stream, admitted):
+        """One request on a context of its own, built and freed here (cache off)."""
         torch = self.torch
         try:
             with torch.cuda.stream(stream):
@@ -153,14 +241,69 @@ class Server:
             return Result(req.rid, None, None, 0, req.arrival, admitted, time.perf_counter() - self.t0, fp,
                           error=repr(e))
 
+    def _run_merged(self, batch, stream, admitted):
+        """The batch's right-hand sides in one solve on the scatterer's resident
+        context (built here on first use, with room for merge_rhs right-hand sides)."""
+        torch = self.torch
+        req0 = batch[0]
+        key = scatterer_key(req0)
+        with self.lock:
+            ent = self.contexts[key]
+        fp = ent["fp"]
+        built = False
+        try:
+            with torch.cuda.stream(stream):
+                if ent["ctx"] is None:
+                    ctx = aim_setup(req0.verts, req0.tris, req0.k, req0.h, M=req0.M, near_radius=req0.near_radius,
+                                    precision=self.precision, max_rhs=max(self.merge_rhs, len(req0.khat)),
+                                    stream=stream.cuda_stream, cfie_alpha=req0.cfie_alpha)
+                    with self.lock:
+                        ent["ctx"] = ctx
+                        self.setups += 1
+                    built = True
+                else:
+                    ctx = ent["ctx"]
+                    aim_set_stream(ctx, stream)
+                kh = np.concatenate([r.khat for r in batch])
+                po = np.concatenate([r.pol for r in batch])
+                V = aim_rhs_planewave(ctx, kh, po)
+                X, info = aim_solve(ctx, V, req0.tol, raise_on_noconv=False)
+                Xh = X.cpu().numpy()
+                out, b0 = [], 0
+                for r in batch:
+                    nb = len(r.khat)
+                    sigma = None
+                    if r.rcs_dirs is not None:
+                        sigma = aim_rcs(ctx, X[b0 : b0 + nb].contiguous(), *r.rcs_dirs)[0]
+                    out.append(Result(r.rid, Xh[b0 : b0 + nb], info["rel_res"][b0 : b0 + nb], info["iterations"],
+                                      r.arrival, admitted, time.perf_counter() - self.t0, fp, sigma,
+                                      batch=len(batch), setup=built and r is req0))
+                    b0 += nb
+                return out
+        except Exception as e:  # reported per request; the server keeps running
+            now = time.perf_counter() - self.t0
+            return [Result(r.rid, None, None, 0, r.arrival, admitted, now, fp, error=repr(e), batch=len(batch))
+                    for r in batch]
+
     def _footprint(self, req):
-        return aim_footprint(req.verts, req.tris, req.h, req.M, req.near_radius, len(req.khat), req.cfie_alpha,
+        nrhs = max(self.merge_rhs, len(req.khat)) if self.cache else len(req.khat)
+        return aim_footprint(req.verts, req.tris, req.h, req.M, req.near_radius, nrhs, req.cfie_alpha,
                              self.precision)
+
+    def close(self):
+        """Free every resident context."""
+        with self.lock:
+            for ent in self.contexts.values():
+                if ent["ctx"] is not None:
+                    ent["ctx"].close()
+            self.contexts.clear()
+            self.claimed = 0
 
     # -------------------------------------------------------------- driver
     def run(self, requests, realtime=True):
         """Feed requests at their arrival times (or all at once) and wait for all results."""
         self.t0 = time.perf_counter()
+        self.stop = False
         threads = [threading.Thread(target=self._worker, args=(i,), daemon=True) for i in range(self.slots)]
         for t in threads:
             t.start()
@@ -170,8 +313,9 @@ class Server:
                 if dt > 0:
                     time.sleep(dt)
             fp = self._footprint(req)
+            key = scatterer_key(req) if self.cache else None
             with self.lock:
-                self.pending.append((req, fp))
+                self.pending.append((req, fp, key))
                 self.lock.notify_all()
         with self.lock:
             self.stop = True
@@ -194,6 +338,8 @@ def summarize(results, makespan):
         "rhs_per_s": sum(len(r.X) for r in ok) / makespan if makespan > 0 else 0.0,
         "makespan_s": makespan,
         "max_rel_res": float(max(r.rel_res.max() for r in ok)) if ok else None,
+        "mean_batch": float(np.mean([r.batch for r in ok])) if ok else None,
+        "setups": int(sum(1 for r in ok if r.setup)),
     }
 
 

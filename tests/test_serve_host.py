@@ -13,6 +13,7 @@ from paper_1010_1456_gb300 import serve
 
 class FakeServer(serve.Server):
     def __init__(self, footprints, durations, fail=(), **kw):
+        kw.setdefault("cache", False)
         super().__init__(**kw)
         self.fps = footprints
         self.durs = durations
@@ -100,3 +101,94 @@ def test_cfie_is_requested_for_spheres_only():
     assert {r.cfie_alpha for r in a if r.label.startswith("plate")} == {1.0}
     assert {r.cfie_alpha for r in a if r.label.startswith("sphere")} == {0.6}
     assert {r.cfie_alpha for r in b} == {1.0}
+
+
+class FakeMergingServer(serve.Server):
+    """Resident contexts and merged solves with the solve replaced by a sleep:
+    records which requests each solve took and whether it had to build."""
+
+    def __init__(self, footprints, duration=0.02, **kw):
+        super().__init__(**kw)
+        self.fps = footprints
+        self.duration = duration
+        self.solves = []
+
+    def _make_stream(self):
+        return None
+
+    def _footprint(self, req):
+        return self.fps[req.rid]
+
+    def _run_merged(self, batch, stream, admitted):
+        key = serve.scatterer_key(batch[0])
+        with self.lock:
+            ent = self.contexts[key]
+            built = ent["ctx"] is None
+            if built:
+                ent["ctx"] = _FakeCtx()
+                self.setups += 1
+        self.solves.append(([r.rid for r in batch], built))
+        time.sleep(self.duration)
+        now = time.perf_counter() - self.t0
+        return [serve.Result(r.rid, np.zeros((len(r.khat), 1)), np.zeros(len(r.khat)), 1, r.arrival, admitted, now,
+                             ent["fp"], batch=len(batch), setup=built and r is batch[0]) for r in batch]
+
+
+class _FakeCtx:
+    closed = 0
+
+    def close(self):
+        _FakeCtx.closed += 1
+
+
+def mesh_reqs(kinds, nrhs=1):
+    """Requests on scatterers named by `kinds` (equal names share a mesh)."""
+    meshes = {}
+    out = []
+    for i, k in enumerate(kinds):
+        if k not in meshes:
+            v = np.zeros((3, 3))
+            v[0, 0] = float(len(meshes) + 1)  # distinct vertex coordinates per scatterer
+            meshes[k] = (v, np.array([[0, 1, 2]], dtype=np.int32))
+        v, t = meshes[k]
+        out.append(serve.Request(i, v, t, np.zeros((nrhs, 3)), np.zeros((nrhs, 3)), label=k))
+    return out
+
+
+def test_same_scatterer_requests_merge_and_reuse_the_resident_context():
+    """Queued requests for one scatterer are solved together; a later request
+    for it reuses the resident context instead of building another."""
+    reqs = mesh_reqs(["a", "a", "b", "a", "b"], nrhs=2)
+    s = FakeMergingServer([10] * 5, slots=1, mem_budget=100, merge_rhs=4)
+    res, _ = s.run(reqs, realtime=False)
+    assert all(r.error is None for r in res)
+    # one slot: the first solve takes a0 with a1 (4 RHS, the merge limit), then b2 with b4, then a3 alone
+    assert s.solves == [([0, 1], True), ([2, 4], True), ([3], False)]
+    assert s.setups == 2
+    summ = serve.summarize(res, 1.0)
+    assert summ["setups"] == 2 and summ["mean_batch"] == pytest.approx((2 + 2 + 2 + 2 + 1) / 5)
+
+
+def test_idle_resident_contexts_are_evicted_for_room():
+    """Three scatterers of 40 bytes each under a budget of 100: the third one's
+    context needs the least recently used idle one freed."""
+    _FakeCtx.closed = 0
+    reqs = mesh_reqs(["a", "b", "c"])
+    s = FakeMergingServer([40, 40, 40], slots=1, mem_budget=100)
+    res, _ = s.run(reqs, realtime=False)
+    assert all(r.error is None for r in res)
+    assert _FakeCtx.closed == 1 and len(s.contexts) == 2 and s.claimed == 80
+    assert s.peak_claimed <= 100
+    s.close()
+    assert s.claimed == 0 and not s.contexts
+
+
+def test_busy_context_makes_its_requests_wait_not_duplicate():
+    """Two slots, two requests for one scatterer arriving one after the other:
+    the second waits for the context (or merges) instead of building a second one."""
+    reqs = mesh_reqs(["a", "a"])
+    reqs[1].arrival = 0.005
+    s = FakeMergingServer([10, 10], duration=0.05, slots=2, mem_budget=100)
+    res, _ = s.run(reqs, realtime=True)
+    assert all(r.error is None for r in res)
+    assert s.setups == 1
