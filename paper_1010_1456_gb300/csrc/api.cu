@@ -409,6 +409,7 @@ int aim_footprint(const aim_mesh* mesh, double h, int M, double near_radius, int
 
 int aim_export(aim_ctx* c, int what, void* dst, size_t bytes) {
   AIM_TRY(check_ctx(c));
+  if (what != AIM_EXPORT_ANCHORS && what != AIM_EXPORT_GHAT) AIM_TRY(fetch_host_arrays(c));
   const void* src = nullptr;
   size_t need = 0;
   std::vector<double> full;

@@ -175,6 +175,7 @@ struct aim_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
   size_t planned_bytes = 0;  // aim_footprint estimate at setup plus grids added beyond it (mem_budget)
+  bool host_synced = false;  // the h_* copies below hold the device setup arrays (fetch_host_arrays)
   int64_t launches = 0;
   // FFT kernel per arithmetic policy (complex64, native FP64, float-float) and
   // pass (z fwd, y fwd, x, y inv, z inv): AIM_FFT_AUTO, AIM_FFT_STOCKHAM,
@@ -184,7 +185,7 @@ struct aim_ctx {
   aim::FftPlan plan[3];
   aim::FftPlan* plan_dev = nullptr;  // device copy of plan[3]
 
-  // host copies (inspection, RHS/RCS geometry)
+  // host copies: anchors always, the rest filled by fetch_host_arrays on aim_export
   std::vector<int32_t> h_anchor;  // [N][3] absolute
   std::vector<double> h_lam;      // [N][4][S]
   std::vector<double> h_lamM;     // [N][3][S] CFIE: differentiated-interpolation (MFIE) weights
@@ -269,29 +270,10 @@ int build_ghat(aim_ctx* c);
 // krylov.cu
 int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_solve_info* info);
 
-// Host arrays for the device near-zone fill (nearfill.cu): geometry, the
-// triangle pairs (CSR by test triangle, sorted by source triangle; ids lists
-// the nsing singular pairs first), the near list, anchors, FP64 weights on
-// the full (M+1)^3 stencil and G_h on offsets [-TE, TE]^3.
-struct TriRule;
-struct NearFillArgs {
-  int N = 0, nv = 0, nt = 0, P = 3, S = 27, TE = 0;
-  int64_t nnz = 0, npairs = 0, nsing = 0, ntab = 0;
-  const double* vert = nullptr;
-  const int32_t* tri = nullptr;
-  const double* area = nullptr;
-  const int32_t *tp = nullptr, *tm = nullptr, *sp = nullptr, *sm = nullptr;
-  const double* len = nullptr;
-  const int32_t *tptr = nullptr, *pP = nullptr, *pQ = nullptr, *ids = nullptr;
-  const int32_t *erow = nullptr, *ecol = nullptr, *nptr = nullptr, *anchor = nullptr;
-  const double* lam = nullptr;
-  const double2* gtab = nullptr;
-  const TriRule *rule_test = nullptr, *rule_test_sing = nullptr, *rule_src = nullptr;
-  double alpha = 1.0;            // CFIE weight of the EFIE (1: EFIE only)
-  const double* lamM = nullptr;  // [N][3][S] MFIE weights (CFIE only)
-};
-// Writes the near values [nnz] (c128) and the MoM diagonal [N] (c128).
-int near_fill_device(aim_ctx* c, const NearFillArgs& a, double* val_out, double* diag_out);
+// setup.cu: copies of the device setup arrays (weights, near list and
+// values, diagonal, projection pointers) into the context's host vectors,
+// once, for aim_export.
+int fetch_host_arrays(aim_ctx* c);
 int alloc_krylov(aim_ctx* c);
 // api.cu: footprint estimate (aim_footprint), and the mem_budget check of the
 // grids of a product precision the setup's estimate did not count.

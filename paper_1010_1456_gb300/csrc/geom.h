@@ -151,21 +151,27 @@ AIM_HD inline Cd operator*(double s, Cd a) { return Cd{s * a.re, s * a.im}; }
 // written as -(jk/4pi) sinc(kR/2) exp(-jkR/2).
 AIM_HD inline Cd green_full(double k, double R) {
   double s = 1.0 / (4.0 * kPi * R);
-  return Cd{cos(k * R) * s, -sin(k * R) * s};
+  double sn, cs;
+  sincos(k * R, &sn, &cs);
+  return Cd{cs * s, -sn * s};
 }
 AIM_HD inline Cd green_smooth(double k, double R) {
   double x = 0.5 * k * R;
-  double sc = (x == 0.0) ? 1.0 : sin(x) / x;
+  double sn, cs;
+  sincos(x, &sn, &cs);
+  double sc = (x == 0.0) ? 1.0 : sn / x;
   double c = -k / (4.0 * kPi) * sc;  // multiplies j * exp(-jx)
   // j * exp(-jx) = j (cos x - j sin x) = sin x + j cos x
-  return Cd{c * sin(x), c * cos(x)};
+  return Cd{c * sn, c * cs};
 }
 
 // EFIE triangle-pair block T[a][b] (a: slot on test triangle P, b: slot on
 // source triangle Q):
 //   T_ab = sum_i W_i [ (r_i - P_a).V_b(r_i) / (4 A_P A_Q) - S0(r_i) / (k^2 A_P A_Q) ]
-//   S0(r) = int_Q G dS',  V_b(r) = int_Q (r' - Q_b) G dS'
-// so that Z_mn += j k eta s_m s_n l_m l_n T[a(m)][b(n)].
+//   S0(r) = int_Q G dS',  V_b(r) = int_Q (r' - Q_b) G dS' = V(r) - Q_b S0(r),  V(r) = int_Q r' G dS'
+// so that Z_mn += j k eta s_m s_n l_m l_n T[a(m)][b(n)].  The source sum
+// accumulates S0 and V only (four complex values per source point); the nine
+// V_b follow per test point.
 AIM_HD inline void pair_block(const V3 P[3], const V3 Q[3], double AP, double AQ, bool singular, double k,
                               const TriRule& test, const TriRule& src, Cd T[3][3]) {
   Cd acc[3][3];
@@ -176,21 +182,22 @@ AIM_HD inline void pair_block(const V3 P[3], const V3 Q[3], double AP, double AQ
     V3 ri = tri_point(P[0], P[1], P[2], test.xi1[i], test.xi2[i]);
     double Wi = AP * test.w[i];
     Cd S0 = cd(0, 0);
-    Cd Vb[3][3];  // [b][xyz]
-    for (int b = 0; b < 3; ++b)
-      for (int c = 0; c < 3; ++c) Vb[b][c] = cd(0, 0);
+    Cd V[3] = {cd(0, 0), cd(0, 0), cd(0, 0)};
     for (int q = 0; q < src.q; ++q) {
       V3 rq = tri_point(Q[0], Q[1], Q[2], src.xi1[q], src.xi2[q]);
       double R = norm(ri - rq);
       Cd g = singular ? green_smooth(k, R) : green_full(k, R);
       g = (AQ * src.w[q]) * g;
       S0 = S0 + g;
-      for (int b = 0; b < 3; ++b) {
-        V3 d = rq - Q[b];
-        Vb[b][0] = Vb[b][0] + d.x * g;
-        Vb[b][1] = Vb[b][1] + d.y * g;
-        Vb[b][2] = Vb[b][2] + d.z * g;
-      }
+      V[0] = V[0] + rq.x * g;
+      V[1] = V[1] + rq.y * g;
+      V[2] = V[2] + rq.z * g;
+    }
+    Cd Vb[3][3];  // [b][xyz]
+    for (int b = 0; b < 3; ++b) {
+      Vb[b][0] = V[0] + (-Q[b].x) * S0;
+      Vb[b][1] = V[1] + (-Q[b].y) * S0;
+      Vb[b][2] = V[2] + (-Q[b].z) * S0;
     }
     if (singular) {
       double I0;

@@ -14,12 +14,13 @@
 // produce the MFIE blocks 1/2 <f_m, f_n> - <f_m, n x int grad G x f_n>
 // (unsymmetrised) and subtract their grid form -sum_c W^c_m . G Lambda^c_n;
 // the entry is alpha EFIE + (1 - alpha) eta MFIE.
-// Every value is FP64.  The host builds the pair lists; the results come
-// back to the host arrays the rest of setup reads.
+// Every value is FP64.  The pair lists, weights and near list come from the
+// device setup (setup_dev.cu); the results stay on the device.
 #include <algorithm>
 
 #include "common.h"
 #include "geom.h"
+#include "setup_dev.h"
 
 namespace aim {
 
@@ -73,34 +74,49 @@ __device__ void mfie_block(const V3 Pv[3], const V3 Qv[3], double AP, double AQ,
   const V3 nP = (1.0 / norm(nP0)) * nP0, nQ = (1.0 / norm(nQ0)) * nQ0;
   const V3 nx = cross(nP, nQ);
   if (fmax(fabs(nx.x), fmax(fabs(nx.y), fabs(nx.z))) == 0.0 && fabs(dot(Qv[0] - Pv[0], nP)) == 0.0) return;
+  (void)nQ;
+  // With positions taken from O = Q_0 (r' = r - O, r'_q = r_q - O), x = ra.r',
+  // v = n.r', z = ra.Q'_b, p = n.Q'_b, the integrand (ra.D)(n.rb) - (ra.rb)(n.D)
+  // summed over the source points with weights gw is
+  //   A1 (x - z) + A0 (z v - x p) + (ra.C)(p - v),
+  // A0 = sum gw, A1 = sum gw n.r'_q, C = sum gw r'_q: five complex sums per
+  // source point instead of nine (a, b) integrands.
+  const V3 O = Qv[0];
+  const V3 Qp[3] = {Qv[0] - O, Qv[1] - O, Qv[2] - O};
+  double pq[3];
+  for (int b = 0; b < 3; ++b) pq[b] = dot(nP, Qp[b]);
   Cd acc[3][3];
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) acc[a][b] = cd(0, 0);
   for (int i = 0; i < test.q; ++i) {
     const V3 r = tri_point(Pv[0], Pv[1], Pv[2], test.xi1[i], test.xi2[i]);
+    const V3 rp = r - O;
     const double W = AP * test.w[i];
-    const V3 ra[3] = {r - Pv[0], r - Pv[1], r - Pv[2]};
+    Cd A0 = cd(0, 0), A1 = cd(0, 0), C[3] = {cd(0, 0), cd(0, 0), cd(0, 0)};
     for (int q = 0; q < src.q; ++q) {
       const V3 rq = tri_point(Qv[0], Qv[1], Qv[2], src.xi1[q], src.xi2[q]);
+      const V3 rqp = rq - O;
       const V3 D = r - rq;
       const double R = norm(D);
       const double kr = k * R, s = W * AQ * src.w[q] / (4.0 * kPi * R * R * R);
-      const double cr = cos(kr), sr = sin(kr);
+      double sr, cr;
+      sincos(kr, &sr, &cr);
       // -(1 + j kR)(cos kR - j sin kR) = -(cos + kR sin) + j (sin - kR cos)
       const Cd gw = cd(-(cr + kr * sr) * s, (sr - kr * cr) * s);
-      const double nD = dot(nP, D);
-      double nb[3];
-      V3 rb[3];
+      A0 = A0 + gw;
+      A1 = A1 + dot(nP, rqp) * gw;
+      C[0] = C[0] + rqp.x * gw;
+      C[1] = C[1] + rqp.y * gw;
+      C[2] = C[2] + rqp.z * gw;
+    }
+    const double v = dot(nP, rp);
+    for (int a = 0; a < 3; ++a) {
+      const V3 ra = r - Pv[a];
+      const double x = dot(ra, rp);
+      const Cd raC = ra.x * C[0] + ra.y * C[1] + ra.z * C[2];
       for (int b = 0; b < 3; ++b) {
-        rb[b] = rq - Qv[b];
-        nb[b] = dot(nP, rb[b]);
-      }
-      for (int a = 0; a < 3; ++a) {
-        const double aD = dot(ra[a], D);
-        for (int b = 0; b < 3; ++b) {
-          const double integ = aD * nb[b] - dot(ra[a], rb[b]) * nD;
-          acc[a][b] = acc[a][b] + integ * gw;
-        }
+        const double z = dot(ra, Qp[b]);
+        acc[a][b] = acc[a][b] + (x - z) * A1 + (z * v - x * pq[b]) * A0 + (pq[b] - v) * raC;
       }
     }
   }
@@ -205,6 +221,10 @@ __global__ void __launch_bounds__(256) k_near_values(const int32_t* __restrict__
       else hi = mid;
     }
     const int64_t et = lo;
+    // EFIE: the grid part is symmetric (G_h depends on |offset|), so the
+    // entry of the pair with m <= n computes it once for both; with CFIE the
+    // MFIE part is not, and every entry computes its own
+    if (!lamM && m > n) continue;
     const double2 a0 = zhalf[e], a1 = zhalf[nnz + e], b0 = zhalf[et], b1 = zhalf[nnz + et];
     const double zr = 0.5 * ((a0.x + a1.x) + (b0.x + b1.x));
     const double zi = 0.5 * ((a0.y + a1.y) + (b0.y + b1.y));
@@ -263,59 +283,27 @@ __global__ void __launch_bounds__(256) k_near_values(const int32_t* __restrict__
         d = make_double2(alpha * d.x + be * zmr, alpha * d.y + be * zmi);
       }
       val[e] = v;
+      if (!wm && m != n) val[et] = v;  // the transposed entry: same symmetrised MoM value and grid part
       if (m == n) diag[m] = d;
     }
   }
 }
 
-// Device part of the near fill; arguments are host arrays (see setup.cu).
-int near_fill_device(aim_ctx* c, const NearFillArgs& A, double* val_out, double* diag_out) {
-  const int64_t nnz = A.nnz, npairs = A.npairs;
-  const size_t N = (size_t)A.N;
-  std::vector<void*> bufs;
-  auto dev = [&](void** p, const void* src, size_t bytes) -> int {
-    AIM_CUDA_TRY(cudaMalloc(p, std::max<size_t>(bytes, 16)));
-    bufs.push_back(*p);
-    if (src && bytes) AIM_CUDA_TRY(cudaMemcpyAsync(*p, src, bytes, cudaMemcpyHostToDevice, c->stream));
-    return AIM_OK;
-  };
+// Device part of the near fill on device inputs (see setup_dev.h).
+int near_fill_dev(aim_ctx* c, const NearFillDev& A, double2* val, double2* diag) {
+  const long long nnz = A.nnz, npairs = A.pairs->npairs;
+  const size_t N = (size_t)c->N;
+  Cd *blk = nullptr, *blkM = nullptr;
+  double2 *zhalf = nullptr, *zMhalf = nullptr;
   int rc = AIM_OK;
   do {
-    FillGeom g{};
-    double *vert = nullptr, *area = nullptr, *len = nullptr, *lam = nullptr;
-    int32_t *tri = nullptr, *tp = nullptr, *tm = nullptr, *sp = nullptr, *sm = nullptr;
-    int32_t *tptr = nullptr, *pP = nullptr, *pQ = nullptr, *ids = nullptr, *erow = nullptr, *ecol = nullptr,
-            *nptr = nullptr, *anc = nullptr;
-    double2 *gtab = nullptr, *zhalf = nullptr, *val = nullptr, *diag = nullptr;
-    Cd* blk = nullptr;
-    if ((rc = dev((void**)&vert, A.vert, sizeof(double) * 3 * A.nv)) ||
-        (rc = dev((void**)&tri, A.tri, sizeof(int32_t) * 3 * A.nt)) ||
-        (rc = dev((void**)&area, A.area, sizeof(double) * A.nt)) ||
-        (rc = dev((void**)&tp, A.tp, sizeof(int32_t) * N)) || (rc = dev((void**)&tm, A.tm, sizeof(int32_t) * N)) ||
-        (rc = dev((void**)&sp, A.sp, sizeof(int32_t) * N)) || (rc = dev((void**)&sm, A.sm, sizeof(int32_t) * N)) ||
-        (rc = dev((void**)&len, A.len, sizeof(double) * N)) ||
-        (rc = dev((void**)&tptr, A.tptr, sizeof(int32_t) * (A.nt + 1))) ||
-        (rc = dev((void**)&pP, A.pP, sizeof(int32_t) * npairs)) ||
-        (rc = dev((void**)&pQ, A.pQ, sizeof(int32_t) * npairs)) ||
-        (rc = dev((void**)&ids, A.ids, sizeof(int32_t) * npairs)) ||
-        (rc = dev((void**)&erow, A.erow, sizeof(int32_t) * nnz)) ||
-        (rc = dev((void**)&ecol, A.ecol, sizeof(int32_t) * nnz)) ||
-        (rc = dev((void**)&nptr, A.nptr, sizeof(int32_t) * (N + 1))) ||
-        (rc = dev((void**)&anc, A.anchor, sizeof(int32_t) * 3 * N)) ||
-        (rc = dev((void**)&lam, A.lam, sizeof(double) * N * 4 * A.S)) ||
-        (rc = dev((void**)&gtab, A.gtab, sizeof(double2) * A.ntab)) ||
-        (rc = dev((void**)&blk, nullptr, sizeof(Cd) * 9 * npairs)) ||
-        (rc = dev((void**)&zhalf, nullptr, sizeof(double2) * 2 * nnz)) ||
-        (rc = dev((void**)&val, nullptr, sizeof(double2) * nnz)) || (rc = dev((void**)&diag, nullptr, sizeof(double2) * N)))
-      break;
-    Cd* blkM = nullptr;
-    double2* zMhalf = nullptr;
-    double* lamM = nullptr;
-    if (A.lamM && ((rc = dev((void**)&blkM, nullptr, sizeof(Cd) * 9 * npairs)) ||
-                   (rc = dev((void**)&zMhalf, nullptr, sizeof(double2) * 2 * nnz)) ||
-                   (rc = dev((void**)&lamM, A.lamM, sizeof(double) * N * 3 * A.S))))
-      break;
     if ((rc = [&]() -> int {
+           AIM_CUDA_TRY(cudaMallocAsync(&blk, sizeof(Cd) * 9 * std::max<long long>(1, npairs), c->stream));
+           AIM_CUDA_TRY(cudaMallocAsync(&zhalf, sizeof(double2) * 2 * std::max<long long>(1, nnz), c->stream));
+           if (A.lamM) {
+             AIM_CUDA_TRY(cudaMallocAsync(&blkM, sizeof(Cd) * 9 * std::max<long long>(1, npairs), c->stream));
+             AIM_CUDA_TRY(cudaMallocAsync(&zMhalf, sizeof(double2) * 2 * std::max<long long>(1, nnz), c->stream));
+           }
            const TriRule* rs[3] = {A.rule_test, A.rule_test_sing, A.rule_src};
            for (int i = 0; i < 3; ++i)
              AIM_CUDA_TRY(cudaMemcpyToSymbolAsync(c_rules, rs[i], sizeof(TriRule), i * kRuleStride,
@@ -324,37 +312,36 @@ int near_fill_device(aim_ctx* c, const NearFillArgs& A, double* val_out, double*
            return AIM_OK;
          }()))
       break;
-    g.vert = vert; g.tri = tri; g.area = area; g.tp = tp; g.tm = tm; g.sp = sp; g.sm = sm; g.len = len;
+    FillGeom g{};
+    g.vert = A.g.vert; g.tri = A.g.tri; g.area = A.g.area; g.tp = A.g.tp; g.tm = A.g.tm; g.sp = A.g.sp;
+    g.sm = A.g.sm; g.len = A.g.len;
+    const PairLists& pl = *A.pairs;
     // ids: the nsing singular pairs first, then the regular ones
-    const int64_t nreg = npairs - A.nsing;
-    if (A.nsing > 0) {
-      AIM_LAUNCH(c, "near_pair_blocks", (k_pair_blocks<true><<<(unsigned)((A.nsing + 127) / 128), 128, 0, c->stream>>>(
-                                            g, ids, pP, pQ, (int)A.nsing, c->k, blk, blkM)));
+    const long long nreg = npairs - pl.nsing;
+    if (pl.nsing > 0) {
+      AIM_LAUNCH(c, "near_pair_blocks", (k_pair_blocks<true><<<(unsigned)((pl.nsing + 127) / 128), 128, 0, c->stream>>>(
+                                            g, pl.ids, pl.pP, pl.pQ, (int)pl.nsing, c->k, blk, blkM)));
       if ((rc = launch_check(c, "near_pair_blocks"))) break;
     }
     if (nreg > 0) {
       AIM_LAUNCH(c, "near_pair_blocks", (k_pair_blocks<false><<<(unsigned)((nreg + 127) / 128), 128, 0, c->stream>>>(
-                                            g, ids + A.nsing, pP, pQ, (int)nreg, c->k, blk, blkM)));
+                                            g, pl.ids + pl.nsing, pl.pP, pl.pQ, (int)nreg, c->k, blk, blkM)));
       if ((rc = launch_check(c, "near_pair_blocks"))) break;
     }
     const double jke = c->k * kEta0;
-    AIM_LAUNCH(c, "near_halves", (k_near_halves<<<152 * 16, 256, 0, c->stream>>>(g, erow, ecol, tptr, pQ, blk, nnz,
-                                                                                   jke, zhalf, blkM, zMhalf)));
+    AIM_LAUNCH(c, "near_halves", (k_near_halves<<<152 * 16, 256, 0, c->stream>>>(g, A.erow, A.ecol, pl.tptr, pl.pQ, blk,
+                                                                                   nnz, jke, zhalf, blkM, zMhalf)));
     if ((rc = launch_check(c, "near_halves"))) break;
-    AIM_LAUNCH(c, "near_values", (k_near_values<<<152 * 16, 256, 0, c->stream>>>(erow, ecol, nptr, zhalf, lam, anc, gtab,
-                                                                                   A.TE, A.P, nnz, c->k, jke, val,
-                                                                                   diag, zMhalf, lamM, A.alpha)));
+    AIM_LAUNCH(c, "near_values", (k_near_values<<<152 * 16, 256, 0, c->stream>>>(A.erow, A.ecol, A.nptr, zhalf, A.lam,
+                                                                                   A.anchor, A.gtab, A.TE, A.P, nnz,
+                                                                                   c->k, jke, val, diag, zMhalf,
+                                                                                   A.lamM, A.alpha)));
     if ((rc = launch_check(c, "near_values"))) break;
-    if ((rc = [&]() -> int {
-           AIM_CUDA_TRY(cudaMemcpyAsync(val_out, val, sizeof(double2) * nnz, cudaMemcpyDeviceToHost, c->stream));
-           AIM_CUDA_TRY(cudaMemcpyAsync(diag_out, diag, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
-           AIM_CUDA_TRY(cudaStreamSynchronize(c->stream));
-           return AIM_OK;
-         }()))
-      break;
   } while (false);
-  cudaStreamSynchronize(c->stream);
-  for (void* p : bufs) cudaFree(p);
+  cudaFreeAsync(blk, c->stream);
+  cudaFreeAsync(zhalf, c->stream);
+  if (blkM) cudaFreeAsync(blkM, c->stream);
+  if (zMhalf) cudaFreeAsync(zMhalf, c->stream);
   return rc;
 }
 
