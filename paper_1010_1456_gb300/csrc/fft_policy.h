@@ -99,6 +99,11 @@ struct P32 {
   }
   AIM_HD static T half(T a) { return make_float2(0.5f * a.x, 0.5f * a.y); }
   template <bool INV> AIM_HD static T mul_mi(T a) { return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x); }
+  // m + sg * mul_mi(c d) with one fused multiply-add per component (sg = +-1)
+  template <bool INV, int SG> AIM_HD static T add_mi_scaled(T m, T d, double, float c, float) {
+    const float cs = SG * (INV ? -c : c);
+    return make_float2(fmaf(cs, d.y, m.x), fmaf(-cs, d.x, m.y));
+  }
   AIM_HD static T conj_if(T w, bool c) { return c ? make_float2(w.x, -w.y) : w; }
 };
 
@@ -119,6 +124,10 @@ struct P64 {
   }
   AIM_HD static T half(T a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
   template <bool INV> AIM_HD static T mul_mi(T a) { return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x); }
+  template <bool INV, int SG> AIM_HD static T add_mi_scaled(T m, T d, double c, float, float) {
+    const double cs = SG * (INV ? -c : c);
+    return make_double2(fma(cs, d.y, m.x), fma(-cs, d.x, m.y));
+  }
   AIM_HD static T conj_if(T w, bool c) { return c ? make_double2(w.x, -w.y) : w; }
 };
 
@@ -145,6 +154,10 @@ struct PFF {
   }
   __device__ static T half(T a) { return cff{ff{0.5f * a.re.hi, 0.5f * a.re.lo}, ff{0.5f * a.im.hi, 0.5f * a.im.lo}}; }
   template <bool INV> __device__ static T mul_mi(T a) { return INV ? cff{ff_neg(a.im), a.re} : cff{a.im, ff_neg(a.re)}; }
+  template <bool INV, int SG> __device__ static T add_mi_scaled(T m, T d, double c, float ch, float cl) {
+    const T t = mul_mi<INV>(mulr(d, c, ch, cl));
+    return SG > 0 ? add(m, t) : sub(m, t);
+  }
   __device__ static T conj_if(T w, bool c) { return c ? cff{w.re, ff_neg(w.im)} : w; }
 };
 
@@ -161,10 +174,10 @@ template <class P, bool INV> AIM_HD __forceinline__ void dft3(typename P::T* v) 
   using T = typename P::T;
   const T a = v[0], s = P::add(v[1], v[2]), d = P::sub(v[1], v[2]);
   const T m = P::sub(a, P::half(s));
-  const T t = P::template mul_mi<INV>(P::mulr(d, AIM_RC(0.86602540378443864676)));  // sin(2 pi / 3)
+  // v1, v2 = m +- (-i) sin(2 pi / 3) d (forward; +i inverse), each a fused multiply-add
   v[0] = P::add(a, s);
-  v[1] = P::add(m, t);
-  v[2] = P::sub(m, t);
+  v[1] = P::template add_mi_scaled<INV, 1>(m, d, AIM_RC(0.86602540378443864676));
+  v[2] = P::template add_mi_scaled<INV, -1>(m, d, AIM_RC(0.86602540378443864676));
 }
 template <class P, bool INV> AIM_HD __forceinline__ void dft4(typename P::T* v) {
   using T = typename P::T;
