@@ -9,7 +9,7 @@ Green's function, projection or solver), so both the CPU oracle and the CUDA
 path may consume its output without sharing any of the method.
 """
 
-from .meshes import plate_mesh, icosphere_mesh, icosphere_frequency, mesh_mean_edge
+from .meshes import plate_mesh, rect_plate_mesh, icosphere_mesh, icosphere_frequency, mesh_mean_edge
 from .incidence import (
     planewave_minus_z_xpol,
     random_incidence,
@@ -19,6 +19,7 @@ from .incidence import (
 
 __all__ = [
     "plate_mesh",
+    "rect_plate_mesh",
     "icosphere_mesh",
     "icosphere_frequency",
     "mesh_mean_edge",

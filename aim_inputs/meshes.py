@@ -39,6 +39,31 @@ def plate_mesh(side, n_squares):
     return verts, tris
 
 
+def rect_plate_mesh(side_x, side_y, nx_squares, ny_squares):
+    """Rectangular plate [-side_x/2, side_x/2] x [-side_y/2, side_y/2] in the z=0
+    plane, cut into nx_squares x ny_squares cells split as in ``plate_mesh``
+    (vertex (i, j) has index j*(nx_squares+1)+i).  Long strips of it give
+    padded grid lengths far apart on the two axes."""
+    nx, ny = int(nx_squares), int(ny_squares)
+    if nx < 1 or ny < 1:
+        raise ValueError("square counts must be >= 1")
+    tx = np.arange(nx + 1, dtype=np.float64) * (float(side_x) / nx) - 0.5 * float(side_x)
+    ty = np.arange(ny + 1, dtype=np.float64) * (float(side_y) / ny) - 0.5 * float(side_y)
+    X, Y = np.meshgrid(tx, ty, indexing="xy")  # [j, i]
+    verts = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], axis=1)
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    i = i.ravel()
+    j = j.ravel()
+    v00 = j * (nx + 1) + i
+    v10 = v00 + 1
+    v01 = v00 + (nx + 1)
+    v11 = v01 + 1
+    tris = np.empty((2 * nx * ny, 3), dtype=np.int32)
+    tris[0::2] = np.stack([v00, v10, v11], axis=1)
+    tris[1::2] = np.stack([v00, v11, v01], axis=1)
+    return verts, tris
+
+
 def _icosahedron():
     phi = (1.0 + np.sqrt(5.0)) / 2.0
     v = []

@@ -542,11 +542,11 @@ def run_serve(args):
 
 
 # ---------------------------------------------------------------- complexity sweep
-SWEEP = {"plate": (1, 2, 4, 8, 16, 32), "sphere": (1, 2, 4, 8, 16)}
+SWEEP = {"plate": (1, 2, 4, 8, 16, 32, 64), "sphere": (1, 2, 4, 8, 16)}
 
 
 def run_sweep(args):
-    """Matvec time against N over the plates 1-32 lambda and spheres 1-16 lambda
+    """Matvec time against N over the plates 1-64 lambda and spheres 1-16 lambda
     (the shape of the paper's complexity figure, Section 3, on one GPU): one
     right-hand side, complex64 and FP64-accurate products, FFT kernels
     autotuned, L2 flushed between products."""
@@ -594,7 +594,7 @@ def run_sweep(args):
         del ctx
         torch.cuda.empty_cache()
     line = {"metric": "AIM matvec time vs N (complexity sweep)", "unit": "ms", "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": "PEC plates 1-32 lambda (mesh lambda/9) and icospheres 1-16 lambda, h = lambda/10, "
+            "config": {"workload": "PEC plates 1-64 lambda (mesh lambda/9) and icospheres 1-16 lambda, h = lambda/10, "
                                    "M = 2, near radius 3h, one RHS", "l2": "flushed between products"},
             "rows": rows}
     print(json.dumps(line), flush=True)

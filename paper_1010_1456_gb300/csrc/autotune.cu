@@ -83,6 +83,10 @@ static int autotune(aim_ctx* c, int precision, int nrhs, int reps, int32_t* kern
       c->fft_kernel[pol][pass] = k;
       double ms = 0.0;
       rc = time_pass(c, pass, x, y, nrhs, precision, reps, &ms);
+      if (rc == AIM_EINVAL) {  // this kernel does not serve the length (shared memory): not a candidate
+        rc = AIM_OK;
+        continue;
+      }
       if (rc != AIM_OK) break;
       if (ms_out) ms_out[pass * AIM_FFT_KERNELS + k] = ms;
       if (best == AIM_FFT_AUTO || ms < best_ms) {

@@ -481,14 +481,21 @@ int build_ghat(aim_ctx* c) {
   s.n_in = Lz; s.n_out = Lz; s.X = Lx; s.A = Ly;
   s.sG_in = total; s.sA_in = Lx; s.sP_in = (long long)Ly * Lx;
   s.sG_out = total; s.sA_out = Lx; s.sP_out = (long long)Ly * Lx;
+  // full transforms; four-step kernels where the length has one (longer than the Stockham kernel allows)
+  const auto pass = [&](const char* name, const double2* in, double2* out, const StridedArgs& sa, int d) -> int {
+    const int rc = Fft4<P64>::strided(c, name, false, in, out, sa, 1, c->L[d], c->p64.tw[d], false);
+    if (rc == 1) return AIM_OK;
+    if (rc < 0) return -rc;
+    return launch_strided<P64, false>(c, name, in, out, sa, 1, c->plan_dev + d, c->L[d], c->p64.tw[d]);
+  };
   if (Lz > 1)
-    AIM_TRY((launch_strided<P64, false>(c, "ghat_z", a, b, s, 1, c->plan_dev + 2, Lz, c->p64.tw[2])));
+    AIM_TRY(pass("ghat_z", a, b, s, 2));
   else
     std::swap(a, b);
   s.n_in = Ly; s.n_out = Ly; s.X = Lx; s.A = Lz;
   s.sA_in = (long long)Ly * Lx; s.sP_in = Lx;
   s.sA_out = (long long)Ly * Lx; s.sP_out = Lx;
-  AIM_TRY((launch_strided<P64, false>(c, "ghat_y", b, a, s, 1, c->plan_dev + 1, Ly, c->p64.tw[1])));
+  AIM_TRY(pass("ghat_y", b, a, s, 1));
   XArgs x{};
   x.nx = Lx; x.rows_y = Ly; x.rows_z = Lz; x.G = 1; x.sG = total;
   x.hx = Lx / 2 + 1; x.hy = Ly / 2 + 1; x.hz = Lz / 2 + 1;

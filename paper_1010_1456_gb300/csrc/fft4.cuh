@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256, 4) fft4_strided_occ4(const typename P::S*
                                                             int AY) {
   strided_body<P, INV, L1, L2, O, WIDE>(in, out, a, twL, AY);
 }
-template <class P, int L> constexpr bool strided_occ4() { return sizeof(typename P::S) <= 8 && L >= 648; }
+template <class P, int L> constexpr bool strided_occ4() { return sizeof(typename P::S) <= 8 && L == 648; }
 
 // The fused x pass.  With k = k1 + L1 k2 and n = n2 + L2 n1,
 //   forward  X[k1 + L1 k2] = sum_n2 w_L2^(n2 k2) w_L^(n2 k1) sum_n1 x[L2 n1 + n2] w_L1^(n1 k1),
@@ -160,8 +160,10 @@ template <class P, int L> constexpr bool strided_occ4() { return sizeof(typename
 // and keeps the RY rows of Ghat in shared memory.
 // Resident 256-thread blocks per SM the register allocation must allow: four
 // for complex64 (three for the longest compiled length, 648, which would
-// spill at four), two for the 16-byte policies.
-template <class P, int L> constexpr int x_min_blocks() { return sizeof(typename P::S) <= 8 ? (L >= 648 ? 3 : 4) : 2; }
+// spill at four; two above it), two for the 16-byte policies (one above 648).
+template <class P, int L> constexpr int x_min_blocks() {
+  return sizeof(typename P::S) <= 8 ? (L > 648 ? 2 : L == 648 ? 3 : 4) : (L > 648 ? 1 : 2);
+}
 
 template <class P, int L1, int L2>
 __global__ void __launch_bounds__(256, x_min_blocks<P, L1 * L2>()) fft4_x(typename P::S* __restrict__ buf, XArgs4 a,
@@ -345,6 +347,7 @@ __global__ void __launch_bounds__(256, x_min_blocks<P, L1 * L2>()) fft4_x_groups
   X(180, 12, 15)                \
   X(324, 18, 18)                \
   X(360, 18, 20)                \
-  X(648, 24, 27)
+  X(648, 24, 27)                \
+  X(1296, 36, 36)
 
 }  // namespace aim

@@ -250,9 +250,13 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
     Nc *= c->n[d];
     Lprod *= c->L[d];
   }
-  if (Nc >= (1LL << 31) || Lprod >= (1LL << 31) || c->L[1] > 900 || c->L[2] > 900 || c->L[0] > 4096) {
+  // strided (y, z) passes: a four-step length up to 1296, any other 2,3,5-smooth length up to 900 (the
+  // Stockham kernel's shared-memory limit)
+  int l1 = 0, l2 = 0;
+  const auto strided_ok = [&](int L) { return L <= 900 || (L <= 1296 && fourstep_split(L, &l1, &l2)); };
+  if (Nc >= (1LL << 31) || Lprod >= (1LL << 31) || !strided_ok(c->L[1]) || !strided_ok(c->L[2]) || c->L[0] > 4096) {
     set_error("aim_setup: grid too large (padded " + std::to_string(c->L[0]) + "x" + std::to_string(c->L[1]) + "x" +
-              std::to_string(c->L[2]) + "; y and z must be <= 900)");
+              std::to_string(c->L[2]) + "; y and z must be <= 900, or 1296)");
     return AIM_EINVAL;
   }
 

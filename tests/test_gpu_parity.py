@@ -472,3 +472,25 @@ def test_mem_budget_and_non_finite_inputs():
     with pytest.raises(g.AIMError):
         g.aim_rcs(ctx, V, np.array([0.1, np.nan]), np.array([0.0, 0.0]))
     ctx.close()
+
+
+@pytest.mark.parametrize("along", ["x", "y"])
+def test_longest_padded_length_strip(along):
+    """A 64 lambda x 1 lambda strip (576 x 9 lambda/9 squares) pads one axis to
+    1296 = 36 x 36, the longest four-step length (the 64 lambda plate's):
+    along x the fused x pass runs at 1296, along y the strided passes do; on
+    the full three-dimensional grid (no plane collapse), every precision."""
+    from aim_inputs import rect_plate_mesh
+
+    v, t = rect_plate_mesh(64.0, 1.0, 576, 9) if along == "x" else rect_plate_mesh(1.0, 64.0, 9, 576)
+    ctx, op = make(v, t, max_rhs=2, planar=False)
+    n, L, _ = g.aim_grid_info(ctx)
+    assert (L[0] if along == "x" else L[1]) == 1296
+    x = random_complex((2, ctx.N), 95)
+    ref = op.matvec(x)
+    for prec in WIDE:
+        y = g.aim_matvec(ctx, torch.from_numpy(x).cuda(), precision=prec).cpu().numpy()
+        assert rel(y, ref) <= 1e-12, (prec, rel(y, ref))
+    y32 = g.aim_matvec(ctx, torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
+    assert rel(y32, op.matvec(x.astype(np.complex64).astype(np.complex128))) <= 1e-5
+    ctx.close()
