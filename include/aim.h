@@ -67,6 +67,7 @@ enum {
 enum { AIM_C64 = 1, AIM_C128 = 2, AIM_C128_F64 = 3 };
 
 typedef struct aim_ctx aim_ctx; /* opaque, library-owned */
+typedef struct aim_pack aim_pack; /* opaque, library-owned: several contexts batched (aim_pack_create) */
 
 /* Triangle mesh, copied by aim_setup (caller keeps ownership). */
 typedef struct {
@@ -364,6 +365,61 @@ int aim_autotune(aim_ctx* ctx, int precision, int nrhs, int reps, int32_t* kerne
  * aim_footprint's estimate.  The context itself is built by aim_setup.
  */
 int aim_matvec_c64_noalloc(aim_ctx* ctx, const void* x_dev, void* y_dev, int nrhs);
+
+/*
+ * Multi-instance batching: several contexts (small scatterers, each with its
+ * own mesh, weights, near list, CFIE weight and right-hand sides) go through
+ * one launch per product stage.  The paper has no counterpart (it solves one
+ * scatterer at a time); this serves a stream of many small requests, whose
+ * products are launch-bound one by one.
+ *
+ * The pack lays every instance's grids over one box: per axis the largest
+ * unpadded extent n_p and the largest padded length L_p among the instances.
+ * Both come from an instance, so L_p >= 2 n_p - 1, and the pack's Green's
+ * function spectrum (the circulant embedding over n_p on L_p, built at
+ * creation) reproduces every instance's convolution exactly: an instance's
+ * nodes fill the corner [0, n_i) of the box, so its products only involve
+ * offsets |d| < n_i, where the two embeddings agree.  Products therefore equal
+ * each instance's own to rounding.  Right-hand side b of the packed vectors
+ * belongs to one instance; its four grids are the pack's grids 4b .. 4b+3,
+ * and the z, y and x passes run over all of them at once.  Projection and
+ * interpolation read each instance's own lists through a table of
+ * descriptors.
+ *
+ * Packed vectors are RHS-major with row length ld = max N_i (aim_pack_dims):
+ * element (b, m) at b*ld + m; instance i owns rows b0_i .. b0_i + nrhs_i - 1
+ * (b0_0 = 0, in the order of ctxs), and entries m >= N_i of its rows are
+ * padding, which products write as zero and solves keep at zero (right-hand
+ * sides must be zero there).
+ *
+ * aim_pack_create: ctxs[K] (1 <= K <= 256, distinct), nrhs[K] (1 <= nrhs_i
+ *   <= max_rhs of ctxs[i], sum <= 256).  The contexts must share the device,
+ *   k, h, M and the stencil layout (all planar, or none), and must outlive
+ *   the pack; while the pack is in use they must not run work of their own.
+ *   The pack takes stream, restart, maxit and check_every from ctxs[0]'s
+ *   options; its solver runs complex64 Arnoldi products with FP64-accurate
+ *   true residuals (AIM_C64 refinement).  Allocates the pack's grids,
+ *   spectrum and staging vectors; synchronises.  AIM_EINVAL for mismatched
+ *   contexts or bad counts.
+ * aim_pack_dims: ld, total right-hand sides, and the first row b0 of each
+ *   instance (b0 may be NULL, else [K]).
+ * aim_pack_matvec: y = Z~ x for every packed row.  AIM_C64: x_dev, y_dev c64
+ *   [B][ld], one launch per stage for all instances.  AIM_C128 or
+ *   AIM_C128_F64: c128 [B][ld], each instance's FP64-accurate product in turn
+ *   (the solver's true residuals).  x and y must not overlap.
+ * aim_pack_solve: every instance's system at once, each right-hand side with
+ *   its own Arnoldi process and diagonal preconditioner (as aim_solve); V_dev,
+ *   X_dev c128 [B][ld]; info->rel_res and converged have B entries.
+ *   Synchronises.
+ * aim_pack_set_stream: the stream of the pack's work.
+ * aim_pack_destroy: frees the pack (not the contexts); NULL is a no-op.
+ */
+int aim_pack_create(aim_ctx* const* ctxs, int K, const int32_t* nrhs, aim_pack** out);
+int aim_pack_dims(const aim_pack* pack, int64_t* ld, int32_t* nrhs_total, int32_t* b0);
+int aim_pack_matvec(aim_pack* pack, const void* x_dev, void* y_dev, int precision);
+int aim_pack_solve(aim_pack* pack, const void* V_dev, void* X_dev, double tol, aim_solve_info* info);
+int aim_pack_set_stream(aim_pack* pack, void* stream);
+void aim_pack_destroy(aim_pack* pack);
 
 const char* aim_strerror(int code);
 const char* aim_last_error(void); /* thread-local detail of the last failure */

@@ -228,6 +228,115 @@ def aim_solve(ctx, V, tol=1e-6, X=None, raise_on_noconv=True):
     }
 
 
+class Pack:
+    """Owning handle of an ``aim_pack*`` (aim_pack_create): several contexts
+    batched through one launch per product stage.  ``ld`` is the packed row
+    length, ``B`` the total of right-hand sides, ``b0[i]`` the first row of
+    instance i.  The contexts must outlive the pack."""
+
+    def __init__(self, handle, ctxs, nrhs, ld, B, b0):
+        self.handle = handle
+        self.ctxs = list(ctxs)
+        self.nrhs = list(nrhs)
+        self.ld = ld
+        self.B = B
+        self.b0 = b0
+
+    def close(self):
+        if self.handle:
+            load().aim_pack_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def rows(self, i):
+        """(first row, end row, columns) of instance i in the packed vectors."""
+        return self.b0[i], self.b0[i] + self.nrhs[i], self.ctxs[i].N
+
+    def pack(self, parts, dtype=None):
+        """Packed [B, ld] device tensor (zero padding) from per-instance [nrhs_i, N_i] tensors."""
+        torch = _torch()
+        dtype = parts[0].dtype if dtype is None else dtype
+        out = torch.zeros((self.B, self.ld), dtype=dtype, device=parts[0].device)
+        for i, p in enumerate(parts):
+            r0, r1, n = self.rows(i)
+            out[r0:r1, :n] = p.reshape(r1 - r0, n)
+        return out
+
+    def unpack(self, X):
+        """Per-instance [nrhs_i, N_i] views of a packed tensor."""
+        out = []
+        for i in range(len(self.ctxs)):
+            r0, r1, n = self.rows(i)
+            out.append(X[r0:r1, :n])
+        return out
+
+
+def aim_pack_create(ctxs, nrhs):
+    """Pack contexts (sharing device, k, h, M and stencil layout) with nrhs[i]
+    right-hand sides each; see aim_pack_create in aim.h."""
+    lib = load()
+    K = len(ctxs)
+    hs = (C.c_void_p * K)(*[c.handle for c in ctxs])
+    nr = (C.c_int32 * K)(*[int(n) for n in nrhs])
+    h_ = C.c_void_p()
+    check(lib.aim_pack_create(hs, K, nr, C.byref(h_)), "aim_pack_create")
+    ld = C.c_int64()
+    B = C.c_int32()
+    b0 = (C.c_int32 * K)()
+    check(lib.aim_pack_dims(h_, C.byref(ld), C.byref(B), b0), "aim_pack_dims")
+    return Pack(h_, ctxs, nrhs, int(ld.value), int(B.value), [int(v) for v in b0])
+
+
+def aim_pack_set_stream(pack, stream):
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    check(load().aim_pack_set_stream(pack.handle, C.c_void_p(h)), "aim_pack_set_stream")
+
+
+def aim_pack_matvec(pack, x, y=None, precision=None):
+    """y = Z~ x on packed [B, ld] vectors (complex64: one launch per stage)."""
+    torch = _torch()
+    if precision is None:
+        precision = AIM_C128 if x.dtype == torch.complex128 else AIM_C64
+    dt = torch.complex64 if precision == AIM_C64 else torch.complex128
+    if y is None:
+        y = torch.empty_like(x)
+    check(load().aim_pack_matvec(pack.handle, _dev(x, dt), _dev(y, dt), int(precision)), "aim_pack_matvec")
+    return y
+
+
+def aim_pack_solve(pack, V, tol=1e-6, X=None, raise_on_noconv=True):
+    """Solve every instance's system at once (packed complex128 [B, ld]); returns (X, info dict)."""
+    torch = _torch()
+    if X is None:
+        X = torch.empty_like(V)
+    B = pack.B
+    rel = (C.c_double * B)()
+    conv = (C.c_int32 * B)()
+    info = aim_solve_info(0, 0, C.cast(rel, C.POINTER(C.c_double)), C.cast(conv, C.POINTER(C.c_int32)))
+    code = load().aim_pack_solve(pack.handle, _dev(V, torch.complex128), _dev(X, torch.complex128), float(tol),
+                                 C.byref(info))
+    if code != 0 and not (code == AIM_ENOCONV and not raise_on_noconv):
+        check(code, "aim_pack_solve")
+    return X, {
+        "iterations": info.iterations,
+        "restarts": info.restarts,
+        "rel_res": np.array(rel[:]),
+        "converged": np.array(conv[:], dtype=bool),
+        "status": code,
+    }
+
+
 def aim_rcs(ctx, X, theta, phi):
     """(sigma_thth, sigma_phph) [nrhs, ndir] (numpy) of device currents X."""
     torch = _torch()

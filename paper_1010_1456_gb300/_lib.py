@@ -77,6 +77,12 @@ SIGNATURES = {
     "aim_probe_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "aim_fft_config": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "aim_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "aim_pack_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_void_p)]),
+    "aim_pack_dims": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "aim_pack_matvec": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "aim_pack_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(aim_solve_info)]),
+    "aim_pack_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "aim_pack_destroy": (None, [C.c_void_p]),
     "aim_strerror": (C.c_char_p, [C.c_int]),
     "aim_last_error": (C.c_char_p, []),
 }

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaim.so")
-SOURCES = ["api.cu", "setup.cu", "setup_dev.cu", "fft.cu", "matvec.cu", "krylov.cu", "rcs.cu", "rcs_ref.cu", "probe.cu", "profile.cu", "noalloc.cu", "autotune.cu", "nearfill.cu", "fft4_p32.cu",
+SOURCES = ["api.cu", "setup.cu", "setup_dev.cu", "fft.cu", "matvec.cu", "krylov.cu", "rcs.cu", "rcs_ref.cu", "probe.cu", "profile.cu", "noalloc.cu", "autotune.cu", "nearfill.cu", "pack.cu", "fft4_p32.cu",
            "fft4_p64.cu", "fft4_pff.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = [

@@ -30,7 +30,7 @@ template <typename R> static void free_prec(PrecData<R>& p) {
   p = PrecData<R>{};
 }
 
-static void free_ctx(aim_ctx* c) {
+void free_context(aim_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   free_prec(c->p64);
@@ -259,14 +259,14 @@ int aim_setup(const aim_mesh* mesh, double k, double h, int M, double near_radiu
   }
   if (rc != AIM_OK) {
     if (rc == AIM_ECUDA && cudaGetLastError() == cudaErrorMemoryAllocation) rc = AIM_ENOMEM;
-    free_ctx(c);
+    free_context(c);
     return rc;
   }
   *out = c;
   return AIM_OK;
 }
 
-void aim_destroy(aim_ctx* ctx) { free_ctx(ctx); }
+void aim_destroy(aim_ctx* ctx) { free_context(ctx); }
 
 int aim_set_stream(aim_ctx* ctx, void* stream) {
   AIM_TRY(check_ctx(ctx));

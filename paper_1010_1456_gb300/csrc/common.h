@@ -219,6 +219,12 @@ struct aim_ctx {
   aim::KrylovWork kw;
   aim::Profiler prof;
   int max_rhs = 1;
+  // Multi-instance packs (pack.cu): the pack's internal context has `pack`
+  // set, so its products run the packed kernels, and holds one diagonal per
+  // right-hand side (dinv_ld = N, the packed row length; 0: one diagonal for
+  // every right-hand side).
+  aim_pack* pack = nullptr;
+  long long dinv_ld = 0;
 };
 
 namespace aim {
@@ -289,6 +295,13 @@ constexpr int kRhsLanesMin = 16;
 // Forgets the solver's captured Arnoldi step (after the kernel choice changed).
 void drop_step_graph(aim_ctx* c);
 void free_krylov(aim_ctx* c);
+// setup.cu: FFT plans (c->plan set), twiddle tables and spectrum storage.
+int fft_tables(aim_ctx* c);
+// api.cu: frees a context and everything it owns.
+void free_context(aim_ctx* c);
+// pack.cu: products and preparation of a pack's internal context.
+int pack_matvec(aim_ctx* c, const void* x, void* y, int nrhs, int precision);
+int pack_prepare(aim_ctx* c, int precision);
 // rcs.cu
 int rhs_planewave(aim_ctx* c, int nrhs, const double* khat, const double* pol, double2* V);
 int rcs(aim_ctx* c, const double2* X, int nrhs, int ndir, const double* theta, const double* phi,

@@ -236,14 +236,15 @@ __global__ void __launch_bounds__(256) k_normalize(const double2* __restrict__ w
 __global__ void k_next_j(int* jdev) { *jdev += 1; }
 __global__ void k_set_j(int* jdev, int j) { *jdev = j; }
 
-// z = dinv .* V_j, in precision R
+// z = dinv .* V_j, in precision R (dinv: row b at b * ldd; ldd = 0 shares one diagonal)
 template <typename R>
 __global__ void k_precond(const double2* __restrict__ V, const double2* __restrict__ dinv, cplx<R>* __restrict__ z,
-                          const int* __restrict__ jdev, int N, long long ldv) {
+                          const int* __restrict__ jdev, int N, long long ldv, long long ldd) {
   const int b = blockIdx.y;
   const double2* v = V + (long long)b * ldv + (long long)(*jdev) * N;
+  const double2* db = dinv + (long long)b * ldd;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
-    const double2 a = v[n], d = dinv[n];
+    const double2 a = v[n], d = db[n];
     z[(long long)b * N + n] = cmake<cplx<R>>(a.x * d.x - a.y * d.y, a.x * d.y + a.y * d.x);
   }
 }
@@ -262,7 +263,8 @@ __global__ void k_residual(const double2* __restrict__ Vrhs, const double2* __re
 
 // X[b] += dinv .* (sum_i y_i V_i)   (active right-hand sides only)
 __global__ void k_xupdate(const double2* __restrict__ V, const double2* __restrict__ y, const double2* __restrict__ dinv,
-                          double2* __restrict__ X, int N, int kk, int m, int ldv_vec, const int* __restrict__ active) {
+                          double2* __restrict__ X, int N, int kk, int m, int ldv_vec, const int* __restrict__ active,
+                          long long ldd) {
   __shared__ double2 ys[256];
   const int b = blockIdx.y;
   if (!active[b]) return;
@@ -276,7 +278,7 @@ __global__ void k_xupdate(const double2* __restrict__ V, const double2* __restri
       s.x += t.x * v.x - t.y * v.y;
       s.y += t.x * v.y + t.y * v.x;
     }
-    const double2 d = dinv[n];
+    const double2 d = dinv[(long long)b * ldd + n];
     double2& x = X[(long long)b * N + n];
     x.x += s.x * d.x - s.y * d.y;
     x.y += s.x * d.y + s.y * d.x;
@@ -359,12 +361,14 @@ struct Solver {
   // the Hessenberg column H[j], v_{j+1} = w / |w|, j += 1.
   int step(int precision) {
     if (precision == AIM_C64) {
-      AIM_LAUNCH(c, "k_precond", k_precond<float><<<vgrid(), 256, 0, st>>>(k.V, c->dinv64, c->p32.xbuf, k.jdev, N, ldV()));
+      AIM_LAUNCH(c, "k_precond", k_precond<float><<<vgrid(), 256, 0, st>>>(k.V, c->dinv64, c->p32.xbuf, k.jdev, N, ldV(),
+                                                                           c->dinv_ld));
       AIM_TRY(chk("k_precond"));
       AIM_TRY(matvec(c, c->p32.xbuf, c->p32.ybuf, B, AIM_C64));
       AIM_TRY(convert_c64_to_c128(c, c->p32.ybuf, k.w, (int64_t)B * N));
     } else {
-      AIM_LAUNCH(c, "k_precond", k_precond<double><<<vgrid(), 256, 0, st>>>(k.V, c->dinv64, c->p64.xbuf, k.jdev, N, ldV()));
+      AIM_LAUNCH(c, "k_precond", k_precond<double><<<vgrid(), 256, 0, st>>>(k.V, c->dinv64, c->p64.xbuf, k.jdev, N, ldV(),
+                                                                            c->dinv_ld));
       AIM_TRY(chk("k_precond"));
       AIM_TRY(matvec(c, c->p64.xbuf, k.w, B, precision));
     }
@@ -583,7 +587,8 @@ int solve(aim_ctx* c, const double2* V, double2* X, int nrhs, double tol, aim_so
     for (int b = 0; b < nrhs; ++b) lsq[b].solve(kk, &ybuf[(size_t)b * m]);
     AIM_CUDA_TRY(cudaMemcpyAsync(k.y, ybuf.data(), sizeof(double2) * (size_t)nrhs * m, cudaMemcpyHostToDevice,
                                  c->stream));
-    AIM_LAUNCH(c, "k_xupdate", k_xupdate<<<s.vgrid(), 256, 0, c->stream>>>(k.V, k.y, c->dinv64, X, N, kk, m, m + 1, k.active));
+    AIM_LAUNCH(c, "k_xupdate", k_xupdate<<<s.vgrid(), 256, 0, c->stream>>>(k.V, k.y, c->dinv64, X, N, kk, m, m + 1, k.active,
+                                                                        c->dinv_ld));
     AIM_TRY(s.chk("k_xupdate"));
   }
   bool conv = true;

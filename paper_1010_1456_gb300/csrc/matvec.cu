@@ -842,6 +842,7 @@ int ensure_grids(aim_ctx* c, int precision) {
 }
 
 int prepare_product(aim_ctx* c, int precision) {
+  if (c->pack) return pack_prepare(c, precision);
   AIM_TRY(ensure_grids(c, precision));
   if (precision == AIM_C128) return ensure_ff_arrays(c);
   if (c->max_rhs >= kRhsLanesMin) {
@@ -859,6 +860,7 @@ int prepare_product(aim_ctx* c, int precision) {
 }
 
 int matvec(aim_ctx* c, const void* x, void* y, int nrhs, int precision) {
+  if (c->pack) return pack_matvec(c, x, y, nrhs, precision);
   AIM_TRY(ensure_grids(c, precision));
   if (precision == AIM_C64)
     return run_product<M32, M32>(c, (const float2*)x, (float2*)y, nrhs, c->p32.grid0,

@@ -196,6 +196,51 @@ struct PhaseClock {
   }
 };
 
+// FFT plans (c->plan must hold make_plan of each padded length), the
+// twiddle tables of the three arithmetic policies and the storage of the
+// Green's function spectrum octants (filled by build_ghat).
+int fft_tables(aim_ctx* c) {
+  AIM_TRY(upload((void**)&c->plan_dev, c->plan, sizeof(c->plan)));
+  for (int d = 0; d < 3; ++d) {
+    if (c->plan[d].nst < 0) {
+      set_error("aim_setup: padded length is not 2,3,5-smooth");
+      return AIM_EINVAL;
+    }
+    // w^t for t < L, then (four-step lengths) w^(k1 n2) as [k1][n2] and as [n2][k1]
+    const int L = c->L[d];
+    int L1 = 0, L2 = 0;
+    const bool four = fourstep_split(L, &L1, &L2);
+    std::vector<double> t64(6 * (size_t)L, 0.0);
+    std::vector<float> t32(6 * (size_t)L, 0.f), tff(12 * (size_t)L, 0.f);
+    const auto put = [&](size_t slot, long long t) {
+      const double ang = (2.0 * kPi * (double)(t % L)) / L;
+      t64[2 * slot] = std::cos(ang);
+      t64[2 * slot + 1] = -std::sin(ang);
+      for (int q = 0; q < 2; ++q) {
+        const float hi = (float)t64[2 * slot + q];
+        t32[2 * slot + q] = hi;
+        tff[4 * slot + 2 * q] = hi;
+        tff[4 * slot + 2 * q + 1] = (float)(t64[2 * slot + q] - (double)hi);
+      }
+    };
+    for (int t = 0; t < L; ++t) put(t, t);
+    if (four)
+      for (int k1 = 0; k1 < L1; ++k1)
+        for (int n2 = 0; n2 < L2; ++n2) {
+          put((size_t)L + (size_t)k1 * L2 + n2, (long long)k1 * n2);
+          put(2 * (size_t)L + (size_t)n2 * L1 + k1, (long long)k1 * n2);
+        }
+    AIM_TRY(upload((void**)&c->p64.tw[d], t64.data(), t64.size() * sizeof(double)));
+    AIM_TRY(upload((void**)&c->p32.tw[d], t32.data(), t32.size() * sizeof(float)));
+    AIM_TRY(upload((void**)&c->pff.tw[d], tff.data(), tff.size() * sizeof(float)));
+  }
+  const size_t oct = (size_t)(c->L[0] / 2 + 1) * (c->L[1] / 2 + 1) * (c->L[2] / 2 + 1);
+  AIM_TRY(upload((void**)&c->p64.ghat, nullptr, oct * sizeof(double2)));
+  AIM_TRY(upload((void**)&c->p32.ghat, nullptr, oct * sizeof(float2)));
+  AIM_TRY(upload((void**)&c->pff.ghat, nullptr, oct * sizeof(float4)));
+  return AIM_OK;
+}
+
 int build_context(aim_ctx* c, const aim_mesh* mesh) {
   PhaseClock clk(c->opts.verbose != 0);
   Topo T;
@@ -435,46 +480,10 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
   AIM_CUDA_TRY(cudaStreamSynchronize(c->stream));
   clk.mark("conversions");
   // FFT plans, twiddles and Ghat
-  AIM_TRY(upload((void**)&c->plan_dev, c->plan, sizeof(c->plan)));
-  for (int d = 0; d < 3; ++d) {
-    if (c->plan[d].nst < 0) {
-      set_error("aim_setup: padded length is not 2,3,5-smooth");
-      return AIM_EINVAL;
-    }
-    // w^t for t < L, then (four-step lengths) w^(k1 n2) as [k1][n2] and as [n2][k1]
-    const int L = c->L[d];
-    int L1 = 0, L2 = 0;
-    const bool four = fourstep_split(L, &L1, &L2);
-    std::vector<double> t64(6 * (size_t)L, 0.0);
-    std::vector<float> t32(6 * (size_t)L, 0.f), tff(12 * (size_t)L, 0.f);
-    const auto put = [&](size_t slot, long long t) {
-      const double ang = (2.0 * kPi * (double)(t % L)) / L;
-      t64[2 * slot] = std::cos(ang);
-      t64[2 * slot + 1] = -std::sin(ang);
-      for (int q = 0; q < 2; ++q) {
-        const float hi = (float)t64[2 * slot + q];
-        t32[2 * slot + q] = hi;
-        tff[4 * slot + 2 * q] = hi;
-        tff[4 * slot + 2 * q + 1] = (float)(t64[2 * slot + q] - (double)hi);
-      }
-    };
-    for (int t = 0; t < L; ++t) put(t, t);
-    if (four)
-      for (int k1 = 0; k1 < L1; ++k1)
-        for (int n2 = 0; n2 < L2; ++n2) {
-          put((size_t)L + (size_t)k1 * L2 + n2, (long long)k1 * n2);
-          put(2 * (size_t)L + (size_t)n2 * L1 + k1, (long long)k1 * n2);
-        }
-    AIM_TRY(upload((void**)&c->p64.tw[d], t64.data(), t64.size() * sizeof(double)));
-    AIM_TRY(upload((void**)&c->p32.tw[d], t32.data(), t32.size() * sizeof(float)));
-    AIM_TRY(upload((void**)&c->pff.tw[d], tff.data(), tff.size() * sizeof(float)));
-  }
-  const size_t oct = (size_t)(c->L[0] / 2 + 1) * (c->L[1] / 2 + 1) * (c->L[2] / 2 + 1);
-  AIM_TRY(upload((void**)&c->p64.ghat, nullptr, oct * sizeof(double2)));
-  AIM_TRY(upload((void**)&c->p32.ghat, nullptr, oct * sizeof(float2)));
-  AIM_TRY(upload((void**)&c->pff.ghat, nullptr, oct * sizeof(float4)));
+  AIM_TRY(fft_tables(c));
   clk.mark("twiddles");
   AIM_TRY(build_ghat(c));
+  const size_t oct = (size_t)(c->L[0] / 2 + 1) * (c->L[1] / 2 + 1) * (c->L[2] / 2 + 1);
   c->h_ghat.resize(2 * oct);
   AIM_CUDA_TRY(cudaMemcpyAsync(c->h_ghat.data(), c->p64.ghat, oct * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
   AIM_CUDA_TRY(cudaStreamSynchronize(c->stream));

@@ -142,3 +142,23 @@ def test_non_finite_vertices_and_budget_are_rejected_on_the_host(lib):
         g.aim_setup(v, t, 6.28, 0.1, mem_budget=1000, stream=0)
     assert e.value.code == _lib.AIM_ENOMEM
     assert b"mem_budget" in lib.aim_last_error()
+
+
+def test_pack_arguments_are_checked_on_the_host(lib):
+    """aim_pack_* reject null or out-of-range arguments before touching a device."""
+    import ctypes as C
+
+    from paper_1010_1456_gb300 import _lib
+
+    out = C.c_void_p()
+    nr = (C.c_int32 * 1)(1)
+    hs = (C.c_void_p * 1)(None)
+    assert lib.aim_pack_create(None, 1, nr, C.byref(out)) == _lib.AIM_EINVAL
+    assert lib.aim_pack_create(hs, 0, nr, C.byref(out)) == _lib.AIM_EINVAL
+    assert lib.aim_pack_create(hs, 1, nr, C.byref(out)) == _lib.AIM_EINVAL  # a null context
+    assert lib.aim_pack_create(hs, 257, nr, C.byref(out)) == _lib.AIM_EINVAL
+    assert lib.aim_pack_dims(None, None, None, None) == _lib.AIM_EINVAL
+    assert lib.aim_pack_matvec(None, None, None, _lib.AIM_C64) == _lib.AIM_EINVAL
+    assert lib.aim_pack_solve(None, None, None, 1e-6, None) == _lib.AIM_EINVAL
+    assert lib.aim_pack_set_stream(None, None) == _lib.AIM_EINVAL
+    lib.aim_pack_destroy(None)  # a no-op
