@@ -480,6 +480,51 @@ def serve_summary(requests=24, slots=4):
             "batching": "resident contexts per scatterer; queued same-scatterer requests merged into one solve"}
 
 
+# a catalogue of small scatterers for the multi-instance serving measurement
+PACK_CATALOGUE = ((0.8, 0.9, 1.0, 1.1, 1.2), (0.4, 0.45, 0.5, 0.55, 0.6))
+
+
+def pack_serve_summary(requests=96, slots=2, pack=8):
+    """Many small scatterers: a catalogue of five plates (0.8-1.2 lambda, EFIE)
+    and five spheres (0.4-0.6 lambda, CFIE alpha 0.6), 1..4 RHS per request,
+    contexts resident (built by a warm-up stream), served without and with
+    multi-instance packs: closed-loop capacity (seed 2), then Poisson arrivals
+    (seed 1) at 0.7 x the capacity without packs, the same stream for both."""
+    from paper_1010_1456_gb300 import serve
+
+    plates, spheres = PACK_CATALOGUE
+
+    def stream(seed, rate):
+        return serve.make_stream(requests, rate=rate, seed=seed, plate_sides=plates, sphere_radii=spheres, max_rhs=4,
+                                 sphere_cfie_alpha=0.6)
+
+    servers, cap = {}, {}
+    for name, p in (("without_packs", 1), ("with_packs", pack)):
+        srv = serve.Server(slots=slots, pack=p)
+        srv.run(stream(5, 1.0), realtime=False)  # builds the resident contexts
+        srv.packs = []
+        res, span = srv.run(stream(2, 1.0), realtime=False)
+        cap[name] = (serve.summarize(res, span), list(srv.packs))
+        servers[name] = srv
+    rate = 0.7 * cap["without_packs"][0]["solves_per_s"]
+    out = {"stream": f"plates {plates} lambda (EFIE), spheres {spheres} lambda (CFIE alpha 0.6), 1..4 RHS, "
+                     f"{requests} requests, contexts resident; Poisson seed 1 at {rate:.1f}/s (0.7 x capacity "
+                     f"without packs), {slots} slots, packs of up to {pack} scatterers"}
+    for name, srv in servers.items():
+        srv.packs = []
+        res, span = srv.run(stream(1, rate), realtime=True)
+        summ = serve.summarize(res, span)
+        c, cpacks = cap[name]
+        out[name] = {"capacity_solves_per_s": c["solves_per_s"],
+                     "capacity_scatterers_per_packed_solve": float(np.mean(cpacks)) if cpacks else None,
+                     "solves_per_s": summ["solves_per_s"], "p50_s": summ["p50_s"], "p99_s": summ["p99_s"],
+                     "failed": summ["failed"], "max_rel_res": summ["max_rel_res"],
+                     "mean_requests_per_solve": summ["mean_batch"],
+                     "scatterers_per_packed_solve": float(np.mean(srv.packs)) if srv.packs else None}
+        srv.close()
+    return out
+
+
 # ---------------------------------------------------------------- serving
 SERVE_SIZES = {
     # the stream of the serving configuration: plate sides / sphere radii in wavelengths
@@ -878,6 +923,7 @@ def run_ours(args, rank, world, local_rank):
             c2.close()
             torch.cuda.empty_cache()
     serving = serve_summary() if args.serve_extra else None
+    serving_packs = pack_serve_summary() if args.serve_extra else None
 
     line = {
         "metric": METRIC,
@@ -906,6 +952,7 @@ def run_ours(args, rank, world, local_rank):
         "variants": variants if nrhs == 1 else None,
         "solve": solve,
         "serving": serving,
+        "serving_many_small_scatterers": serving_packs,
         "autotune": tune,
         "cufft_comparison": cufft,
         "kernels": kernels,

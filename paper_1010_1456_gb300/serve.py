@@ -24,6 +24,14 @@ Two batching levels sit on top (``cache=True``, the default):
   own Arnoldi process in the batched GMRES, so a request's result is the one
   it would get alone.
 
+A third level packs different scatterers (``pack`` > 1): a slot that takes a
+request also takes pending requests for other scatterers of the same pack
+class (k, h, M, tolerance, flat or not; see ``pack_class``) whose grid boxes
+are within ``pack_ratio`` of the first one's volume, up to ``pack`` scatterers
+and ``pack_rhs`` right-hand sides, and solves them as one multi-instance pack
+(``aim_pack_create`` / ``aim_pack_solve``): every product stage is one launch
+for all of them, and each right-hand side keeps its own Arnoldi process.
+
 The request/response path is the library's C ABI only; no step of a solve
 runs in Python.
 """
@@ -37,7 +45,10 @@ import numpy as np
 
 from . import (
     AIM_C64,
+    AIMError,
     aim_footprint,
+    aim_pack_create,
+    aim_pack_solve,
     aim_rcs,
     aim_rhs_planewave,
     aim_set_stream,
@@ -94,9 +105,25 @@ def scatterer_key(req):
             float(req.tol))
 
 
+def pack_class(req):
+    """Requests whose contexts can share a pack: equal k, h, M and tolerance, and
+    the same grid layout (a mesh flat in z gets the planar grid)."""
+    flat = bool(np.ptp(np.asarray(req.verts)[:, 2]) == 0.0)
+    return (float(req.k), float(req.h), int(req.M), float(req.tol), flat)
+
+
+def box_volume(req):
+    """Nodes of the request's grid box, estimated from the mesh's bounding box."""
+    v = np.asarray(req.verts)
+    n = np.floor(np.ptp(v, axis=0) / req.h) + req.M + 2
+    if np.ptp(v[:, 2]) == 0.0:
+        n[2] = 1
+    return float(np.prod(n))
+
+
 class Server:
     def __init__(self, slots=4, mem_budget=None, device=0, precision=AIM_C64, max_skip=8, cache=True,
-                 merge_rhs=16):
+                 merge_rhs=16, pack=1, pack_rhs=64, pack_ratio=4.0):
         import torch
 
         self.torch = torch
@@ -113,6 +140,10 @@ class Server:
         self.max_skip = max_skip
         self.cache = cache
         self.merge_rhs = int(merge_rhs)
+        self.pack = int(pack) if cache else 1  # packs are built from resident contexts
+        self.pack_rhs = int(pack_rhs)
+        self.pack_ratio = float(pack_ratio)
+        self.packs = []  # scatterers per packed solve
         self.claimed = 0  # footprints of running uncached requests and of every resident context
         self.lock = threading.Condition()
         self.pending = []  # admitted-not-yet requests, arrival order: (req, footprint, key)
@@ -168,8 +199,52 @@ class Server:
                     else:
                         ent["busy"] = True
                         ent["used"] = time.perf_counter()
+                    if self.pack > 1:
+                        need += self._pack_more(req, key, batch, need)
                 return batch, need
         return None
+
+    def _pack_more(self, req, key, batch, need):
+        """Add to `batch` the pending requests of other scatterers that can share
+        its pack (each with its same-scatterer followers); returns the footprint
+        their new contexts add to the claim (under the lock)."""
+        cls, vol = pack_class(req), box_volume(req)
+        keys = {key}
+        tot = sum(len(r.khat) for r in batch)
+        extra = 0
+        j = 0
+        while j < len(self.pending) and len(keys) < self.pack:
+            r2, fp2, k2 = self.pending[j]
+            ent2 = self.contexts.get(k2)
+            v2 = box_volume(r2)
+            fits = (k2 not in keys and pack_class(r2) == cls and max(v2, vol) <= self.pack_ratio * min(v2, vol)
+                    and tot + len(r2.khat) <= self.pack_rhs and not (ent2 is not None and ent2["busy"]))
+            need2 = 0 if ent2 is not None else fp2
+            if not fits or (need2 and self.claimed + need + extra + need2 > self.budget):
+                j += 1
+                continue
+            self.pending.pop(j)
+            group = [r2]
+            ntot = len(r2.khat)
+            i = j
+            while i < len(self.pending):  # its own followers, as for the first scatterer
+                r3, _fp3, k3 = self.pending[i]
+                if k3 == k2 and ntot + len(r3.khat) <= self.merge_rhs and tot + ntot + len(r3.khat) <= self.pack_rhs:
+                    group.append(r3)
+                    ntot += len(r3.khat)
+                    self.pending.pop(i)
+                else:
+                    i += 1
+            batch.extend(group)
+            tot += ntot
+            keys.add(k2)
+            extra += need2
+            if ent2 is None:
+                self.contexts[k2] = {"ctx": None, "fp": fp2, "busy": True, "used": time.perf_counter()}
+            else:
+                ent2["busy"] = True
+                ent2["used"] = time.perf_counter()
+        return extra
 
     def _make_stream(self):
         torch = self.torch
@@ -199,14 +274,14 @@ class Server:
                 if not self.cache:
                     self.claimed -= claim
                 else:
-                    key = scatterer_key(batch[0])
-                    ent = self.contexts.get(key)
-                    if ent is not None:
-                        ent["busy"] = False
-                        ent["used"] = time.perf_counter()
-                        if ent["ctx"] is None:  # its setup failed: nothing resident
-                            self.claimed -= ent["fp"]
-                            del self.contexts[key]
+                    for key in dict.fromkeys(scatterer_key(r) for r in batch):
+                        ent = self.contexts.get(key)
+                        if ent is not None:
+                            ent["busy"] = False
+                            ent["used"] = time.perf_counter()
+                            if ent["ctx"] is None:  # its setup failed: nothing resident
+                                self.claimed -= ent["fp"]
+                                del self.contexts[key]
                 self.busy -= 1
                 for r in res:
                     self.results[r.rid] = r
@@ -215,6 +290,11 @@ class Server:
     def _solve_batch(self, batch, claim, stream, admitted):
         if not self.cache:
             return [self._run(req, self._footprint(req), stream, admitted) for req in batch]
+        groups = {}
+        for r in batch:
+            groups.setdefault(scatterer_key(r), []).append(r)
+        if len(groups) > 1:
+            return self._run_packed(list(groups.values()), stream, admitted)
         return self._run_merged(batch, stream, admitted)
 
     def _run(self, req, fp, stream, admitted):
@@ -241,29 +321,81 @@ class Server:
             return Result(req.rid, None, None, 0, req.arrival, admitted, time.perf_counter() - self.t0, fp,
                           error=repr(e))
 
+    def _context(self, req0, stream):
+        """The scatterer's resident context, built on first use with room for
+        merge_rhs right-hand sides; returns (ctx, footprint, built)."""
+        key = scatterer_key(req0)
+        with self.lock:
+            ent = self.contexts[key]
+        if ent["ctx"] is None:
+            ctx = aim_setup(req0.verts, req0.tris, req0.k, req0.h, M=req0.M, near_radius=req0.near_radius,
+                            precision=self.precision, max_rhs=max(self.merge_rhs, len(req0.khat)),
+                            stream=stream.cuda_stream, cfie_alpha=req0.cfie_alpha)
+            with self.lock:
+                ent["ctx"] = ctx
+                self.setups += 1
+            return ctx, ent["fp"], True
+        aim_set_stream(ent["ctx"], stream)
+        return ent["ctx"], ent["fp"], False
+
+    def _run_packed(self, groups, stream, admitted):
+        """Several scatterers' groups of requests in one multi-instance pack: one
+        launch per product stage for all of them (aim_pack_solve).  A pack the
+        library refuses (grid layouts that differ after setup) is solved group
+        by group instead."""
+        torch = self.torch
+        nreq = sum(len(grp) for grp in groups)
+        try:
+            with torch.cuda.stream(stream):
+                ctxs, fps, builts = [], [], []
+                for grp in groups:
+                    ctx, fp, built = self._context(grp[0], stream)
+                    ctxs.append(ctx)
+                    fps.append(fp)
+                    builts.append(built)
+                try:
+                    pack = aim_pack_create(ctxs, [sum(len(r.khat) for r in grp) for grp in groups])
+                except AIMError:
+                    return [res for grp in groups for res in self._run_merged(grp, stream, admitted)]
+                try:
+                    Vs = [aim_rhs_planewave(ctx, np.concatenate([r.khat for r in grp]),
+                                            np.concatenate([r.pol for r in grp])) for ctx, grp in zip(ctxs, groups)]
+                    X, info = aim_pack_solve(pack, pack.pack(Vs), groups[0][0].tol, raise_on_noconv=False)
+                    parts = pack.unpack(X)
+                    with self.lock:
+                        self.packs.append(len(groups))
+                    out = []
+                    for i, grp in enumerate(groups):
+                        Xi = parts[i]
+                        Xh = Xi.cpu().numpy()
+                        r0, b0 = pack.b0[i], 0
+                        for r in grp:
+                            nb = len(r.khat)
+                            sigma = None
+                            if r.rcs_dirs is not None:
+                                sigma = aim_rcs(ctxs[i], Xi[b0 : b0 + nb].contiguous(), *r.rcs_dirs)[0]
+                            out.append(Result(r.rid, Xh[b0 : b0 + nb], info["rel_res"][r0 + b0 : r0 + b0 + nb],
+                                              info["iterations"], r.arrival, admitted, time.perf_counter() - self.t0,
+                                              fps[i], sigma, batch=nreq, setup=builts[i] and r is grp[0]))
+                            b0 += nb
+                    return out
+                finally:
+                    pack.close()
+        except Exception as e:  # reported per request; the server keeps running
+            now = time.perf_counter() - self.t0
+            return [Result(r.rid, None, None, 0, r.arrival, admitted, now, 0, error=repr(e), batch=nreq)
+                    for grp in groups for r in grp]
+
     def _run_merged(self, batch, stream, admitted):
         """The batch's right-hand sides in one solve on the scatterer's resident
         context (built here on first use, with room for merge_rhs right-hand sides)."""
         torch = self.torch
         req0 = batch[0]
-        key = scatterer_key(req0)
-        with self.lock:
-            ent = self.contexts[key]
-        fp = ent["fp"]
+        fp = 0
         built = False
         try:
             with torch.cuda.stream(stream):
-                if ent["ctx"] is None:
-                    ctx = aim_setup(req0.verts, req0.tris, req0.k, req0.h, M=req0.M, near_radius=req0.near_radius,
-                                    precision=self.precision, max_rhs=max(self.merge_rhs, len(req0.khat)),
-                                    stream=stream.cuda_stream, cfie_alpha=req0.cfie_alpha)
-                    with self.lock:
-                        ent["ctx"] = ctx
-                        self.setups += 1
-                    built = True
-                else:
-                    ctx = ent["ctx"]
-                    aim_set_stream(ctx, stream)
+                ctx, fp, built = self._context(req0, stream)
                 kh = np.concatenate([r.khat for r in batch])
                 po = np.concatenate([r.pol for r in batch])
                 V = aim_rhs_planewave(ctx, kh, po)
@@ -344,14 +476,17 @@ def summarize(results, makespan):
 
 
 def make_stream(n_requests, rate, seed=1, plate_sides=(2, 4, 8, 16, 32), sphere_radii=(1, 2, 4, 8), max_rhs=16,
-                theta_max_deg=80.0, sphere_cfie_alpha=1.0):
+                theta_max_deg=80.0, sphere_cfie_alpha=1.0, size_jitter=0.0):
     """Synthetic request stream: Poisson arrivals at ``rate`` per second.
 
     Draw order per request: inter-arrival time, kind (plate or sphere, 50/50),
     size, number of right-hand sides (uniform 1..max_rhs), then the incidence
     angles and polarisations (``aim_inputs.random_incidence``).  Spheres are
     solved with CFIE when ``sphere_cfie_alpha`` < 1 (Section 2.2 uses 0.6 for
-    closed bodies); plates are open and always take the EFIE.
+    closed bodies); plates are open and always take the EFIE.  With
+    ``size_jitter`` > 0 each size is scaled by a factor drawn uniformly from
+    [1 - size_jitter, 1 + size_jitter] (after the number of right-hand sides)
+    and rounded to 0.01, so nearly every request is a scatterer of its own.
     """
     from aim_inputs import icosphere_frequency, icosphere_mesh, plate_mesh, random_incidence
 
@@ -364,6 +499,8 @@ def make_stream(n_requests, rate, seed=1, plate_sides=(2, 4, 8, 16, 32), sphere_
         plate = rng.uniform() < 0.5
         size = float(rng.choice(plate_sides if plate else sphere_radii))
         nrhs = int(rng.integers(1, max_rhs + 1))
+        if size_jitter > 0:
+            size = round(size * float(rng.uniform(1.0 - size_jitter, 1.0 + size_jitter)), 2)
         ndir = (nrhs + 1) // 2
         kh, po = random_incidence(ndir, theta_max_deg=theta_max_deg, rng=rng)
         kh, po = kh[:nrhs], po[:nrhs]

@@ -103,3 +103,31 @@ def test_resident_contexts_and_merged_solves_match_alone():
         assert np.linalg.norm(a - m.X) <= 1e-4 * np.linalg.norm(a), r.rid
         assert _true_residual(r, m.X) <= 1.01e-6
     s.close()
+
+
+def test_packed_solves_of_different_scatterers_match_alone():
+    """Five scatterers of two pack classes (three flat plates, two CFIE spheres),
+    all queued at once on one slot with packs of up to four: the plates share a
+    pack, the spheres another; every result meets the tolerance and matches its
+    solve alone."""
+    meshes = [(plate_mesh(1.0, 9), 1.0), (plate_mesh(1.1, 10), 1.0), (icosphere_mesh(0.4, icosphere_frequency(0.4)), 0.6),
+              (plate_mesh(0.9, 8), 1.0), (icosphere_mesh(0.45, icosphere_frequency(0.45)), 0.6)]
+    rng = np.random.default_rng(12)
+    reqs = []
+    for i, ((v, t), alpha) in enumerate(meshes):
+        nrhs = int(rng.integers(1, 4))
+        kh, po = random_incidence((nrhs + 1) // 2, rng=rng)
+        reqs.append(serve.Request(i, v, t, kh[:nrhs], po[:nrhs], cfie_alpha=alpha))
+    s = serve.Server(slots=1, pack=4)
+    res, span = s.run(reqs, realtime=False)
+    summ = serve.summarize(res, span)
+    assert summ["failed"] == 0, [r.error for r in res]
+    assert s.packs and max(s.packs) >= 2  # some solve carried several scatterers
+    for r in reqs:
+        m = res[r.rid]
+        assert m.rel_res.max() <= 1e-6
+        alone, _ = serve.Server(slots=1, cache=False).run([r], realtime=False)
+        a = alone[0].X
+        assert np.linalg.norm(a - m.X) <= 1e-4 * np.linalg.norm(a), r.rid
+        assert _true_residual(r, m.X) <= 1.01e-6
+    s.close()

@@ -192,3 +192,86 @@ def test_busy_context_makes_its_requests_wait_not_duplicate():
     res, _ = s.run(reqs, realtime=True)
     assert all(r.error is None for r in res)
     assert s.setups == 1
+
+
+class FakePackingServer(serve.Server):
+    """Packs with the solves replaced by a sleep: records the scatterers of each solve."""
+
+    def __init__(self, footprints, duration=0.02, **kw):
+        super().__init__(**kw)
+        self.fps = footprints
+        self.duration = duration
+        self.solves = []
+
+    def _make_stream(self):
+        return None
+
+    def _footprint(self, req):
+        return self.fps[req.rid]
+
+    def _finish(self, groups, admitted):
+        with self.lock:
+            for grp in groups:
+                ent = self.contexts[serve.scatterer_key(grp[0])]
+                if ent["ctx"] is None:
+                    ent["ctx"] = _FakeCtx()
+                    self.setups += 1
+        self.solves.append([[r.rid for r in grp] for grp in groups])
+        time.sleep(self.duration)
+        now = time.perf_counter() - self.t0
+        n = sum(len(grp) for grp in groups)
+        return [serve.Result(r.rid, np.zeros((len(r.khat), 1)), np.zeros(len(r.khat)), 1, r.arrival, admitted, now, 1,
+                             batch=n) for grp in groups for r in grp]
+
+    def _run_packed(self, groups, stream, admitted):
+        return self._finish(groups, admitted)
+
+    def _run_merged(self, batch, stream, admitted):
+        return self._finish([batch], admitted)
+
+
+def shaped_reqs(shapes, nrhs=1):
+    """One request per (name, extent x, extent y, extent z): equal names share a mesh."""
+    meshes, out = {}, []
+    for i, (name, ex, ey, ez) in enumerate(shapes):
+        if name not in meshes:
+            v = np.array([[0.0, 0.0, 0.0], [ex, 0.0, 0.0], [0.0, ey, ez]])
+            meshes[name] = (v, np.array([[0, 1, 2]], dtype=np.int32))
+        v, t = meshes[name]
+        out.append(serve.Request(i, v, t, np.zeros((nrhs, 3)), np.zeros((nrhs, 3)), label=name))
+    return out
+
+
+def test_pack_takes_other_scatterers_of_its_class():
+    """One slot, pack of up to 3: three flat scatterers of similar size share the
+    first solve; the curved one (another grid layout), the much larger flat one
+    (box volume beyond the ratio) and the fourth flat one (pack full) wait."""
+    reqs = shaped_reqs([("a", 1.0, 1.0, 0.0), ("b", 1.1, 0.9, 0.0), ("s", 0.5, 0.5, 0.5), ("c", 1.2, 1.0, 0.0),
+                        ("big", 6.0, 6.0, 0.0), ("d", 1.0, 1.1, 0.0)])
+    s = FakePackingServer([10] * 6, slots=1, mem_budget=1000, pack=3, pack_ratio=4.0)
+    res, _ = s.run(reqs, realtime=False)
+    assert all(r.error is None for r in res)
+    assert s.solves[0] == [[0], [1], [3]]
+    assert sorted(sum(s.solves[1:], []), key=lambda g: g[0]) == [[2], [4], [5]]
+    assert s.setups == 6
+
+
+def test_pack_respects_budget_and_rhs_limit():
+    """A scatterer whose new context would exceed the budget, or whose right-hand
+    sides would exceed pack_rhs, is left for a later solve."""
+    reqs = shaped_reqs([("a", 1.0, 1.0, 0.0), ("b", 1.01, 1.0, 0.0), ("c", 1.02, 1.0, 0.0),
+                        ("d", 1.03, 1.0, 0.0)], nrhs=3)
+    s = FakePackingServer([40, 70, 40, 10], slots=1, mem_budget=100, pack=4, pack_rhs=6)
+    res, _ = s.run(reqs, realtime=False)
+    assert all(r.error is None for r in res)
+    # b does not fit beside a (40 + 70 > 100); c does (80), and a + c fill pack_rhs = 6
+    assert s.solves[0] == [[0], [2]]
+    assert [[1], [3]] in s.solves[1:] or [[1]] in s.solves[1:]
+    assert s.peak_claimed <= 100
+
+
+def test_pack_of_one_scatterer_is_a_merged_solve():
+    reqs = shaped_reqs([("a", 1.0, 1.0, 0.0), ("a", 1.0, 1.0, 0.0)])
+    s = FakePackingServer([10, 10], slots=1, mem_budget=100, pack=4)
+    res, _ = s.run(reqs, realtime=False)
+    assert s.solves == [[[0, 1]]]
