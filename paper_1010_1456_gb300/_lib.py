@@ -8,7 +8,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libaim.so")
+# AIM_LIBRARY selects another build of the library in this tree, e.g. the
+# index-checking debug build libaim_check.so (build.py --check)
+LIB_PATH = os.path.join(HERE, os.environ.get("AIM_LIBRARY", "libaim.so"))
 
 AIM_OK, AIM_EINVAL, AIM_ENOMEM, AIM_ECUDA, AIM_ENOCONV, AIM_ETIMEOUT, AIM_ENODEV = range(7)
 AIM_C64, AIM_C128, AIM_C128_F64 = 1, 2, 3

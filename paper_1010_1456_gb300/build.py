@@ -2,7 +2,7 @@
 
 Each translation unit is compiled by nvcc in parallel, then linked into one
 shared object next to this file.  No cmake, no torch extension machinery.
-Usage: ``python -m paper_1010_1456_gb300.build`` (or ``build()``).
+Usage: ``python -m paper_1010_1456_gb300.build [--force] [--check]`` (or ``build()``).
 """
 
 import concurrent.futures as cf
@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaim.so")
+LIB_CHECK = os.path.join(HERE, "libaim_check.so")
 SOURCES = ["api.cu", "setup.cu", "setup_dev.cu", "fft.cu", "matvec.cu", "krylov.cu", "rcs.cu", "rcs_ref.cu", "probe.cu", "profile.cu", "noalloc.cu", "autotune.cu", "nearfill.cu", "pack.cu", "fft4_p32.cu",
            "fft4_p64.cu", "fft4_pff.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -44,18 +45,23 @@ def _newer(src_list, target):
     return any(os.path.getmtime(s) > t for s in src_list)
 
 
-def build(verbose=False, force=False):
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(verbose=False, force=False, check=False):
+    """Compile the library (check=True: the index-checking debug build
+    ``libaim_check.so``, compiled with -DAIM_CHECK into its own object folder)."""
+    out_dir = OUT_DIR + ("_check" if check else "")
+    lib = LIB_CHECK if check else LIB
+    flags = FLAGS + (["-DAIM_CHECK"] if check else [])
+    os.makedirs(out_dir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "aim.h"))
     objs = []
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        o = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _newer([s] + headers, o):
-            jobs.append([nvcc(), *ARCH, *FLAGS, "-c", s, "-o", o])
+            jobs.append([nvcc(), *ARCH, *flags, "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -66,10 +72,10 @@ def build(verbose=False, force=False):
 
     with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4) or 1) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _newer(objs, LIB):
-        run([nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lpthread"])
-    return LIB
+    if force or jobs or _newer(objs, lib):
+        run([nvcc(), *ARCH, "-shared", "-o", lib, *objs, "-lpthread"])
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, force="--force" in sys.argv))
+    print(build(verbose=True, force="--force" in sys.argv, check="--check" in sys.argv))

@@ -36,6 +36,46 @@ struct Status {
     if (_c != AIM_OK) return _c;   \
   } while (0)
 
+// ---------------------------------------------------------------- debug index checks
+// Built with -DAIM_CHECK (build.py check=True, libaim_check.so), the product
+// kernels test the indices they gather through before using them: every
+// projection entry's basis function and every near column must lie in
+// [0, N), and every stencil (its first node plus M along each axis) inside the
+// grid.  A failed test skips the entries or the stencil in question and
+// records the first failure (site, index) in the translation unit's own copy
+// of the variables below; the host reads them after every product
+// (read_index_checks), so a check build synchronises per product, and its
+// solver launches the Arnoldi step without a CUDA graph.  Sites: 1 projection
+// entry, 2 stencil, 3 near column (4, 5, 6: the same in the packed kernels).
+#ifdef AIM_CHECK
+static __device__ unsigned int g_check_fails;
+static __device__ long long g_check_first[2];
+__device__ __forceinline__ void index_fail(int site, long long idx) {
+  if (atomicAdd(&g_check_fails, 1u) == 0) {
+    g_check_first[0] = site;
+    g_check_first[1] = idx;
+  }
+}
+// every idx[e], e0 <= e < e1, in [0, n)
+__device__ __forceinline__ bool indices_ok(const int32_t* idx, long long e0, long long e1, long long n, int site) {
+  for (long long e = e0; e < e1; ++e)
+    if (idx[e] < 0 || idx[e] >= n) {
+      index_fail(site, idx[e]);
+      return false;
+    }
+  return true;
+}
+// the stencil of (M+1) nodes per axis (one plane when S = (M+1)^2) from flat
+// node `base` lies inside an nx x ny x (Nc / (nx ny)) grid
+__device__ __forceinline__ bool stencil_ok(long long base, int nx, int ny, long long Nc, int P, int S, int site) {
+  const long long plane = (long long)nx * ny;
+  const bool ok = base >= 0 && base % nx + P - 1 < nx && (base / nx) % ny + P - 1 < ny &&
+                  (base / plane + (S == P * P * P ? P - 1 : 0)) * plane < Nc;
+  if (!ok) index_fail(site, base);
+  return ok;
+}
+#endif
+
 // ---------------------------------------------------------------- complex
 template <typename R> struct cplx_t;
 template <> struct cplx_t<float> { using type = float2; };
@@ -302,6 +342,25 @@ void free_context(aim_ctx* c);
 // pack.cu: products and preparation of a pack's internal context.
 int pack_matvec(aim_ctx* c, const void* x, void* y, int nrhs, int precision);
 int pack_prepare(aim_ctx* c, int precision);
+#ifdef AIM_CHECK
+// The index checks of this translation unit's kernels since the last read:
+// AIM_EINVAL with the first failure (site, index) in aim_last_error, then the
+// count is cleared.  Synchronises the stream.
+[[maybe_unused]] static int read_index_checks(aim_ctx* c, const char* where) {
+  unsigned int n = 0;
+  long long first[2] = {0, 0};
+  AIM_CUDA_TRY(cudaMemcpyFromSymbolAsync(&n, g_check_fails, sizeof(n), 0, cudaMemcpyDeviceToHost, c->stream));
+  AIM_CUDA_TRY(cudaMemcpyFromSymbolAsync(first, g_check_first, sizeof(first), 0, cudaMemcpyDeviceToHost, c->stream));
+  AIM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (n == 0) return AIM_OK;
+  const unsigned int zero = 0;
+  AIM_CUDA_TRY(cudaMemcpyToSymbolAsync(g_check_fails, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, c->stream));
+  AIM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  set_error(std::string(where) + ": index check failed " + std::to_string(n) + " time(s); first at site " +
+            std::to_string(first[0]) + ", index " + std::to_string(first[1]));
+  return AIM_EINVAL;
+}
+#endif
 // rcs.cu
 int rhs_planewave(aim_ctx* c, int nrhs, const double* khat, const double* pol, double2* V);
 int rcs(aim_ctx* c, const double2* X, int nrhs, int ndir, const double* theta, const double* phi,

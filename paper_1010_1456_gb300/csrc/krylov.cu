@@ -397,6 +397,9 @@ struct Solver {
   // The step as a CUDA graph (captured on first use for this precision and
   // batch size), or launched directly while the profiler is on.
   int run_step(int precision, bool allow_graph) {
+#ifdef AIM_CHECK
+    allow_graph = false;  // the check build reads its index checks (a synchronisation) after every product
+#endif
     if (!allow_graph || c->prof.on) return step(precision);
     if (!k.step_exec || k.step_prec != precision || k.step_nrhs != B) {
       if (k.step_exec) {

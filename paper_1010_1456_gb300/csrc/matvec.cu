@@ -109,7 +109,11 @@ __global__ void __launch_bounds__(256) proj_gather(const cplx<typename MD::R>* _
     const long long u0 = tasks.node(t);
     const bool live = u0 < Nc;
     const long long u = live ? u0 : Nc - 1;
-    const int e0 = pe0, e1 = pe1;
+    const int e0 = pe0;
+    int e1 = pe1;
+#ifdef AIM_CHECK
+    if (!indices_ok(mm, e0, e1, N, 1)) e1 = e0;
+#endif
     tasks.bounds(ptr, t + nwarps, &pe0, &pe1);
     if (__all_sync(0xffffffffu, e0 == e1)) {  // the warp's 8 nodes are empty: zeros, no reduction
       if (live)
@@ -189,11 +193,18 @@ __global__ void __launch_bounds__(256) interp_near(const typename MD::S* __restr
   const int b0 = base[mm];
   const R* lm = lam + (long long)mm * 4 * S;
   const R* wm = MF ? lamM + (long long)mm * 3 * S : nullptr;
-  const int r0 = nptr[mm], r1 = nptr[mm + 1];
+  const int r0 = nptr[mm];
+  int r1 = nptr[mm + 1];
+#ifdef AIM_CHECK
+  const int Sc = stencil_ok(b0, nx, ny, Nc, P, S, 2) ? S : 0;
+  if (!indices_ok(ncol, r0, r1, N, 3)) r1 = r0;
+#else
+  const int Sc = S;
+#endif
   for (int b = 0; b < nrhs; ++b) {
     const typename MD::S* Pb = Phi + (long long)b * 4 * Nc;
     C av = cmake<C>(0, 0), ar = av, an = av, am = av;
-    for (int s = lane; s < S; s += 8) {
+    for (int s = lane; s < Sc; s += 8) {
       const long long node = b0 + (long long)s_off[s];
       const C px = MD::get(Pb[node]), py = MD::get(Pb[Nc + node]), pz = MD::get(Pb[2 * Nc + node]),
               pr = MD::get(Pb[3 * Nc + node]);
@@ -309,7 +320,14 @@ __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R
     const int b0 = base[m];
     const R* lm = lam + (long long)m * 4 * S;
     const R* wm = MF ? lamM + (long long)m * 3 * S : nullptr;
-    const int r0 = nptr[m], r1 = nptr[m + 1];
+    const int r0 = nptr[m];
+    int r1 = nptr[m + 1];
+#ifdef AIM_CHECK
+    const int Sc = stencil_ok(b0, nx, ny, Nc, P, S, 2) ? S : 0;
+    if (!indices_ok(ncol, r0, r1, N, 3)) r1 = r0;
+#else
+    const int Sc = S;
+#endif
     const long long cs = Nc * B;  // component stride of PhiT
     for (int bc = 0; bc < B; bc += 32 * RL) {
       const int b = bc + RL * lane;  // B is a multiple of RL
@@ -318,7 +336,7 @@ __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R
 #pragma unroll
         for (int q = 0; q < RL; ++q) av[q] = ar[q] = an[q] = am[q] = cmake<C>(0, 0);
 #pragma unroll 3
-        for (int s = 0; s < S; ++s) {
+        for (int s = 0; s < Sc; ++s) {
           const C* ph = PhiT + (b0 + (long long)s_off[s]) * B + b;
           const Run<C, RL> px = load_run<C, RL>(ph), py = load_run<C, RL>(ph + cs), pz = load_run<C, RL>(ph + 2 * cs),
                            pr = load_run<C, RL>(ph + 3 * cs);
@@ -406,7 +424,7 @@ __global__ void __launch_bounds__(256) proj_gather_rhs(const cplx<typename MD::R
                                                        typename MD::S* __restrict__ Q, const int32_t* __restrict__ ptr,
                                                        const int32_t* __restrict__ mm,
                                                        const typename MD::R* __restrict__ w, long long Nc, int B,
-                                                       int ldx) {
+                                                       int ldx, int N) {
   using R = typename MD::R;
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -417,7 +435,11 @@ __global__ void __launch_bounds__(256) proj_gather_rhs(const cplx<typename MD::R
   for (int i = warp; i < 32; i += 8) {
     const long long u = u0 + i;
     if (u >= Nc) break;
-    const int e0 = ptr[u], e1 = ptr[u + 1];
+    const int e0 = ptr[u];
+    int e1 = ptr[u + 1];
+#ifdef AIM_CHECK
+    if (!indices_ok(mm, e0, e1, N, 1)) e1 = e0;
+#endif
     for (int bc = 0; bc < B; bc += 32 * RL) {
       const int b = bc + RL * lane;  // B is a multiple of RL
       if (b >= B) continue;
@@ -503,7 +525,11 @@ __global__ void __launch_bounds__(256) proj_gather_ff(const float4* __restrict__
     const long long u0 = tasks.node(t);
     const bool live = u0 < Nc;
     const long long u = live ? u0 : Nc - 1;
-    const int e0 = pe0, e1 = pe1;
+    const int e0 = pe0;
+    int e1 = pe1;
+#ifdef AIM_CHECK
+    if (!indices_ok(mm, e0, e1, N, 1)) e1 = e0;
+#endif
     tasks.bounds(ptr, t + nwarps, &pe0, &pe1);
     if (__all_sync(0xffffffffu, e0 == e1)) {  // the warp's 8 nodes are empty: zeros, no reduction
       if (live)
@@ -579,12 +605,19 @@ __global__ void __launch_bounds__(256) interp_near_ff(const float4* __restrict__
   const int b0 = base[mm];
   const float2* lm = lam + (long long)mm * 4 * S;
   const float2* wm = MF ? lamM + (long long)mm * 3 * S : nullptr;
-  const int r0 = nptr[mm], r1 = nptr[mm + 1];
+  const int r0 = nptr[mm];
+  int r1 = nptr[mm + 1];
+#ifdef AIM_CHECK
+  const int Sc = stencil_ok(b0, nx, ny, Nc, P, S, 2) ? S : 0;
+  if (!indices_ok(ncol, r0, r1, N, 3)) r1 = r0;
+#else
+  const int Sc = S;
+#endif
   const ff kv = ffv(fvec.x, fvec.y), kr = ffv(frho.x, frho.y), km = ffv(fmf.x, fmf.y);
   for (int b = 0; b < nrhs; ++b) {
     const float4* Pb = Phi + (long long)b * 4 * Nc;
     ff avr = ffv(0.f, 0.f), avi = avr, arr = avr, ari = avr, anr = avr, ani = avr, amr = avr, ami = avr;
-    for (int s = lane; s < S; s += 8) {
+    for (int s = lane; s < Sc; s += 8) {
       const long long node = b0 + (long long)s_off[s];
       const float4 px = Pb[node], py = Pb[Nc + node], pz = Pb[2 * Nc + node], pr = Pb[3 * Nc + node];
       const float2 wx = lm[s], wy = lm[S + s], wz = lm[2 * S + s], wr = lm[3 * S + s];
@@ -745,11 +778,11 @@ static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename 
       if (nb == 64 && nrhs % 2 == 0)  // two per lane: 16-byte loads need an even row stride
         AIM_LAUNCH(c, "proj_gather", (proj_gather_rhs<MD, 2><<<blocks, 256, sm, c->stream>>>(xs, qd, c->pnode_ptr,
                                                                                             c->pnode_m, pw, Nc, nb,
-                                                                                            nrhs)));
+                                                                                            nrhs, c->N)));
       else
         AIM_LAUNCH(c, "proj_gather", (proj_gather_rhs<MD, 1><<<blocks, 256, sm, c->stream>>>(xs, qd, c->pnode_ptr,
                                                                                             c->pnode_m, pw, Nc, nb,
-                                                                                            nrhs)));
+                                                                                            nrhs, c->N)));
       AIM_TRY(launch_check(c, "proj_gather"));
     }
   } else {
@@ -862,15 +895,21 @@ int prepare_product(aim_ctx* c, int precision) {
 int matvec(aim_ctx* c, const void* x, void* y, int nrhs, int precision) {
   if (c->pack) return pack_matvec(c, x, y, nrhs, precision);
   AIM_TRY(ensure_grids(c, precision));
+  int rc;
   if (precision == AIM_C64)
-    return run_product<M32, M32>(c, (const float2*)x, (float2*)y, nrhs, c->p32.grid0,
-                                 phi_grid(c, c->p32.grid0, c->p32.grid2), c->p32.pnode_w,
-                                 c->p32.lam, c->p32.near_val, fft_convolve_c64);
-  if (precision == AIM_C128_F64)
-    return run_product<M64, M64>(c, (const double2*)x, (double2*)y, nrhs, c->p64.grid0,
-                                 phi_grid(c, c->p64.grid0, c->p64.grid2),
-                                 c->p64.pnode_w, c->p64.lam, c->p64.near_val, fft_convolve_c128);
-  return run_product_ff(c, (const double2*)x, (double2*)y, nrhs);
+    rc = run_product<M32, M32>(c, (const float2*)x, (float2*)y, nrhs, c->p32.grid0,
+                               phi_grid(c, c->p32.grid0, c->p32.grid2), c->p32.pnode_w,
+                               c->p32.lam, c->p32.near_val, fft_convolve_c64);
+  else if (precision == AIM_C128_F64)
+    rc = run_product<M64, M64>(c, (const double2*)x, (double2*)y, nrhs, c->p64.grid0,
+                               phi_grid(c, c->p64.grid0, c->p64.grid2),
+                               c->p64.pnode_w, c->p64.lam, c->p64.near_val, fft_convolve_c128);
+  else
+    rc = run_product_ff(c, (const double2*)x, (double2*)y, nrhs);
+#ifdef AIM_CHECK
+  if (rc == AIM_OK) rc = read_index_checks(c, "product");
+#endif
+  return rc;
 }
 
 __global__ void k_c128_to_c64(const double2* __restrict__ in, float2* __restrict__ out, long long n) {
@@ -931,6 +970,9 @@ int matvec_c64_bufs(aim_ctx* c, const float2* x, float2* y, int nrhs, float2* g0
 
     AIM_TRY(launch_check(c, "interp_near"));
   }
+#ifdef AIM_CHECK
+  AIM_TRY(read_index_checks(c, "product (no allocation)"));
+#endif
   return AIM_OK;
 }
 }  // namespace aim

@@ -91,6 +91,9 @@ __global__ void __launch_bounds__(256) proj_pack(const float2* __restrict__ x, f
         const long long loc = ((long long)uz * d.ny + uy) * d.nx + ux;
         e0 = d.pptr[loc];
         e1 = d.pptr[loc + 1];
+#ifdef AIM_CHECK
+        if (!indices_ok(d.pm, e0, e1, d.N, 4)) e1 = e0;
+#endif
       }
     }
     for (int bc = 0; bc < d.nrhs; bc += 4) {
@@ -158,12 +161,19 @@ __global__ void __launch_bounds__(256) interp_pack(const float2* __restrict__ Ph
     const int bs = d.base[m];
     const float* lm = d.lam + (long long)m * 4 * S;
     const float* wm = d.lamM ? d.lamM + (long long)m * 3 * S : nullptr;
-    const int r0 = d.nptr[m], r1 = d.nptr[m + 1];
+    const int r0 = d.nptr[m];
+    int r1 = d.nptr[m + 1];
+#ifdef AIM_CHECK
+    const int Sc = stencil_ok(bs, nxp, nyp, Ncp, P, S, 5) ? S : 0;
+    if (!indices_ok(d.ncol, r0, r1, d.N, 6)) r1 = r0;
+#else
+    const int Sc = S;
+#endif
     for (int b = 0; b < d.nrhs; ++b) {
       const long long g = d.b0 + b;
       const float2* Pb = Phi + g * 4 * Ncp;
       float2 av = make_float2(0.f, 0.f), ar = av, an = av, am = av;
-      for (int s = lane; s < S; s += 8) {
+      for (int s = lane; s < Sc; s += 8) {
         const long long node = bs + (long long)s_off[s];
         const float2 px = Pb[node], py = Pb[Ncp + node], pz = Pb[2 * Ncp + node], pr = Pb[3 * Ncp + node];
         const float wx = lm[s], wy = lm[S + s], wz = lm[2 * S + s], wr = lm[3 * S + s];
@@ -264,8 +274,12 @@ int pack_matvec(aim_ctx* c, const void* x, void* y, int nrhs, int precision) {
     set_error("pack product: every packed row takes part (nrhs must equal the pack's total)");
     return AIM_EINVAL;
   }
-  if (precision == AIM_C64) return pack_c64(P, (const float2*)x, (float2*)y);
-  return pack_exact(P, (const double2*)x, (double2*)y, precision);
+  if (precision != AIM_C64) return pack_exact(P, (const double2*)x, (double2*)y, precision);
+  AIM_TRY(pack_c64(P, (const float2*)x, (float2*)y));
+#ifdef AIM_CHECK
+  AIM_TRY(read_index_checks(c, "packed product"));
+#endif
+  return AIM_OK;
 }
 
 int pack_prepare(aim_ctx* c, int precision) {
