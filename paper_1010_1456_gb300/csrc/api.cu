@@ -26,7 +26,7 @@ template <typename R> static void free_prec(PrecData<R>& p) {
   cudaFree(p.lam); cudaFree(p.lamM); cudaFree(p.pnode_w); cudaFree(p.ghat); cudaFree(p.near_val);
   for (int d = 0; d < 3; ++d) cudaFree(p.tw[d]);
   cudaFree(p.grid0); cudaFree(p.grid1); cudaFree(p.grid2); cudaFree(p.xbuf); cudaFree(p.ybuf);
-  cudaFree(p.phiT); cudaFree(p.xT);
+  cudaFree(p.phiT); cudaFree(p.xT); cudaFree(p.ngrp_val);
   p = PrecData<R>{};
 }
 
@@ -43,6 +43,7 @@ void free_context(aim_ctx* c) {
   cudaFree(c->plan_dev);
   free_krylov(c);
   profile_free(c);
+  cudaFree(c->ngrp_ptr); cudaFree(c->ngrp_col);
   cudaFree(c->base); cudaFree(c->near_ptr); cudaFree(c->near_col); cudaFree(c->pnode_ptr); cudaFree(c->pnode_m);
   cudaFree(c->diag); cudaFree(c->dinv64); cudaFree(c->d_verts); cudaFree(c->d_tris); cudaFree(c->rwg_tri);
   cudaFree(c->rwg_free); cudaFree(c->rwg_len); cudaFree(c->tri_area); cudaFree(c->tri_nrm); cudaFree(c->pgroups);

@@ -131,6 +131,7 @@ template <typename R> struct PrecData {
   cplx<R>* ybuf = nullptr;        // [B][N]
   cplx<R>* phiT = nullptr;        // [4][nz][ny][nx][B] Phi, RHS-minor (many-RHS interpolation)
   cplx<R>* xT = nullptr;          // [N][B] x, RHS-minor
+  cplx<R>* ngrp_val = nullptr;    // [ngrp_nnz][kNearGroup] near entries per union column of a row group
 };
 
 // Float-float copies of the AIM_C128 path: spectrum, twiddles and grids of
@@ -241,6 +242,12 @@ struct aim_ctx {
   int32_t* near_col = nullptr;    // [nnz]
   int32_t* pnode_ptr = nullptr;   // [Nc+1]
   int32_t* pnode_m = nullptr;     // [nent]
+  // many-RHS near product: rows in groups of kNearGroup consecutive basis
+  // functions, each group's near columns merged (sorted union), built on the
+  // first product with lanes over right-hand sides
+  int32_t* ngrp_ptr = nullptr;    // [ngroups + 1]
+  int32_t* ngrp_col = nullptr;    // [ngrp_nnz]
+  long long ngrp_nnz = 0;
   double2* diag = nullptr;        // [N] diag(Z~) FP64
   double2* dinv64 = nullptr;      // [N] 1/diag
   // RWG geometry on device (for RHS and far field)
@@ -332,6 +339,8 @@ int budget_grids(aim_ctx* c, int precision);
 int prepare_product(aim_ctx* c, int precision);
 // Right-hand sides from which the products run with lanes over them.
 constexpr int kRhsLanesMin = 16;
+// Rows per group of the many-RHS near product.
+constexpr int kNearGroup = 4;
 // Forgets the solver's captured Arnoldi step (after the kernel choice changed).
 void drop_step_graph(aim_ctx* c);
 void free_krylov(aim_ctx* c);

@@ -20,9 +20,12 @@
 
 #include <type_traits>
 
+#include <climits>
+
 #include "common.h"
 #include "ff.h"
 #include "geom.h"
+#include "setup_dev.h"
 
 namespace aim {
 
@@ -412,6 +415,190 @@ __global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R
   }
 }
 
+// ---- row groups of the many-RHS near product ----
+// Group g holds rows m0 = kNearGroup g .. m0 + kNearGroup - 1 (the last one
+// fewer).  Its near columns are the sorted union of the rows' (sorted)
+// columns; for each union column the group stores kNearGroup entries, the
+// rows' own values or zero.  One thread per group walks the rows' lists
+// together (a merge); FILL = false counts the union, FILL = true writes it.
+template <bool FILL, class C>
+__global__ void k_near_groups(const int32_t* __restrict__ nptr, const int32_t* __restrict__ ncol,
+                              const C* __restrict__ nval, int N, long long ngroups, int32_t* __restrict__ cnt_or_ptr,
+                              int32_t* __restrict__ gcol, C* __restrict__ gval) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= ngroups) return;
+  const int m0 = (int)(g * kNearGroup);
+  int p[kNearGroup], e[kNearGroup];
+#pragma unroll
+  for (int r = 0; r < kNearGroup; ++r) {
+    const bool row = m0 + r < N;
+    p[r] = row ? nptr[m0 + r] : 0;
+    e[r] = row ? nptr[m0 + r + 1] : 0;
+  }
+  long long u = FILL ? cnt_or_ptr[g] : 0;
+  for (;;) {
+    int col = INT_MAX;
+#pragma unroll
+    for (int r = 0; r < kNearGroup; ++r)
+      if (p[r] < e[r]) col = min(col, ncol[p[r]]);
+    if (col == INT_MAX) break;
+    if constexpr (FILL) gcol[u] = col;
+#pragma unroll
+    for (int r = 0; r < kNearGroup; ++r) {
+      const bool has = p[r] < e[r] && ncol[p[r]] == col;
+      if constexpr (FILL) gval[u * kNearGroup + r] = has ? nval[p[r]] : cmake<C>(0, 0);
+      if (has) ++p[r];
+    }
+    ++u;
+  }
+  if constexpr (!FILL) cnt_or_ptr[g] = (int32_t)u;
+}
+
+// Interpolation + near correction for many right-hand sides over groups of
+// kNearGroup consecutive basis functions: one warp per group, lanes over
+// right-hand sides (RL consecutive ones per lane) on RHS-minor Phi and x.
+// The grid part runs row by row as in interp_near_rhs; the near part walks
+// the group's union of columns, so each x run is gathered once per group
+// rather than once per row that holds the column (neighbouring basis
+// functions share most of their near zone), at the price of multiplying the
+// zeros of the rows that lack a column.  The block's 32 rows of y are staged
+// in shared memory and written back in the [B][N] layout.
+template <class MI, int RL, bool MF>
+__global__ void __launch_bounds__(256) interp_near_grp(const cplx<typename MI::R>* __restrict__ PhiT,
+                                                       const cplx<typename MI::R>* __restrict__ xT,
+                                                       cplx<typename MI::R>* __restrict__ y,
+                                                       const typename MI::R* __restrict__ lam,
+                                                       const int32_t* __restrict__ base,
+                                                       const int32_t* __restrict__ gptr,
+                                                       const int32_t* __restrict__ gcol,
+                                                       const cplx<typename MI::R>* __restrict__ gval, int N,
+                                                       long long Nc, int nx, int ny, int B, typename MI::R fvec,
+                                                       typename MI::R frho, int S, int P,
+                                                       const typename MI::R* __restrict__ lamM, typename MI::R fmf) {
+  using R = typename MI::R;
+  using C = cplx<R>;
+  constexpr int G = kNearGroup;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* ys = reinterpret_cast<C*>(smem_raw);  // [8 G][B]
+  __shared__ int s_off[kMaxStencil];
+  stencil_offsets_smem(s_off, S, P, nx, ny);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long g = blockIdx.x * 8LL + warp;
+  const int m0 = (int)(g * G);
+  if (m0 < N) {
+    const int nr = min(G, N - m0);
+    const int u0 = gptr[g];
+    int u1 = gptr[g + 1];
+#ifdef AIM_CHECK
+    if (!indices_ok(gcol, u0, u1, N, 3)) u1 = u0;
+#endif
+    const long long cs = Nc * B;  // component stride of PhiT
+    for (int bc = 0; bc < B; bc += 32 * RL) {
+      const int b = bc + RL * lane;  // B is a multiple of RL
+      if (b >= B) continue;
+      C acc[G][RL];
+#pragma unroll
+      for (int r = 0; r < G; ++r)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) acc[r][q] = cmake<C>(0, 0);
+      // grid part, row by row: j (fvec av - frho ar) - fmf am
+#pragma unroll
+      for (int r = 0; r < G; ++r) {
+        if (r >= nr) break;
+        const int m = m0 + r;
+        const int b0 = base[m];
+#ifdef AIM_CHECK
+        const int Sc = stencil_ok(b0, nx, ny, Nc, P, S, 2) ? S : 0;
+#else
+        const int Sc = S;
+#endif
+        const R* lm = lam + (long long)m * 4 * S;
+        const R* wm = MF ? lamM + (long long)m * 3 * S : nullptr;
+        C av[RL], ar[RL], am[RL];
+#pragma unroll
+        for (int q = 0; q < RL; ++q) av[q] = ar[q] = am[q] = cmake<C>(0, 0);
+#pragma unroll 3
+        for (int s = 0; s < Sc; ++s) {
+          const C* ph = PhiT + (b0 + (long long)s_off[s]) * B + b;
+          const Run<C, RL> px = load_run<C, RL>(ph), py = load_run<C, RL>(ph + cs), pz = load_run<C, RL>(ph + 2 * cs),
+                           pr = load_run<C, RL>(ph + 3 * cs);
+          const R wx = lm[s], wy = lm[S + s], wz = lm[2 * S + s], wr = lm[3 * S + s];
+#pragma unroll
+          for (int q = 0; q < RL; ++q) {
+            av[q].x += wx * px.v[q].x + wy * py.v[q].x + wz * pz.v[q].x;
+            av[q].y += wx * px.v[q].y + wy * py.v[q].y + wz * pz.v[q].y;
+            ar[q].x += wr * pr.v[q].x;
+            ar[q].y += wr * pr.v[q].y;
+          }
+          if constexpr (MF) {
+            const R mx = wm[s], my = wm[S + s], mz = wm[2 * S + s];
+#pragma unroll
+            for (int q = 0; q < RL; ++q) {
+              am[q].x += mx * px.v[q].x + my * py.v[q].x + mz * pz.v[q].x;
+              am[q].y += mx * px.v[q].y + my * py.v[q].y + mz * pz.v[q].y;
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+          const R tx = fvec * av[q].x - frho * ar[q].x, ty = fvec * av[q].y - frho * ar[q].y;
+          acc[r][q].x = -ty;
+          acc[r][q].y = tx;
+          if constexpr (MF) {
+            acc[r][q].x -= fmf * am[q].x;
+            acc[r][q].y -= fmf * am[q].y;
+          }
+        }
+      }
+      // near part over the group's union of columns, EB columns in flight
+      constexpr int EB = 4;
+      int u = u0;
+      for (; u + EB <= u1; u += EB) {
+        int col[EB];
+#pragma unroll
+        for (int i = 0; i < EB; ++i) col[i] = gcol[u + i];
+        Run<C, RL> xv[EB];
+#pragma unroll
+        for (int i = 0; i < EB; ++i) xv[i] = load_run<C, RL>(xT + (long long)col[i] * B + b);
+#pragma unroll
+        for (int i = 0; i < EB; ++i)
+#pragma unroll
+          for (int r = 0; r < G; ++r) {
+            const C v = gval[(long long)(u + i) * G + r];
+#pragma unroll
+            for (int q = 0; q < RL; ++q) {
+              acc[r][q].x += v.x * xv[i].v[q].x - v.y * xv[i].v[q].y;
+              acc[r][q].y += v.x * xv[i].v[q].y + v.y * xv[i].v[q].x;
+            }
+          }
+      }
+      for (; u < u1; ++u) {
+        const Run<C, RL> xv = load_run<C, RL>(xT + (long long)gcol[u] * B + b);
+#pragma unroll
+        for (int r = 0; r < G; ++r) {
+          const C v = gval[(long long)u * G + r];
+#pragma unroll
+          for (int q = 0; q < RL; ++q) {
+            acc[r][q].x += v.x * xv.v[q].x - v.y * xv.v[q].y;
+            acc[r][q].y += v.x * xv.v[q].y + v.y * xv.v[q].x;
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < G; ++r)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) ys[(warp * G + r) * B + b + q] = acc[r][q];
+    }
+  }
+  __syncthreads();
+  const long long mb = blockIdx.x * 8LL * G;
+  const int rows = (int)min(8LL * G, (long long)N - mb);
+  for (int t = threadIdx.x; t < 8 * G * B; t += blockDim.x) {
+    const int i = t % (8 * G), bb = t / (8 * G);
+    if (i < rows) y[(long long)bb * N + mb + i] = ys[i * B + bb];
+  }
+}
+
 // Projection for many right-hand sides: one warp per grid node, lanes over
 // right-hand sides (RL consecutive ones per lane) on the RHS-minor x, so each
 // entry's x values are one contiguous run; the entry's four weights are
@@ -744,6 +931,35 @@ template <typename R> PrecData<R>& prec_data(aim_ctx* c);
 template <> PrecData<float>& prec_data<float>(aim_ctx* c) { return c->p32; }
 template <> PrecData<double>& prec_data<double>(aim_ctx* c) { return c->p64; }
 
+// The row groups of the many-RHS near product: the union columns once, the
+// entries of a precision on its first use.
+template <typename R>
+static int ensure_near_groups(aim_ctx* c, PrecData<R>& pd) {
+  const long long ng = ((long long)c->N + kNearGroup - 1) / kNearGroup;
+  const unsigned blocks = (unsigned)((ng + 255) / 256);
+  if (!c->ngrp_ptr) {
+    AIM_CUDA_TRY(cudaMalloc(&c->ngrp_ptr, sizeof(int32_t) * (ng + 1)));
+    AIM_LAUNCH(c, "near_groups", (k_near_groups<false, cplx<R>><<<blocks, 256, 0, c->stream>>>(
+                                     c->near_ptr, c->near_col, nullptr, c->N, ng, c->ngrp_ptr, nullptr, nullptr)));
+    AIM_TRY(launch_check(c, "near_groups"));
+    long long total = 0;
+    AIM_TRY(scan_exclusive(c, c->ngrp_ptr, ng, &total));
+    const int32_t t32 = (int32_t)total;
+    AIM_CUDA_TRY(cudaMemcpyAsync(c->ngrp_ptr + ng, &t32, sizeof(t32), cudaMemcpyHostToDevice, c->stream));
+    AIM_CUDA_TRY(cudaMalloc(&c->ngrp_col, sizeof(int32_t) * std::max(1LL, total)));
+    AIM_CUDA_TRY(cudaStreamSynchronize(c->stream));  // t32 is read by the copy
+    c->ngrp_nnz = total;
+  }
+  if (!pd.ngrp_val) {
+    AIM_CUDA_TRY(cudaMalloc(&pd.ngrp_val, sizeof(cplx<R>) * std::max(1LL, c->ngrp_nnz) * kNearGroup));
+    AIM_LAUNCH(c, "near_groups", (k_near_groups<true, cplx<R>><<<blocks, 256, 0, c->stream>>>(
+                                     c->near_ptr, c->near_col, pd.near_val, c->N, ng, c->ngrp_ptr, c->ngrp_col,
+                                     pd.ngrp_val)));
+    AIM_TRY(launch_check(c, "near_groups"));
+  }
+  return AIM_OK;
+}
+
 // MD: storage of the projected grid; MI: storage of Phi read by the interpolation.
 template <class MD, class MI>
 static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename MD::R>* y, int nrhs,
@@ -801,24 +1017,30 @@ static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename 
   AIM_TRY(convolve(c, 4 * nrhs));
   if (many) {
     AIM_TRY(transpose(c, "transpose_phi", reinterpret_cast<const cplx<R>*>(phi), pd.phiT, nrhs, 4 * Nc));
-    const int blocks = (c->N + 7) / 8;
-    const size_t sm = sizeof(cplx<R>) * 8 * nrhs;
+    AIM_TRY(ensure_near_groups(c, pd));
+    const int blocks = (int)((c->N + 8 * kNearGroup - 1) / (8 * kNearGroup));
+    const size_t sm = sizeof(cplx<R>) * 8 * kNearGroup * nrhs;
     const R fvec = (R)(c->alpha * c->k * kEta0), frho = (R)(c->alpha * kEta0 / c->k),
             fmf = (R)((1.0 - c->alpha) * kEta0);
-    const auto go = [&](auto mf) {
-    if (two)
+    const auto go = [&](auto mf, auto rl) {
+      constexpr bool MF = decltype(mf)::value;
+      constexpr int RL = decltype(rl)::value;
+      // staged rows: at most 32 x 256 complex128 (128 KB), beside the stencil offsets
+      static const cudaError_t attr = cudaFuncSetAttribute(interp_near_grp<MI, RL, MF>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      AIM_CUDA_TRY(attr);
       AIM_LAUNCH(c, "interp_near",
-             (interp_near_rhs<MI, 2, decltype(mf)::value><<<blocks, 256, sm, c->stream>>>(pd.phiT, pd.xT, y, lam, c->base,
-                                                                          c->near_ptr, c->near_col, nval, c->N, Nc,
-                                                                          c->n[0], c->n[1], nrhs, fvec, frho, c->S, c->M + 1, pd.lamM, fmf)));
-    else
-      AIM_LAUNCH(c, "interp_near",
-             (interp_near_rhs<MI, 1, decltype(mf)::value><<<blocks, 256, sm, c->stream>>>(pd.phiT, pd.xT, y, lam, c->base,
-                                                                          c->near_ptr, c->near_col, nval, c->N, Nc,
-                                                                          c->n[0], c->n[1], nrhs, fvec, frho, c->S, c->M + 1, pd.lamM, fmf)));
+                 (interp_near_grp<MI, RL, MF><<<blocks, 256, sm, c->stream>>>(
+                     pd.phiT, pd.xT, y, lam, c->base, c->ngrp_ptr, c->ngrp_col, pd.ngrp_val, c->N, Nc, c->n[0],
+                     c->n[1], nrhs, fvec, frho, c->S, c->M + 1, pd.lamM, fmf)));
+      return AIM_OK;
     };
-    if (pd.lamM) go(std::true_type{}); else go(std::false_type{});
-
+    using T2 = std::integral_constant<int, 2>;
+    using T1 = std::integral_constant<int, 1>;
+    if (pd.lamM)
+      AIM_TRY(two ? go(std::true_type{}, T2{}) : go(std::true_type{}, T1{}));
+    else
+      AIM_TRY(two ? go(std::false_type{}, T2{}) : go(std::false_type{}, T1{}));
     return launch_check(c, "interp_near");
   }
   {
@@ -888,6 +1110,8 @@ int prepare_product(aim_ctx* c, int precision) {
       AIM_CUDA_TRY(cudaMalloc(&c->p64.phiT, sizeof(double2) * c->max_rhs * 4 * Nc));
       AIM_CUDA_TRY(cudaMalloc(&c->p64.xT, sizeof(double2) * c->max_rhs * c->N));
     }
+    if (precision == AIM_C64) AIM_TRY(ensure_near_groups(c, c->p32));
+    if (precision == AIM_C128_F64) AIM_TRY(ensure_near_groups(c, c->p64));
   }
   return AIM_OK;
 }
