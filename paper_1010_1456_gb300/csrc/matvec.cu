@@ -293,128 +293,6 @@ template <class C, int RL> __device__ __forceinline__ Run<C, RL> load_run(const 
   return r;
 }
 
-// Interpolation + near correction for many right-hand sides: one warp per
-// basis function, lanes over right-hand sides (RL consecutive ones per lane),
-// with Phi and x in RHS-minor layout so every grid value and every near-zone
-// x value a warp reads is one contiguous run of right-hand sides; the weights
-// and near entries are warp-uniform.  The block's 8 rows of y are staged in
-// shared memory and written back in the [B][N] layout.
-template <class MI, int RL, bool MF>
-__global__ void __launch_bounds__(256) interp_near_rhs(const cplx<typename MI::R>* __restrict__ PhiT,
-                                                       const cplx<typename MI::R>* __restrict__ xT,
-                                                       cplx<typename MI::R>* __restrict__ y,
-                                                       const typename MI::R* __restrict__ lam,
-                                                       const int32_t* __restrict__ base,
-                                                       const int32_t* __restrict__ nptr,
-                                                       const int32_t* __restrict__ ncol,
-                                                       const cplx<typename MI::R>* __restrict__ nval, int N,
-                                                       long long Nc, int nx, int ny, int B, typename MI::R fvec,
-                                                       typename MI::R frho, int S, int P,
-                                                       const typename MI::R* __restrict__ lamM, typename MI::R fmf) {
-  using R = typename MI::R;
-  using C = cplx<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* ys = reinterpret_cast<C*>(smem_raw);  // [8][B]
-  __shared__ int s_off[kMaxStencil];
-  stencil_offsets_smem(s_off, S, P, nx, ny);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * 8, m = m0 + warp;
-  if (m < N) {
-    const int b0 = base[m];
-    const R* lm = lam + (long long)m * 4 * S;
-    const R* wm = MF ? lamM + (long long)m * 3 * S : nullptr;
-    const int r0 = nptr[m];
-    int r1 = nptr[m + 1];
-#ifdef AIM_CHECK
-    const int Sc = stencil_ok(b0, nx, ny, Nc, P, S, 2) ? S : 0;
-    if (!indices_ok(ncol, r0, r1, N, 3)) r1 = r0;
-#else
-    const int Sc = S;
-#endif
-    const long long cs = Nc * B;  // component stride of PhiT
-    for (int bc = 0; bc < B; bc += 32 * RL) {
-      const int b = bc + RL * lane;  // B is a multiple of RL
-      if (b < B) {
-        C av[RL], ar[RL], an[RL], am[RL];
-#pragma unroll
-        for (int q = 0; q < RL; ++q) av[q] = ar[q] = an[q] = am[q] = cmake<C>(0, 0);
-#pragma unroll 3
-        for (int s = 0; s < Sc; ++s) {
-          const C* ph = PhiT + (b0 + (long long)s_off[s]) * B + b;
-          const Run<C, RL> px = load_run<C, RL>(ph), py = load_run<C, RL>(ph + cs), pz = load_run<C, RL>(ph + 2 * cs),
-                           pr = load_run<C, RL>(ph + 3 * cs);
-          const R wx = lm[s], wy = lm[S + s], wz = lm[2 * S + s], wr = lm[3 * S + s];
-#pragma unroll
-          for (int q = 0; q < RL; ++q) {
-            av[q].x += wx * px.v[q].x + wy * py.v[q].x + wz * pz.v[q].x;
-            av[q].y += wx * px.v[q].y + wy * py.v[q].y + wz * pz.v[q].y;
-            ar[q].x += wr * pr.v[q].x;
-            ar[q].y += wr * pr.v[q].y;
-          }
-          if constexpr (MF) {
-            const R mx = wm[s], my = wm[S + s], mz = wm[2 * S + s];
-#pragma unroll
-            for (int q = 0; q < RL; ++q) {
-              am[q].x += mx * px.v[q].x + my * py.v[q].x + mz * pz.v[q].x;
-              am[q].y += mx * px.v[q].y + my * py.v[q].y + mz * pz.v[q].y;
-            }
-          }
-        }
-        // near entries in batches of EB: the batch's columns first, then its
-        // EB gathers of x, all in flight together
-        constexpr int EB = 4;
-        int e = r0;
-        for (; e + EB <= r1; e += EB) {
-          int col[EB];
-#pragma unroll
-          for (int i = 0; i < EB; ++i) col[i] = ncol[e + i];
-          Run<C, RL> xv[EB];
-#pragma unroll
-          for (int i = 0; i < EB; ++i) xv[i] = load_run<C, RL>(xT + (long long)col[i] * B + b);
-#pragma unroll
-          for (int i = 0; i < EB; ++i) {
-            const C v = nval[e + i];
-#pragma unroll
-            for (int q = 0; q < RL; ++q) {
-              an[q].x += v.x * xv[i].v[q].x - v.y * xv[i].v[q].y;
-              an[q].y += v.x * xv[i].v[q].y + v.y * xv[i].v[q].x;
-            }
-          }
-        }
-        for (; e < r1; ++e) {
-          const C v = nval[e];
-          const Run<C, RL> xv = load_run<C, RL>(xT + (long long)ncol[e] * B + b);
-#pragma unroll
-          for (int q = 0; q < RL; ++q) {
-            an[q].x += v.x * xv.v[q].x - v.y * xv.v[q].y;
-            an[q].y += v.x * xv.v[q].y + v.y * xv.v[q].x;
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < RL; ++q) {
-          C t;
-          t.x = fvec * av[q].x - frho * ar[q].x;
-          t.y = fvec * av[q].y - frho * ar[q].y;
-          C out;
-          out.x = an[q].x - t.y;
-          out.y = an[q].y + t.x;
-          if constexpr (MF) {
-            out.x -= fmf * am[q].x;
-            out.y -= fmf * am[q].y;
-          }
-          ys[warp * B + b + q] = out;
-        }
-      }
-    }
-  }
-  __syncthreads();
-  const int rows = min(8, N - m0);
-  for (int t = threadIdx.x; t < 8 * B; t += blockDim.x) {
-    const int i = t & 7, b = t >> 3;
-    if (i < rows) y[(long long)b * N + m0 + i] = ys[i * B + b];
-  }
-}
-
 // ---- row groups of the many-RHS near product ----
 // Group g holds rows m0 = kNearGroup g .. m0 + kNearGroup - 1 (the last one
 // fewer).  Its near columns are the sorted union of the rows' (sorted)
@@ -457,12 +335,25 @@ __global__ void k_near_groups(const int32_t* __restrict__ nptr, const int32_t* _
 // Interpolation + near correction for many right-hand sides over groups of
 // kNearGroup consecutive basis functions: one warp per group, lanes over
 // right-hand sides (RL consecutive ones per lane) on RHS-minor Phi and x.
-// The grid part runs row by row as in interp_near_rhs; the near part walks
+// The grid part runs row by row (each stencil node's four grid values are
+// contiguous runs of right-hand sides; weights warp-uniform); the near part walks
 // the group's union of columns, so each x run is gathered once per group
 // rather than once per row that holds the column (neighbouring basis
 // functions share most of their near zone), at the price of multiplying the
 // zeros of the rows that lack a column.  The block's 32 rows of y are staged
 // in shared memory and written back in the [B][N] layout.
+// The group's kNearGroup entries of union column u (one 32-byte row for complex64).
+template <class C> struct GroupVals {
+  C v[kNearGroup];
+};
+__device__ __forceinline__ GroupVals<float2> load_group(const float2* p) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+  return GroupVals<float2>{{make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y), make_float2(b.z, b.w)}};
+}
+__device__ __forceinline__ GroupVals<double2> load_group(const double2* p) {
+  return GroupVals<double2>{{p[0], p[1], p[2], p[3]}};
+}
+static_assert(kNearGroup == 4, "load_group reads four entries");
 template <class MI, int RL, bool MF>
 __global__ void __launch_bounds__(256) interp_near_grp(const cplx<typename MI::R>* __restrict__ PhiT,
                                                        const cplx<typename MI::R>* __restrict__ xT,
@@ -561,22 +452,25 @@ __global__ void __launch_bounds__(256) interp_near_grp(const cplx<typename MI::R
 #pragma unroll
         for (int i = 0; i < EB; ++i) xv[i] = load_run<C, RL>(xT + (long long)col[i] * B + b);
 #pragma unroll
-        for (int i = 0; i < EB; ++i)
+        for (int i = 0; i < EB; ++i) {
+          const GroupVals<C> gv = load_group(gval + (long long)(u + i) * G);
 #pragma unroll
           for (int r = 0; r < G; ++r) {
-            const C v = gval[(long long)(u + i) * G + r];
+            const C v = gv.v[r];
 #pragma unroll
             for (int q = 0; q < RL; ++q) {
               acc[r][q].x += v.x * xv[i].v[q].x - v.y * xv[i].v[q].y;
               acc[r][q].y += v.x * xv[i].v[q].y + v.y * xv[i].v[q].x;
             }
           }
+        }
       }
       for (; u < u1; ++u) {
         const Run<C, RL> xv = load_run<C, RL>(xT + (long long)gcol[u] * B + b);
+        const GroupVals<C> gv = load_group(gval + (long long)u * G);
 #pragma unroll
         for (int r = 0; r < G; ++r) {
-          const C v = gval[(long long)u * G + r];
+          const C v = gv.v[r];
 #pragma unroll
           for (int q = 0; q < RL; ++q) {
             acc[r][q].x += v.x * xv.v[q].x - v.y * xv.v[q].y;
