@@ -332,16 +332,6 @@ __global__ void k_near_groups(const int32_t* __restrict__ nptr, const int32_t* _
   if constexpr (!FILL) cnt_or_ptr[g] = (int32_t)u;
 }
 
-// Interpolation + near correction for many right-hand sides over groups of
-// kNearGroup consecutive basis functions: one warp per group, lanes over
-// right-hand sides (RL consecutive ones per lane) on RHS-minor Phi and x.
-// The grid part runs row by row (each stencil node's four grid values are
-// contiguous runs of right-hand sides; weights warp-uniform); the near part walks
-// the group's union of columns, so each x run is gathered once per group
-// rather than once per row that holds the column (neighbouring basis
-// functions share most of their near zone), at the price of multiplying the
-// zeros of the rows that lack a column.  The block's 32 rows of y are staged
-// in shared memory and written back in the [B][N] layout.
 // The group's kNearGroup entries of union column u (one 32-byte row for complex64).
 template <class C> struct GroupVals {
   C v[kNearGroup];
@@ -354,6 +344,17 @@ __device__ __forceinline__ GroupVals<double2> load_group(const double2* p) {
   return GroupVals<double2>{{p[0], p[1], p[2], p[3]}};
 }
 static_assert(kNearGroup == 4, "load_group reads four entries");
+
+// Interpolation + near correction for many right-hand sides over groups of
+// kNearGroup consecutive basis functions: one warp per group, lanes over
+// right-hand sides (RL consecutive ones per lane) on RHS-minor Phi and x.
+// The grid part runs row by row (each stencil node's four grid values are
+// contiguous runs of right-hand sides; weights warp-uniform); the near part walks
+// the group's union of columns, so each x run is gathered once per group
+// rather than once per row that holds the column (neighbouring basis
+// functions share most of their near zone), at the price of multiplying the
+// zeros of the rows that lack a column.  The block's 32 rows of y are staged
+// in shared memory and written back in the [B][N] layout.
 template <class MI, int RL, bool MF>
 __global__ void __launch_bounds__(256) interp_near_grp(const cplx<typename MI::R>* __restrict__ PhiT,
                                                        const cplx<typename MI::R>* __restrict__ xT,
