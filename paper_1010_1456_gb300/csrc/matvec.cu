@@ -371,7 +371,8 @@ __global__ void __launch_bounds__(256) interp_near_grp(const cplx<typename MI::R
   using C = cplx<R>;
   constexpr int G = kNearGroup;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* ys = reinterpret_cast<C*>(smem_raw);  // [8 G][B]
+  C* ys = reinterpret_cast<C*>(smem_raw);  // [8 G][B + 1] (a padded row: the write-back reads down a column)
+  const int YS = B + 1;
   __shared__ int s_off[kMaxStencil];
   stencil_offsets_smem(s_off, S, P, nx, ny);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(256) interp_near_grp(const cplx<typename MI::R
 #pragma unroll
       for (int r = 0; r < G; ++r)
 #pragma unroll
-        for (int q = 0; q < RL; ++q) ys[(warp * G + r) * B + b + q] = acc[r][q];
+        for (int q = 0; q < RL; ++q) ys[(warp * G + r) * YS + b + q] = acc[r][q];
     }
   }
   __syncthreads();
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(256) interp_near_grp(const cplx<typename MI::R
   const int rows = (int)min(8LL * G, (long long)N - mb);
   for (int t = threadIdx.x; t < 8 * G * B; t += blockDim.x) {
     const int i = t % (8 * G), bb = t / (8 * G);
-    if (i < rows) y[(long long)bb * N + mb + i] = ys[i * B + bb];
+    if (i < rows) y[(long long)bb * N + mb + i] = ys[i * YS + bb];
   }
 }
 
@@ -530,9 +531,9 @@ __global__ void __launch_bounds__(256) proj_gather_rhs(const cplx<typename MD::R
       for (int cc = 0; cc < 4; ++cc)
 #pragma unroll
         for (int q = 0; q < RL; ++q) a[cc][q] = cmake<C>(0, 0);
-      for (int e = e0; e < e1; ++e) {
-        const W4<R> ww = load_w4(w, e);
-        const Run<C, RL> xv = load_run<C, RL>(xT + (long long)mm[e] * ldx + b);
+      // entries in batches of EB: the batch's columns, then its EB gathers of x, in flight together
+      constexpr int EB = 4;
+      const auto add = [&](const W4<R>& ww, const Run<C, RL>& xv) {
 #pragma unroll
         for (int q = 0; q < RL; ++q) {
           a[0][q].x += ww.x * xv.v[q].x; a[0][q].y += ww.x * xv.v[q].y;
@@ -540,7 +541,19 @@ __global__ void __launch_bounds__(256) proj_gather_rhs(const cplx<typename MD::R
           a[2][q].x += ww.z * xv.v[q].x; a[2][q].y += ww.z * xv.v[q].y;
           a[3][q].x += ww.w * xv.v[q].x; a[3][q].y += ww.w * xv.v[q].y;
         }
+      };
+      int e = e0;
+      for (; e + EB <= e1; e += EB) {
+        int col[EB];
+#pragma unroll
+        for (int i = 0; i < EB; ++i) col[i] = mm[e + i];
+        Run<C, RL> xv[EB];
+#pragma unroll
+        for (int i = 0; i < EB; ++i) xv[i] = load_run<C, RL>(xT + (long long)col[i] * ldx + b);
+#pragma unroll
+        for (int i = 0; i < EB; ++i) add(load_w4(w, e + i), xv[i]);
       }
+      for (; e < e1; ++e) add(load_w4(w, e), load_run<C, RL>(xT + (long long)mm[e] * ldx + b));
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc)
 #pragma unroll
@@ -914,7 +927,7 @@ static int run_product(aim_ctx* c, const cplx<typename MD::R>* x, cplx<typename 
     AIM_TRY(transpose(c, "transpose_phi", reinterpret_cast<const cplx<R>*>(phi), pd.phiT, nrhs, 4 * Nc));
     AIM_TRY(ensure_near_groups(c, pd));
     const int blocks = (int)((c->N + 8 * kNearGroup - 1) / (8 * kNearGroup));
-    const size_t sm = sizeof(cplx<R>) * 8 * kNearGroup * nrhs;
+    const size_t sm = sizeof(cplx<R>) * 8 * kNearGroup * (nrhs + 1);
     const R fvec = (R)(c->alpha * c->k * kEta0), frho = (R)(c->alpha * kEta0 / c->k),
             fmf = (R)((1.0 - c->alpha) * kEta0);
     const auto go = [&](auto mf, auto rl) {
