@@ -121,7 +121,11 @@ int footprint_estimate(const aim_mesh* mesh, double h, int M, double near_radius
   b += (double)max_rhs * N * (16 * 53 + 48);                           // Krylov basis (m = 50) and vectors
   if (precision != AIM_C128_F64)
     b += (double)N * 4 * S * 8 * 2 + (double)nnz * 16;                 // float-float weights and near values
-  if (max_rhs >= kRhsLanesMin) b += (double)max_rhs * (4.0 * nc + N) * 16;  // RHS-minor copies of Phi and x
+  if (max_rhs >= kRhsLanesMin) {
+    b += (double)max_rhs * (4.0 * nc + N) * 16;  // RHS-minor copies of Phi and x
+    // near row groups: union columns (about 0.4 nnz) with kNearGroup entries each, in the solver precision
+    b += (double)N / kNearGroup * 4 + 0.4 * nnz * (4 + kNearGroup * (precision == AIM_C64 ? 8 : 16));
+  }
   b += (double)mesh->nt * 60 * (144 + 12) + (double)nnz * 56;          // near-fill scratch at setup (peak)
   if (alpha < 1.0)  // MFIE weights in three precisions, MFIE pair blocks and halves at setup
     b += (double)N * 3 * S * (8 + 4 + 8) + (double)mesh->nt * 60 * 144 + (double)nnz * 32;
