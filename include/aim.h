@@ -102,7 +102,12 @@ typedef struct {
                       and precision exceeds it; a later product in a precision whose grids that
                       estimate does not include (see aim_footprint) returns AIM_ENOMEM when its
                       grids would take the planned total above the budget. */
+  int krylov;        /* AIM_GMRES (default): restarted GMRES(restart); AIM_TFQMR: transpose-free QMR
+                      (nine vectors per right-hand side, no basis; restart is not used).  See aim_solve. */
 } aim_opts;
+
+/* Krylov methods of aim_solve (aim_opts.krylov, aim_set_krylov). */
+enum { AIM_GMRES = 0, AIM_TFQMR = 1 };
 
 /* Per-solve report. rel_res and iters are caller arrays of length nrhs. */
 typedef struct {
@@ -142,6 +147,10 @@ int aim_set_stream(aim_ctx* ctx, void* stream);
  * after setup; AIM_EINVAL for anything else. */
 int aim_set_precision(aim_ctx* ctx, int precision);
 
+/* Change the solver's Krylov method (AIM_GMRES or AIM_TFQMR) after setup;
+ * AIM_EINVAL for anything else. */
+int aim_set_krylov(aim_ctx* ctx, int krylov);
+
 /* N (number of unknowns). */
 int aim_num_unknowns(const aim_ctx* ctx, int64_t* N);
 
@@ -176,8 +185,14 @@ int aim_matvec_host(aim_ctx* ctx, const void* x_host, void* y_host, int nrhs, in
 
 /*
  * Solve Z~ X = V for nrhs right-hand sides (paper Section 2.2: diagonal
- * preconditioner, stop on the relative residual).  Right-preconditioned
- * restarted GMRES(m), M^-1 = diag(Z~)^-1.  On the device: the products,
+ * preconditioner, stop on the relative residual; the paper does not name its
+ * Krylov method).  opts.krylov = AIM_GMRES: right-preconditioned restarted
+ * GMRES(m), M^-1 = diag(Z~)^-1.  AIM_TFQMR: transpose-free QMR (Freund) on
+ * the same preconditioned system, two products per step pair, its scalars on
+ * the device and the step pair replayed from a CUDA graph; each cycle runs
+ * until the quasi-residual bound falls below its target, then the true
+ * residual is recomputed as for GMRES (info->restarts counts those cycles,
+ * info->iterations the products).  GMRES:  On the device: the products,
  * classical Gram-Schmidt with FP64 dot products and a second pass where the
  * Daniel-Gragg-Kaufman-Stewart test asks for it, one Arnoldi step replayed
  * from a CUDA graph.  On the host, every opts.check_every steps: Givens

@@ -27,6 +27,8 @@ from ._lib import (  # noqa: F401
     AIM_EXPORT_PROJ_PTR,
     AIM_EXPORT_WEIGHTS,
     AIM_ENOCONV,
+    AIM_GMRES,
+    AIM_TFQMR,
     AIMError,
     aim_mesh,
     aim_opts,
@@ -93,7 +95,8 @@ def aim_default_opts():
 
 
 def aim_setup(verts, tris, k, h, M=2, near_radius=None, precision=AIM_C128, restart=50, maxit=3000,
-              check_every=5, max_rhs=1, stream=None, planar=True, verbose=False, cfie_alpha=1.0, mem_budget=0):
+              check_every=5, max_rhs=1, stream=None, planar=True, verbose=False, cfie_alpha=1.0, mem_budget=0,
+              krylov=AIM_GMRES):
     """Build a context (host FP64 setup + device spectrum); see aim_setup in aim.h."""
     lib = load()
     mesh, keep = _mesh(verts, tris)
@@ -108,6 +111,7 @@ def aim_setup(verts, tris, k, h, M=2, near_radius=None, precision=AIM_C128, rest
     o.verbose = 1 if verbose else 0
     o.cfie_alpha = float(cfie_alpha)
     o.mem_budget = int(mem_budget)
+    o.krylov = int(krylov)
     h_ = C.c_void_p()
     r = 3.0 * h if near_radius is None else float(near_radius)
     check(lib.aim_setup(C.byref(mesh), float(k), float(h), int(M), r, C.byref(o), C.byref(h_)), "aim_setup")
@@ -130,6 +134,11 @@ def aim_set_stream(ctx, stream):
 def aim_set_precision(ctx, precision):
     check(load().aim_set_precision(ctx.handle, int(precision)), "aim_set_precision")
     ctx.precision = precision
+
+
+def aim_set_krylov(ctx, krylov):
+    """AIM_GMRES or AIM_TFQMR for the context's next solves."""
+    check(load().aim_set_krylov(ctx.handle, int(krylov)), "aim_set_krylov")
 
 
 def aim_num_unknowns(ctx):

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, os.environ.get("AIM_LIBRARY", "libaim.so"))
 
 AIM_OK, AIM_EINVAL, AIM_ENOMEM, AIM_ECUDA, AIM_ENOCONV, AIM_ETIMEOUT, AIM_ENODEV = range(7)
 AIM_C64, AIM_C128, AIM_C128_F64 = 1, 2, 3
+AIM_GMRES, AIM_TFQMR = 0, 1
 (AIM_EXPORT_ANCHORS, AIM_EXPORT_WEIGHTS, AIM_EXPORT_NEAR_PTR, AIM_EXPORT_NEAR_COL, AIM_EXPORT_NEAR_VAL,
  AIM_EXPORT_DIAG, AIM_EXPORT_GHAT, AIM_EXPORT_PROJ_PTR, AIM_EXPORT_MFIE_WEIGHTS) = range(1, 10)
 
@@ -34,6 +35,7 @@ class aim_opts(C.Structure):
         ("planar", C.c_int),
         ("cfie_alpha", C.c_double),
         ("mem_budget", C.c_size_t),
+        ("krylov", C.c_int),
     ]
 
 
@@ -54,6 +56,7 @@ SIGNATURES = {
     "aim_destroy": (None, [C.c_void_p]),
     "aim_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "aim_set_precision": (C.c_int, [C.c_void_p, C.c_int]),
+    "aim_set_krylov": (C.c_int, [C.c_void_p, C.c_int]),
     "aim_num_unknowns": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "aim_grid_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "aim_rhs_planewave": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),

@@ -189,6 +189,8 @@ void aim_default_opts(aim_opts* o) {
   o->stream = nullptr;
   o->planar = 1;
   o->cfie_alpha = 1.0;
+  o->mem_budget = 0;
+  o->krylov = AIM_GMRES;
 }
 
 int aim_setup(const aim_mesh* mesh, double k, double h, int M, double near_radius, const aim_opts* opts,
@@ -211,6 +213,10 @@ int aim_setup(const aim_mesh* mesh, double k, double h, int M, double near_radiu
   }
   if (!(o.cfie_alpha > 0.0 && o.cfie_alpha <= 1.0)) {
     set_error("aim_setup: cfie_alpha must be in (0, 1]");
+    return AIM_EINVAL;
+  }
+  if (o.krylov != AIM_GMRES && o.krylov != AIM_TFQMR) {
+    set_error("aim_setup: krylov must be AIM_GMRES or AIM_TFQMR");
     return AIM_EINVAL;
   }
   if (o.restart < 1 || o.restart > 200 || o.max_rhs < 1 || o.max_rhs > 256 || o.maxit < 1 || o.check_every < 1) {
@@ -286,6 +292,16 @@ int aim_set_precision(aim_ctx* ctx, int precision) {
     return AIM_EINVAL;
   }
   ctx->opts.precision = precision;
+  return AIM_OK;
+}
+
+int aim_set_krylov(aim_ctx* ctx, int krylov) {
+  AIM_TRY(check_ctx(ctx));
+  if (krylov != AIM_GMRES && krylov != AIM_TFQMR) {
+    set_error("aim_set_krylov: krylov must be AIM_GMRES or AIM_TFQMR");
+    return AIM_EINVAL;
+  }
+  ctx->opts.krylov = krylov;
   return AIM_OK;
 }
 

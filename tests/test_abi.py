@@ -162,3 +162,15 @@ def test_pack_arguments_are_checked_on_the_host(lib):
     assert lib.aim_pack_solve(None, None, None, 1e-6, None) == _lib.AIM_EINVAL
     assert lib.aim_pack_set_stream(None, None) == _lib.AIM_EINVAL
     lib.aim_pack_destroy(None)  # a no-op
+
+
+def test_unknown_krylov_method_is_rejected_on_the_host(lib):
+    import paper_1010_1456_gb300 as g
+    from aim_inputs import plate_mesh
+    from paper_1010_1456_gb300 import _lib
+
+    v, t = plate_mesh(1.0, 9)
+    with pytest.raises(g.AIMError) as e:
+        g.aim_setup(v, t, 6.28, 0.1, krylov=5, stream=0)
+    assert e.value.code == _lib.AIM_EINVAL
+    assert lib.aim_set_krylov(None, 0) == _lib.AIM_EINVAL

@@ -137,3 +137,53 @@ def test_graph_replayed_steps_equal_direct_launches(sphere):
     g.aim_set_stream(ctx, torch.cuda.current_stream())
     assert torch.equal(Xs, Xg)
     assert true_res(op, V.cpu().numpy(), Xg.cpu().numpy()).max() <= 1.01 * TOL
+
+
+# ---------------------------------------------------------------- TFQMR
+@pytest.mark.parametrize("prec", [g.AIM_C64, g.AIM_C128])
+def test_tfqmr_reaches_tolerance_and_matches_gmres(prec):
+    """TFQMR (aim_opts.krylov = AIM_TFQMR) on the 1 lambda plate with three
+    right-hand sides: every true residual <= 1e-6 against the oracle operator,
+    the solutions equal GMRES's to the tolerance."""
+    v, t = plate_mesh(1.0, 9)
+    op = oaim.AIMOperator(RWG(v, t), K0, H, 2)
+    ctx = g.aim_setup(v, t, K0, H, precision=prec, max_rhs=3, krylov=g.AIM_TFQMR)
+    kh, po = random_incidence(2, seed=3)
+    V = g.aim_rhs_planewave(ctx, kh[:3], po[:3])
+    X, info = g.aim_solve(ctx, V, TOL)
+    assert info["converged"].all() and info["rel_res"].max() <= TOL
+    Vn, Xn = V.cpu().numpy(), X.cpu().numpy()
+    assert true_res(op, Vn, Xn).max() <= 1.01 * TOL
+    g.aim_set_krylov(ctx, g.AIM_GMRES)
+    Xg, ig = g.aim_solve(ctx, V, TOL)
+    assert ig["converged"].all()
+    Xgn = Xg.cpu().numpy()
+    assert np.linalg.norm(Xn - Xgn) <= 1e-4 * np.linalg.norm(Xgn)
+
+
+def test_tfqmr_cfie_sphere_graph_equals_direct(sphere):
+    """TFQMR on the CFIE sphere (alpha 0.6): the step pairs replayed from the
+    captured graph give the iterate of direct launches bit for bit, and the
+    solution meets the tolerance against the oracle's CFIE operator."""
+    R, v, t, _ = sphere
+    op = oaim.AIMOperator(RWG(v, t), K0, H, 2, alpha=0.6)
+    kh, po = random_incidence(1, seed=8)
+    ctx = g.aim_setup(v, t, K0, H, max_rhs=2, precision=g.AIM_C64, cfie_alpha=0.6, krylov=g.AIM_TFQMR)
+    V = g.aim_rhs_planewave(ctx, kh, po)
+    g.aim_solve(ctx, V, TOL)  # first-solve allocations
+    Xg, ig = g.aim_solve(ctx, V, TOL)
+    g.aim_profile(ctx, 1)
+    Xd, idd = g.aim_solve(ctx, V, TOL)
+    g.aim_profile(ctx, 0)
+    assert ig["iterations"] == idd["iterations"] and torch.equal(Xg, Xd)
+    assert ig["converged"].all()
+    assert true_res(op, V.cpu().numpy(), Xg.cpu().numpy()).max() <= 1.01 * TOL
+
+
+def test_tfqmr_rejects_unknown_method():
+    v, t = plate_mesh(1.0, 9)
+    with pytest.raises(g.AIMError):
+        g.aim_setup(v, t, K0, H, krylov=7)
+    ctx = g.aim_setup(v, t, K0, H)
+    with pytest.raises(g.AIMError):
+        g.aim_set_krylov(ctx, 2)
