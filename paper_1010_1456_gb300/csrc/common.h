@@ -167,7 +167,8 @@ struct Profiler {
 };
 
 struct KrylovWork {
-  double2* V = nullptr;      // [B][m+1][N] Arnoldi basis
+  double2* V = nullptr;      // [B][m+1][N] Arnoldi basis (TFQMR: [B][9][N], its vectors)
+  int slots = 0;             // vectors per right-hand side V holds
   double2* w = nullptr;      // [B][N]
   double2* r = nullptr;      // [B][N]
   double2* H = nullptr;      // [m][B][m+1] Hessenberg columns (column j of every RHS is contiguous)

@@ -290,8 +290,17 @@ __global__ void k_xupdate(const double2* __restrict__ V, const double2* __restri
 // ------------------------------------------------------------------ host driver
 int alloc_krylov(aim_ctx* c) {
   KrylovWork& k = c->kw;
-  if (k.V) return AIM_OK;
   const int B = c->max_rhs, m = c->opts.restart, N = c->N;
+  // vectors per right-hand side: the GMRES basis, or the TFQMR vectors
+  const int slots = c->opts.krylov == AIM_TFQMR ? kTfqmrVecs : m + 1;
+  if (k.V && k.slots < slots) {  // a method that needs more vectors than the storage holds
+    drop_step_graph(c);          // its captured step reads the old storage
+    cudaFree(k.V);
+    k.V = nullptr;
+    AIM_CUDA_TRY(cudaMalloc(&k.V, (size_t)N * sizeof(double2) * B * slots));
+    k.slots = slots;
+  }
+  if (k.V) return AIM_OK;
   k.m = m;
   // norm kernel: about four blocks per SM over all right-hand sides, at least 256 elements per block
   k.nblk = std::max(1, std::min((4 * 152 + B - 1) / B, (N + 255) / 256));
@@ -299,8 +308,8 @@ int alloc_krylov(aim_ctx* c) {
   k.nblk_dot = std::max(1, std::min((2 * 152 + B - 1) / B, (N + 1023) / 1024));
   const int nb = std::max(k.nblk, k.nblk_dot);
   const size_t vec = (size_t)N * sizeof(double2);
-  // at least kTfqmrVecs slots per right-hand side (the TFQMR vectors share the basis storage)
-  AIM_CUDA_TRY(cudaMalloc(&k.V, vec * B * std::max(m + 1, kTfqmrVecs)));
+  AIM_CUDA_TRY(cudaMalloc(&k.V, vec * B * slots));
+  k.slots = slots;
   AIM_CUDA_TRY(cudaMalloc(&k.w, vec * B));
   AIM_CUDA_TRY(cudaMalloc(&k.r, vec * B));
   AIM_CUDA_TRY(cudaMalloc(&k.H, sizeof(double2) * B * (m + 1) * m));
