@@ -172,10 +172,9 @@ struct KrylovWork {
   double2* w = nullptr;      // [B][N]
   double2* r = nullptr;      // [B][N]
   double2* H = nullptr;      // [m][B][m+1] Hessenberg columns (column j of every RHS is contiguous)
-  double2* hcol = nullptr;   // [B][m+1] current column (dot results)
   double2* partial = nullptr;// [B][nblk][m+1+kDotGroup] partial dots
   double2* y = nullptr;      // [B][m] least-squares solution of the cycle
-  double* nrm = nullptr;     // [B] norms; then w0 [B] (|w|^2 before orthogonalising), norm partials
+  double* nrm = nullptr;     // [B] norms, [B] spare, then [B][nblk] norm partials
   double* bnorm = nullptr;   // [B]
   double2* h_H = nullptr;    // pinned host copy of H columns
   int* active = nullptr;     // [B]

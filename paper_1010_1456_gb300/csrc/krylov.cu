@@ -90,61 +90,49 @@ __global__ void __launch_bounds__(256) k_dots(const double2* __restrict__ V, con
   block_reduce_store<kDotGroup>(acc, partial + ((long long)b * nblk + blk) * ldp + i0, 1);
 }
 
-// hcol[b][i] = sum over blocks of the partial dots (one warp per (b, i));
-// H[j][b][i] = hcol (first pass) or += hcol (second pass).  First pass,
-// slot i = j + 1: w0[b] = |w|^2.
-__global__ void __launch_bounds__(256) k_dots_reduce(const double2* __restrict__ partial, double2* __restrict__ hcol,
-                                                     double2* __restrict__ H, double* __restrict__ w0,
-                                                     const int* __restrict__ jdev, const int* __restrict__ reorth,
-                                                     int nblk, int ldp, int m, int B, int pass) {
-  const int j = *jdev, nvec = j + 1;
-  const int nslot = pass == 0 ? nvec + 1 : nvec;
-  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int b = wid / (m + 2), i = wid % (m + 2);
-  if (b >= B || i >= nslot || (pass == 1 && !reorth[b])) return;
-  double2 s = make_double2(0, 0);
-  for (int blk = lane; blk < nblk; blk += 32) {
-    const double2 p = partial[((long long)b * nblk + blk) * ldp + i];
-    s.x += p.x;
-    s.y += p.y;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-  }
-  if (lane != 0) return;
-  if (i == nvec) {  // first pass only
-    w0[b] = s.x;
-    return;
-  }
-  hcol[(long long)b * (m + 1) + i] = s;
-  double2* h = H + ((long long)j * B + b) * (m + 1) + i;
-  if (pass == 1) {
-    h->x += s.x;
-    h->y += s.y;
-  } else {
-    *h = s;
-  }
-}
-
-// w[b] -= sum_{i <= j} hcol[b][i] V[b][i].  After the first pass every block
-// of right-hand side b evaluates the re-orthogonalisation test of Daniel,
-// Gragg, Kaufman and Stewart on the same data, |w1|^2 = |w0|^2 - |h|^2 <
-// |w0|^2 / 2, and block 0 stores it; the second pass runs only where it holds.
+// w[b] -= sum_{i <= j} h[b][i] V[b][i], where every block first sums the dot
+// kernel's partials itself (h[i] = sum over blk of partial[b][blk][i], in a
+// fixed order, so every block holds the same values) and block 0 stores the
+// Hessenberg column: H[j][b][i] = h (first pass) or += h (second pass).  On
+// the first pass slot i = j + 1 holds |w|^2 before orthogonalising, and
+// block 0 evaluates the re-orthogonalisation test of Daniel, Gragg, Kaufman
+// and Stewart, |w1|^2 = |w0|^2 - |h|^2 < |w0|^2 / 2; the second pass runs
+// only where it holds.
 __global__ void __launch_bounds__(256) k_update(const double2* __restrict__ V, double2* __restrict__ w,
-                                                const double2* __restrict__ hcol, const double* __restrict__ w0,
+                                                const double2* __restrict__ partial, double2* __restrict__ H,
                                                 int* __restrict__ reorth, const int* __restrict__ jdev, int N,
-                                                int ldv_vec, int m, int pass) {
+                                                int ldv_vec, int m, int B, int nblk, int ldp, int pass) {
   __shared__ double2 hs[256];
   const int b = blockIdx.y;
   if (pass == 1 && !reorth[b]) return;
-  const int nvec = *jdev + 1;
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = hcol[(long long)b * (m + 1) + i];
+  const int j = *jdev, nvec = j + 1;
+  const int nslot = pass == 0 ? nvec + 1 : nvec;
+  for (int i = threadIdx.x; i < nslot; i += blockDim.x) {
+    double2 t = make_double2(0, 0);
+    for (int blk = 0; blk < nblk; ++blk) {
+      const double2 p = partial[((long long)b * nblk + blk) * ldp + i];
+      t.x += p.x;
+      t.y += p.y;
+    }
+    hs[i] = t;
+  }
   __syncthreads();
-  if (pass == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-    double h2 = 0.0;
-    for (int i = 0; i < nvec; ++i) h2 += hs[i].x * hs[i].x + hs[i].y * hs[i].y;
-    reorth[b] = (w0[b] - h2) < 0.5 * w0[b] ? 1 : 0;
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+      double2* h = H + ((long long)j * B + b) * (m + 1) + i;
+      if (pass == 1) {
+        h->x += hs[i].x;
+        h->y += hs[i].y;
+      } else {
+        *h = hs[i];
+      }
+    }
+    if (pass == 0 && threadIdx.x == 0) {
+      double h2 = 0.0;
+      for (int i = 0; i < nvec; ++i) h2 += hs[i].x * hs[i].x + hs[i].y * hs[i].y;
+      const double w0 = hs[nvec].x;
+      reorth[b] = (w0 - h2) < 0.5 * w0 ? 1 : 0;
+    }
   }
   const double2* Vb = V + (long long)b * ldv_vec * N;
   double2* wb = w + (long long)b * N;
@@ -313,7 +301,6 @@ int alloc_krylov(aim_ctx* c) {
   AIM_CUDA_TRY(cudaMalloc(&k.w, vec * B));
   AIM_CUDA_TRY(cudaMalloc(&k.r, vec * B));
   AIM_CUDA_TRY(cudaMalloc(&k.H, sizeof(double2) * B * (m + 1) * m));
-  AIM_CUDA_TRY(cudaMalloc(&k.hcol, sizeof(double2) * B * (m + 1)));
   AIM_CUDA_TRY(cudaMalloc(&k.partial, sizeof(double2) * B * nb * (m + 1 + kDotGroup)));
   AIM_CUDA_TRY(cudaMalloc(&k.y, sizeof(double2) * B * std::max(m, kTfqmrScalars)));
   AIM_CUDA_TRY(cudaMalloc(&k.nrm, sizeof(double) * B * (2 + nb)));
@@ -335,7 +322,7 @@ void free_krylov(aim_ctx* c) {
   KrylovWork& k = c->kw;
   if (k.step_exec) cudaGraphExecDestroy(k.step_exec);
   if (k.cap_stream) cudaStreamDestroy(k.cap_stream);
-  cudaFree(k.V); cudaFree(k.w); cudaFree(k.r); cudaFree(k.H); cudaFree(k.hcol); cudaFree(k.partial);
+  cudaFree(k.V); cudaFree(k.w); cudaFree(k.r); cudaFree(k.H); cudaFree(k.partial);
   cudaFree(k.y); cudaFree(k.nrm); cudaFree(k.bnorm);
   cudaFree(k.active); cudaFree(k.reorth); cudaFree(k.jdev);
   if (k.h_H) cudaFreeHost(k.h_H);
@@ -348,10 +335,8 @@ struct Solver {
   KrylovWork& k;
   int B, N, m;
   cudaStream_t st;
-  double* w0;        // device [B]
   double* npart;     // device [B][nblk]
   Solver(aim_ctx* cc, int nrhs) : c(cc), k(cc->kw), B(nrhs), N(cc->N), m(cc->kw.m), st(cc->stream) {
-    w0 = k.nrm + B;
     npart = k.nrm + 2 * B;
   }
   dim3 vgrid() const { return dim3((unsigned)std::min(1024, std::max(1, (N + 255) / 256)), B); }
@@ -386,16 +371,12 @@ struct Solver {
     }
     const int ldp = m + 1 + kDotGroup;
     const dim3 dgrid((m + 2 + kDotGroup - 1) / kDotGroup, k.nblk_dot, B);
-    const int rblocks = (B * (m + 2) * 32 + 255) / 256;
     for (int pass = 0; pass < 2; ++pass) {
       AIM_LAUNCH(c, "k_dots", k_dots<<<dgrid, 256, 0, st>>>(k.V, k.w, k.partial, k.jdev, k.reorth, N, m + 1,
                                                             k.nblk_dot, ldp, pass));
       AIM_TRY(chk("k_dots"));
-      AIM_LAUNCH(c, "k_dots_reduce", k_dots_reduce<<<rblocks, 256, 0, st>>>(k.partial, k.hcol, k.H, w0, k.jdev,
-                                                                            k.reorth, k.nblk_dot, ldp, m, B, pass));
-      AIM_TRY(chk("k_dots_reduce"));
-      AIM_LAUNCH(c, "k_update", k_update<<<vgrid(), 256, 0, st>>>(k.V, k.w, k.hcol, w0, k.reorth, k.jdev, N, m + 1,
-                                                                  m, pass));
+      AIM_LAUNCH(c, "k_update", k_update<<<vgrid(), 256, 0, st>>>(k.V, k.w, k.partial, k.H, k.reorth, k.jdev, N,
+                                                                  m + 1, m, B, k.nblk_dot, ldp, pass));
       AIM_TRY(chk("k_update"));
     }
     AIM_TRY(norm_partials(k.w, N));
