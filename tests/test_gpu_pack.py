@@ -166,3 +166,27 @@ def test_pack_rejects_mismatched_contexts():
     finally:
         for c in (a, b, s):
             c.close()
+
+
+def test_packed_tfqmr_solve_matches_gmres():
+    """A pack takes its Krylov method from its first context: TFQMR on two
+    plates gives every instance the GMRES solution to the tolerance."""
+    ctxs = []
+    for side, n in ((1.0, 9), (1.3, 12)):
+        v, t = plate_mesh(side, n)
+        ctxs.append(g.aim_setup(v, t, K0, H, max_rhs=2, precision=g.AIM_C64, krylov=g.AIM_TFQMR))
+    try:
+        kh, po = random_incidence(1, seed=6)
+        Vs = [g.aim_rhs_planewave(c, kh, po) for c in ctxs]
+        pack = g.aim_pack_create(ctxs, [2, 2])
+        X, info = g.aim_pack_solve(pack, pack.pack(Vs), tol=1e-6)
+        assert info["converged"].all() and info["rel_res"].max() <= 1e-6
+        for i, c in enumerate(ctxs):
+            g.aim_set_krylov(c, g.AIM_GMRES)
+            Xg, _ = g.aim_solve(c, Vs[i].clone(), tol=1e-6)
+            a = Xg.cpu().numpy()
+            assert np.linalg.norm(pack.unpack(X)[i].cpu().numpy() - a) <= 1e-4 * np.linalg.norm(a)
+        pack.close()
+    finally:
+        for c in ctxs:
+            c.close()
