@@ -43,7 +43,7 @@ void free_context(aim_ctx* c) {
   cudaFree(c->plan_dev);
   free_krylov(c);
   profile_free(c);
-  cudaFree(c->ngrp_ptr); cudaFree(c->ngrp_col);
+  cudaFree(c->ngrp_ptr); cudaFree(c->ngrp_col); cudaFree(c->colmask);
   cudaFree(c->base); cudaFree(c->near_ptr); cudaFree(c->near_col); cudaFree(c->pnode_ptr); cudaFree(c->pnode_m);
   cudaFree(c->diag); cudaFree(c->dinv64); cudaFree(c->d_verts); cudaFree(c->d_tris); cudaFree(c->rwg_tri);
   cudaFree(c->rwg_free); cudaFree(c->rwg_len); cudaFree(c->tri_area); cudaFree(c->tri_nrm); cudaFree(c->pgroups);

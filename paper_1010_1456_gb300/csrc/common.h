@@ -203,6 +203,11 @@ struct aim_ctx {
   // with z passes only)
   int sparse_proj = 0;
   int32_t* pgroups = nullptr;  // [ngroups] indices g of the groups [8g, 8g + 8) with entries
+  // Grids with z passes: [ny][nx] flags of the (x, y) columns that hold a
+  // stencil node.  The forward z pass reads no other column (its input is
+  // zero there) and the inverse z pass writes no other (nothing interpolates
+  // from it).
+  uint8_t* colmask = nullptr;
   int64_t ngroups = 0;
   double alpha = 1.0;        // CFIE weight of the EFIE (1: EFIE)
   int kk0 = 0;               // that plane's offset in the stencil

@@ -376,6 +376,7 @@ static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P
   if (zpass) {  // z forward: g0 [G][nz][ny][nx] -> g1 [G][Lz][ny][nx]
     StridedArgs a{};
     a.n_in = nz; a.n_out = Lz; a.X = nx; a.A = ny;
+    a.cols = c->colmask;  // empty (x, y) columns read nothing
     a.sG_in = (long long)nz * ny * nx; a.sA_in = nx; a.sP_in = (long long)ny * nx;
     a.sG_out = (long long)Lz * ny * nx; a.sA_out = nx; a.sP_out = (long long)ny * nx;
     AIM_TRY((strided_pass<P, false>(c, 0, "fft_z_fwd", g0, g1, a, G, pd + 2, Lz, tw[2])));
@@ -404,6 +405,7 @@ static int convolve(aim_ctx* c, typename P::S* g0, typename P::S* g1, typename P
   if (zpass) {  // z inverse: g1 -> phi [G][nz][ny][nx] (g0, or g2 when grid0 keeps the projection's zeros)
     StridedArgs a{};
     a.n_in = Lz; a.n_out = nz; a.X = nx; a.A = ny;
+    a.cols = c->colmask;  // columns without a stencil node are never interpolated from
     a.sG_in = (long long)Lz * ny * nx; a.sA_in = nx; a.sP_in = (long long)ny * nx;
     a.sG_out = (long long)nz * ny * nx; a.sA_out = nx; a.sP_out = (long long)ny * nx;
     AIM_TRY((strided_pass<P, true>(c, 4, "fft_z_inv", g1, phi, a, G, pd + 2, Lz, tw[2])));

@@ -34,6 +34,10 @@ struct StridedArgs4 {
   int X, A;         // contiguous extent, other-axis extent
   long long sG_in, sA_in, sP_in;
   long long sG_out, sA_out, sP_out;
+  // optional [A][X] flags of the pencils that matter (z passes of a 3-D grid:
+  // the (x, y) columns that hold a stencil node): the others read no input
+  // (it is zero) and, in an inverse pass, write no output (nothing reads it)
+  const uint8_t* cols = nullptr;
 };
 
 struct XArgs4 {
@@ -97,7 +101,7 @@ __device__ __forceinline__ void strided_body(const typename P::S* __restrict__ i
   for (int u = threadIdx.x; u < nay * TX * L2; u += blockDim.x) {
     const int t = u / (TX * L2), rem = u - t * (TX * L2);
     const int c = rem % TX, n2 = rem / TX;
-    const bool col = x0 + c < a.X;
+    const bool col = x0 + c < a.X && (!a.cols || a.cols[(long long)(ia0 + t) * a.X + x0 + c]);
     const S* src = in + g * a.sG_in + (long long)(ia0 + t) * a.sA_in + x0 + c;
     T v[L1];
     static_for<0, L1>([&](auto n1) {
@@ -119,7 +123,7 @@ __device__ __forceinline__ void strided_body(const typename P::S* __restrict__ i
     static_for<0, L2>([&](auto n2) { w[n2] = P::ld(y[(k1 * L2 + decltype(n2)::value) * TX + c]); });
     RegDFT<P, L2, INV>::run(w);
     O* dst = out + g * a.sG_out + (long long)(ia0 + t) * a.sA_out + x0 + c;
-    if (x0 + c < a.X)
+    if (x0 + c < a.X && (!INV || !a.cols || a.cols[(long long)(ia0 + t) * a.X + x0 + c]))
       static_for<0, L2>([&](auto k2) {
         const int p = k1 + L1 * decltype(k2)::value;
         if (p < a.n_out) dst[(long long)p * a.sP_out] = OutConv4<S, O>::f(P::st(w[k2]));

@@ -468,6 +468,7 @@ int build_context(aim_ctx* c, const aim_mesh* mesh) {
     c->pgroups = pj.groups;
     c->ngroups = pj.ngroups;
   }
+  if (c->L[2] > 1) AIM_TRY(column_mask_device(c, c->pnode_ptr, Nc, &c->colmask));
   clk.mark("projection lists");
 
   // ---- FP32 copies and the inverse diagonal

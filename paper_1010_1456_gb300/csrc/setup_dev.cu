@@ -823,4 +823,20 @@ int inverse_diag_device(aim_ctx* c, const double2* d, double2** out) {
   return launch_check(c, "setup_convert");
 }
 
+
+// ---- column flags of the z passes
+__global__ void k_colmask(const int32_t* __restrict__ ptr, long long Nc, long long plane, uint8_t* __restrict__ mask) {
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < Nc; u += (long long)gridDim.x * blockDim.x)
+    if (ptr[u + 1] > ptr[u]) mask[u % plane] = 1;  // every writer stores the same value
+}
+
+int column_mask_device(aim_ctx* c, const int32_t* pnode_ptr, long long Nc, uint8_t** out) {
+  const long long plane = (long long)c->n[0] * c->n[1];
+  AIM_CUDA_TRY(cudaMalloc(out, plane));
+  AIM_CUDA_TRY(cudaMemsetAsync(*out, 0, plane, c->stream));
+  AIM_LAUNCH(c, "setup_colmask", (k_colmask<<<(unsigned)std::min<long long>((Nc + 255) / 256, 152LL * 32), 256, 0,
+                                              c->stream>>>(pnode_ptr, Nc, plane, *out)));
+  return launch_check(c, "setup_colmask");
+}
+
 }  // namespace aim

@@ -70,6 +70,8 @@ struct ProjLists {
   long long nent = 0, ngroups = 0;
 };
 int projection_device(aim_ctx* c, const double* lam, int S, int P, long long Nc, ProjLists* out);
+// [n_y][n_x] flags of the grid columns (x, y) that hold a node with projection entries.
+int column_mask_device(aim_ctx* c, const int32_t* pnode_ptr, long long Nc, uint8_t** out);
 
 int to_f32_device(aim_ctx* c, const double* in, long long n, float** out);
 int inverse_diag_device(aim_ctx* c, const double2* d, double2** out);
