@@ -275,3 +275,38 @@ def test_pack_of_one_scatterer_is_a_merged_solve():
     s = FakePackingServer([10, 10], slots=1, mem_budget=100, pack=4)
     res, _ = s.run(reqs, realtime=False)
     assert s.solves == [[[0, 1]]]
+
+
+def test_pack_class_and_box_volume():
+    """Flat meshes (constant z) get the planar class and a one-plane box; the
+    box grows with the bounding box in grid steps."""
+    flat = serve.Request(0, np.array([[0.0, 0, 0], [1.0, 0, 0], [0, 1.0, 0]]), np.zeros((1, 3), np.int32),
+                         np.zeros((1, 3)), np.zeros((1, 3)))
+    solid = serve.Request(1, np.array([[0.0, 0, 0], [1.0, 0, 0], [0, 1.0, 0.5]]), np.zeros((1, 3), np.int32),
+                          np.zeros((1, 3)), np.zeros((1, 3)))
+    assert serve.pack_class(flat)[-1] is True and serve.pack_class(solid)[-1] is False
+    assert serve.pack_class(flat)[:4] == serve.pack_class(solid)[:4]
+    # h = 0.1, M = 2: 10 + 4 nodes per unit side, one plane when flat
+    assert serve.box_volume(flat) == 14 * 14 * 1
+    assert serve.box_volume(solid) == 14 * 14 * 9
+
+
+def test_pack_rows_layout_on_the_host():
+    """Pack.pack / unpack place instance i's [nrhs_i, N_i] block at rows
+    b0_i.. and columns 0..N_i - 1 of the [B, ld] array, zeros elsewhere."""
+    torch = pytest.importorskip("torch")
+    from paper_1010_1456_gb300 import Pack
+
+    class C:
+        def __init__(self, N):
+            self.N = N
+
+    p = Pack(None, [C(3), C(5)], [2, 1], 5, 3, [0, 2])
+    a = torch.arange(6, dtype=torch.float64).reshape(2, 3) + 1
+    b = torch.arange(5, dtype=torch.float64).reshape(1, 5) + 10
+    packed = p.pack([a, b])
+    assert packed.shape == (3, 5)
+    assert torch.equal(packed[:2, :3], a) and torch.count_nonzero(packed[:2, 3:]).item() == 0
+    assert torch.equal(packed[2:, :], b)
+    ua, ub = p.unpack(packed)
+    assert torch.equal(ua, a) and torch.equal(ub, b)
