@@ -411,11 +411,13 @@ int aim_matvec_c64_noalloc(aim_ctx* ctx, const void* x_dev, void* y_dev, int nrh
  *   <= max_rhs of ctxs[i], sum <= 256).  The contexts must share the device,
  *   k, h, M and the stencil layout (all planar, or none), and must outlive
  *   the pack; while the pack is in use they must not run work of their own.
- *   The pack takes stream, restart, maxit and check_every from ctxs[0]'s
- *   options; its solver runs complex64 Arnoldi products with FP64-accurate
- *   true residuals (AIM_C64 refinement).  Allocates the pack's grids,
- *   spectrum and staging vectors; synchronises.  AIM_EINVAL for mismatched
- *   contexts or bad counts.
+ *   The pack takes stream, restart, maxit, check_every and krylov from
+ *   ctxs[0]'s options; its solver runs complex64 products with FP64-accurate
+ *   true residuals (AIM_C64 refinement).  Allocates the pack's grids
+ *   (complex64, 4 B grids over the pack's box, three pass buffers), spectrum,
+ *   staging vectors and, at its first solve, solver storage; none of it is
+ *   part of any context's aim_footprint estimate.  Synchronises.  AIM_EINVAL
+ *   for mismatched contexts or bad counts.
  * aim_pack_dims: ld, total right-hand sides, and the first row b0 of each
  *   instance (b0 may be NULL, else [K]).
  * aim_pack_matvec: y = Z~ x for every packed row.  AIM_C64: x_dev, y_dev c64
