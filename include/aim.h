@@ -120,14 +120,15 @@ typedef struct {
 void aim_default_opts(aim_opts* opts);
 
 /*
- * Build a context for one scatterer (paper Section 2.2: AIM fill).  Host FP64
- * setup: RWG functions, stencil anchors a = floor(c/h - (M-1)/2), moment-
- * matching weights on (M+1)^3 grid nodes (with CFIE also the MFIE's
- * differentiated-interpolation weights), near list |c_m - c_n| <= near_radius,
- * projection lists.  Device FP64: near entries (symmetrised MoM entry minus
- * its grid approximation; with CFIE plus the MFIE entry minus its grid form)
- * and the grid Green's function spectrum on the zero-padded grid (padded
- * length per axis = smallest 2,3,5-smooth integer >= 2n-1), kept resident.
+ * Build a context for one scatterer (paper Section 2.2: AIM fill), in FP64.
+ * On the host: RWG functions (mesh topology), stencil anchors
+ * a = floor(c/h - (M-1)/2) and the grid box.  On the device: moment-matching
+ * weights on (M+1)^3 grid nodes (with CFIE also the MFIE's differentiated-
+ * interpolation weights), near list |c_m - c_n| <= near_radius, projection
+ * lists, near entries (symmetrised MoM entry minus its grid approximation;
+ * with CFIE plus the MFIE entry minus its grid form) and the grid Green's
+ * function spectrum on the zero-padded grid (padded length per axis =
+ * smallest 2,3,5-smooth integer >= 2n-1), all kept resident.
  *   k > 0, h > 0, M in {1, ..., 5} (M = 2: 27 nodes; the paper's production
  *   setting is M = 3, its reference solutions go to M = 5), near_radius >= 0.
  *   Synchronises.
