@@ -111,8 +111,9 @@ enum { AIM_GMRES = 0, AIM_TFQMR = 1 };
 
 /* Per-solve report. rel_res and iters are caller arrays of length nrhs. */
 typedef struct {
-  int32_t iterations;    /* inner Arnoldi steps taken (all right-hand sides in lockstep) */
-  int32_t restarts;      /* restart cycles (each ends with an FP64 true residual) */
+  int32_t iterations;    /* inner steps taken, all right-hand sides in lockstep (GMRES: Arnoldi
+                            steps; TFQMR: products) */
+  int32_t restarts;      /* cycles (each ends with an FP64-accurate true residual) */
   double* rel_res;       /* [nrhs] out: final true relative residual ||b - Z x|| / ||b|| */
   int32_t* converged;    /* [nrhs] out: 1 if rel_res <= tol */
 } aim_solve_info;
